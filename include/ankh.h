@@ -1,0 +1,140 @@
+/*
+ * ankh.h -- C ABI of the GB300 implementation of ANKH-FFT: the periodic
+ * point-multipole Coulomb energy of the paper's Eq. 1 (charges, dipoles,
+ * quadrupoles on the lattice 2 r_B Z^3), evaluated by the interpolated-Ewald
+ * split of Sec. 3-4 (Alg. 5), and its exact gradient.
+ *
+ * Units: positions in Angstrom, charges in e, dipoles in e*A, quadrupoles in
+ * e*A^2, energies in e^2/A (no Coulomb constant, as in Eq. 1).
+ *
+ * Conventions shared by every entry point:
+ *   - The box is cubic with edge L = 2 r_B, centred at the origin (Eq. 1 and
+ *     Sec. 3.3).  Positions outside it are wrapped.
+ *   - D_u = q_u + mu_u . grad + Theta_u : grad grad (Sec. 1); Theta is
+ *     symmetric and passed as its six stored entries xx, xy, xz, yy, yz, zz.
+ *   - dEdtheta is the derivative with respect to those six stored entries
+ *     (a stored off-diagonal entry stands for both Theta_ab and Theta_ba).
+ *   - Arrays are row-major, float32, in the caller's atom order.
+ *   - Device pointers are caller-owned; the library never frees them and
+ *     never keeps them after the call returns.
+ *   - All device work is issued on the given CUDA stream (NULL = legacy
+ *     default stream).  Calls on one handle must not overlap.
+ *   - Return value: ANKH_OK or one of the error codes below; the message of
+ *     the last error of the calling thread is returned by ankh_last_error().
+ *     No C++ exception crosses the ABI.
+ */
+#ifndef ANKH_H
+#define ANKH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    ANKH_OK = 0,
+    ANKH_EINVAL = 1,   /* invalid argument (sizes, orders, NULL pointer, box) */
+    ANKH_ENOMEM = 2,   /* device or host allocation failed; nothing leaked */
+    ANKH_ECUDA = 3,    /* a CUDA or cuFFT call failed */
+    ANKH_ETIMEOUT = 4, /* a bounded device-side wait ran out */
+    ANKH_ENUMERIC = 5  /* a non-finite input coordinate was seen */
+};
+
+/* flags */
+#define ANKH_INCLUDE_REC 1u  /* add the smooth reciprocal part of the xi split
+                                to the far-field kernel (approximates the full
+                                Ewald energy; without it E_rec(xi) is neglected
+                                as in Sec. 3.1) -- default on */
+#define ANKH_MIXED 2u        /* adjacent-leaf correction on the tensor cores
+                                (3xTF32 split, FP32 accumulate); otherwise plain
+                                FP32 on the CUDA cores */
+
+typedef struct {
+    double xi;        /* Ewald screening [1/A]; Sec. 5 uses 0.01 */
+    int n_cells;      /* leaves per axis n >= 3 (0 = choose from the box) */
+    int Lu;           /* equispaced interpolation order, 2..8 (0 = 5) */
+    int Lc;           /* Chebyshev interpolation order, 2..16 (0 = Lu) */
+    int max_order;    /* 0 = charges, 1 = + dipoles, 2 = + quadrupoles */
+    unsigned flags;   /* ANKH_* flags above */
+} ankh_params;
+
+typedef struct {
+    int n_cells, Lu, Lc, nf;  /* leaves per axis, orders, fine grid points per axis = n (Lu-1) */
+    int64_t n_atoms;
+    double box, h, xi;
+    double precompute_ms;     /* wall time of ankh_create's table set-up */
+    int64_t device_bytes;     /* device memory held by the handle */
+} ankh_info;
+
+typedef struct ankh_handle ankh_handle;
+
+/* Fill *p with the defaults (xi = 0.01, n chosen from the box, Lu = Lc = 5,
+ * quadrupoles, ANKH_INCLUDE_REC | ANKH_MIXED). */
+void ankh_default_params(ankh_params *p);
+
+/* Create a handle for a cubic box of edge box_edge (= 2 r_B) holding N atoms.
+ * Runs the per-box precomputation (Alg. 4 / Sec. 4.3): the interpolation
+ * matrices, the spectrum of the periodic far-field kernel on the merged
+ * equispaced grid, and the adjacent-leaf correction blocks.  Allocates all
+ * device scratch on the current device.  params may be NULL (defaults).
+ * Errors: ANKH_EINVAL (N < 1, box not finite and > 0, n < 3, orders out of
+ * range, xi <= 0), ANKH_ENOMEM, ANKH_ECUDA.  *out is NULL on error. */
+int ankh_create(double box_edge, int64_t N, const ankh_params *params, ankh_handle **out);
+
+/* Energy of Eq. 1 by Alg. 5: near field over adjacent leaves (step 3), far
+ * field by the diagonalised circulant (step 2), self term (step 4).
+ * x: N x 3 device; q: N device; mu: N x 3 device or NULL; theta: N x 6 device
+ * or NULL.  *E_host receives the energy after the stream work completes (the
+ * call synchronises the stream).  Errors: ANKH_EINVAL, ANKH_ECUDA,
+ * ANKH_ENUMERIC. */
+int ankh_energy(ankh_handle *h, const float *x, const float *q, const float *mu,
+                const float *theta, double *E_host, void *cuda_stream);
+
+/* Energy and its exact gradient (the adjoint of every step; forces are not in
+ * the paper, which lists them as future work in Sec. 3.8 and 6).
+ * Outputs (device, N x 3 / N / N x 3 / N x 6 / N x 3, each may be NULL):
+ *   dEdx = dE/dx (minus the force), dEdq = potential, dEdmu = minus the field,
+ *   dEdtheta (stored-entry convention), torque = -dE/d(rotation angle) of each
+ *   atom's dipole and quadrupole about its own position.
+ * E_host may be NULL (then the call does not synchronise). */
+int ankh_energy_forces(ankh_handle *h, const float *x, const float *q, const float *mu,
+                       const float *theta, double *E_host, float *dEdx, float *dEdq,
+                       float *dEdmu, float *dEdtheta, float *torque, void *cuda_stream);
+
+/* Same as ankh_energy_forces with HOST input and output arrays (pageable or
+ * pinned): copies in, evaluates, copies out, synchronises. */
+int ankh_energy_forces_host(ankh_handle *h, const float *x, const float *q, const float *mu,
+                            const float *theta, double *E, float *dEdx, float *dEdq,
+                            float *dEdmu, float *dEdtheta, float *torque, void *cuda_stream);
+
+/* Energy terms of the last completed call on h, in e^2/A:
+ * [0] near field, [1] far field on the merged grid (k != 0), [2] its k = 0
+ * term, [3] adjacent-leaf correction, [4] self term, [5] total. */
+int ankh_last_terms(const ankh_handle *h, double terms[6]);
+
+int ankh_get_info(const ankh_handle *h, ankh_info *info);
+
+/* Copy an internal device buffer of the last call into caller memory dst
+ * (device pointer, at least *bytes long; with dst == NULL only *bytes is
+ * set).  which: 0 = permutation (int32, sorted slot -> atom), 1 = leaf
+ * start offsets (int32, n^3 + 1), 2 = equispaced modified charges M
+ * (float32, n^3 x ldm), 3 = merged grid charges (float32, nf^3),
+ * 4 = correction potential psi (float32, n^3 x ldm, forces calls only),
+ * 5 = leaf id of each sorted slot (int32).  ldm = ankh_ldm(h). */
+int ankh_debug_copy(const ankh_handle *h, int which, void *dst, int64_t *bytes, void *cuda_stream);
+int ankh_ldm(const ankh_handle *h);
+
+/* Free everything the handle owns.  NULL is ignored. */
+void ankh_destroy(ankh_handle *h);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char *ankh_last_error(void);
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int ankh_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ANKH_H */

@@ -1,0 +1,498 @@
+// C ABI of libankh: handle life cycle, per-box precomputation and the
+// evaluation sequence of Alg. 5 on one GPU.
+#include "ankh_internal.cuh"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+namespace ankh {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string &msg) { g_err = msg; }
+
+static int fail(int code, const std::string &msg)
+{
+    set_error(msg);
+    return code;
+}
+
+#define ANKH_CU(call, what)                                                                   \
+    do {                                                                                      \
+        cudaError_t _e = (call);                                                              \
+        if (_e != cudaSuccess)                                                                \
+            return fail(_e == cudaErrorMemoryAllocation ? ANKH_ENOMEM : ANKH_ECUDA,           \
+                        std::string(what) + ": " + cudaGetErrorString(_e));                  \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Host FP64 tables
+
+// Fused Chebyshev -> equispaced derivative matrices W_p = (2/h)^p E H D^p,
+// p = 0..3, each L_u x L_c (Sec. 3.4 and 4.1):
+//   Chebyshev nodes r_k = cos((2k+1) pi / (2 L_c));
+//   H[k][m] = (m == 0 ? 1 : 2 T_m(r_k)) / L_c        (S = H T);
+//   D with T' = D T: D[m][j] = 2m / c_j for j < m, m - j odd (c_0 = 2);
+//   E[a][k] = U_a(r_k), U_a the Lagrange basis of the L_u equispaced nodes
+//   -1 + 2a/(L_u - 1).
+static std::vector<double> make_W(int Lu, int Lc, double h)
+{
+    std::vector<double> r(Lc), Hm(Lc * Lc), Dm(Lc * Lc, 0.0), Em(Lu * Lc);
+    for (int k = 0; k < Lc; ++k) r[k] = std::cos((2.0 * k + 1.0) * M_PI / (2.0 * Lc));
+    for (int k = 0; k < Lc; ++k) {
+        double t0 = 1.0, t1 = r[k];
+        for (int m = 0; m < Lc; ++m) {
+            double tm;
+            if (m == 0) tm = 1.0;
+            else if (m == 1) tm = r[k];
+            else {
+                tm = 2.0 * r[k] * t1 - t0;
+                t0 = t1;
+                t1 = tm;
+            }
+            Hm[k * Lc + m] = (m == 0 ? 1.0 : 2.0 * tm) / Lc;
+        }
+    }
+    for (int m = 0; m < Lc; ++m)
+        for (int j = 0; j < m; ++j)
+            if ((m - j) % 2 == 1) Dm[m * Lc + j] = 2.0 * m / (j == 0 ? 2.0 : 1.0);
+    for (int a = 0; a < Lu; ++a)
+        for (int k = 0; k < Lc; ++k) {
+            double u = 1.0, ea = -1.0 + 2.0 * a / (Lu - 1);
+            for (int c = 0; c < Lu; ++c) {
+                if (c == a) continue;
+                double ec = -1.0 + 2.0 * c / (Lu - 1);
+                u *= (r[k] - ec) / (ea - ec);
+            }
+            Em[a * Lc + k] = u;
+        }
+    std::vector<double> W(4 * Lu * Lc);
+    std::vector<double> Dp(Lc * Lc, 0.0), tmp(Lc * Lc);
+    for (int k = 0; k < Lc; ++k) Dp[k * Lc + k] = 1.0;
+    double scale = 1.0;
+    for (int p = 0; p < 4; ++p) {
+        // EH = E * H, then EH * D^p
+        for (int a = 0; a < Lu; ++a)
+            for (int m = 0; m < Lc; ++m) {
+                double s = 0.0;
+                for (int k = 0; k < Lc; ++k) {
+                    double eh = 0.0;
+                    for (int kk = 0; kk < Lc; ++kk) eh += Em[a * Lc + kk] * Hm[kk * Lc + k];
+                    s += eh * Dp[k * Lc + m];
+                }
+                W[(p * Lu + a) * Lc + m] = scale * s;
+            }
+        // Dp = D * Dp
+        for (int i = 0; i < Lc; ++i)
+            for (int j = 0; j < Lc; ++j) {
+                double s = 0.0;
+                for (int k = 0; k < Lc; ++k) s += Dm[i * Lc + k] * Dp[k * Lc + j];
+                tmp[i * Lc + j] = s;
+            }
+        Dp = tmp;
+        scale *= 2.0 / h;
+    }
+    return W;
+}
+
+// Adjacent-leaf correction blocks C_d, d = (dx+1)*9 + (dy+1)*3 + (dz+1):
+//   (C_d)_{kl} = erfc(xi r)/r at z = (k - l - d (Lu-1)) delta if |k - l - d (Lu-1)|_inf >= Lu - 1.
+static std::vector<double> make_C(int Lu, int ldm, double delta, double xi)
+{
+    const int P = Lu * Lu * Lu;
+    std::vector<double> C((size_t)27 * ldm * ldm, 0.0);
+    for (int d = 0; d < 27; ++d) {
+        const int dv[3] = {d / 9 - 1, (d / 3) % 3 - 1, d % 3 - 1};
+        for (int k = 0; k < P; ++k) {
+            const int kv[3] = {k / (Lu * Lu), (k / Lu) % Lu, k % Lu};
+            for (int l = 0; l < P; ++l) {
+                const int lv[3] = {l / (Lu * Lu), (l / Lu) % Lu, l % Lu};
+                int jmax = 0;
+                double r2 = 0.0;
+                for (int a = 0; a < 3; ++a) {
+                    const int j = kv[a] - lv[a] - dv[a] * (Lu - 1);
+                    jmax = std::max(jmax, std::abs(j));
+                    r2 += (j * delta) * (j * delta);
+                }
+                if (jmax < Lu - 1) continue;
+                const double r = std::sqrt(r2);
+                C[((size_t)d * ldm + k) * ldm + l] = std::erfc(xi * r) / r;
+            }
+        }
+    }
+    return C;
+}
+
+static bool good_fft_size(int m)
+{
+    for (int p : {2, 3, 5, 7})
+        while (m % p == 0) m /= p;
+    return m == 1;
+}
+
+static int choose_n(double box, int Lu)
+{
+    // leaf edge near 4.4 A for L_u = 5 (balances near-field pairs and
+    // correction work); prefer a merged grid size with small prime factors
+    const double target = 4.4;
+    int n0 = std::max(3, (int)std::lround(box / target));
+    int best = n0;
+    for (int dn = 0; dn <= 3; ++dn) {
+        for (int sgn : {1, -1}) {
+            int n = n0 + sgn * dn;
+            if (n < 3) continue;
+            if (good_fft_size(n * (Lu - 1))) return n;
+        }
+    }
+    return best;
+}
+
+static void free_device(Handle *H)
+{
+    if (!H) return;
+    void *ptrs[] = {H->d_cellid, H->d_rank, H->d_count, H->d_start, H->d_perm, H->d_scell, H->d_flag,
+                    H->d_A0, H->d_A1, H->d_A2, H->d_A3, H->d_W, H->d_M, H->d_rho, H->d_rhohat, H->d_D,
+                    H->d_phi, H->d_C, H->d_Chi, H->d_Clo, H->d_psi, H->d_gfar, H->d_gnear, H->d_part,
+                    H->d_partoff, H->d_terms, H->d_hostbuf};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (H->h_terms) cudaFreeHost(H->h_terms);
+    if (H->have_plans) {
+        cufftDestroy(H->plan_r2c);
+        cufftDestroy(H->plan_c2r);
+    }
+    H->have_plans = 0;
+}
+
+template <typename T>
+static cudaError_t dalloc(Handle *H, T **p, size_t count)
+{
+    size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+    cudaError_t e = cudaMalloc((void **)p, bytes);
+    if (e == cudaSuccess) H->device_bytes += (int64_t)bytes;
+    return e;
+}
+
+static int run_sequence(Handle &H, const float *x, const float *q, const float *mu, const float *theta,
+                        bool forces, float *dEdx, float *dEdq, float *dEdmu, float *dEdtheta, float *torque,
+                        cudaStream_t s)
+{
+    ANKH_CU(launch_bin(H, x, s), "bin");
+    ANKH_CU(launch_scan(H, s), "scan");
+    ANKH_CU(launch_scatter_sort_gather(H, x, q, mu, theta, s), "sort");
+    ANKH_CU(launch_self_dc(H, s), "self");
+    ANKH_CU(launch_p2m(H, s), "p2m");
+    ANKH_CU(launch_fine_gather(H, s), "merge");
+    if (cufftSetStream(H.plan_r2c, s) != CUFFT_SUCCESS) return fail(ANKH_ECUDA, "cufftSetStream");
+    if (cufftExecR2C(H.plan_r2c, H.d_rho, H.d_rhohat) != CUFFT_SUCCESS) return fail(ANKH_ECUDA, "cufftExecR2C");
+    ANKH_CU(launch_spectral(H, forces, s), "spectral");
+    ANKH_CU(launch_corr(H, forces, s), "corr");
+    ANKH_CU(launch_near(H, forces, s), "near");
+    if (forces) {
+        if (cufftSetStream(H.plan_c2r, s) != CUFFT_SUCCESS) return fail(ANKH_ECUDA, "cufftSetStream");
+        if (cufftExecC2R(H.plan_c2r, H.d_rhohat, H.d_phi) != CUFFT_SUCCESS)
+            return fail(ANKH_ECUDA, "cufftExecC2R");
+        ANKH_CU(launch_l2p(H, s), "l2p");
+        ANKH_CU(launch_finalize(H, dEdx, dEdq, dEdmu, dEdtheta, torque, s), "finalize");
+    }
+    ANKH_CU(launch_reduce(H, s), "reduce");
+    return ANKH_OK;
+}
+
+static int fetch_terms(Handle &H, double *E_host, cudaStream_t s)
+{
+    ANKH_CU(cudaMemcpyAsync(H.h_terms, H.d_terms, 8 * sizeof(double), cudaMemcpyDeviceToHost, s), "copy E");
+    ANKH_CU(cudaStreamSynchronize(s), "synchronize");
+    for (int k = 0; k < 6; ++k) H.last_terms[k] = H.h_terms[k];
+    if (std::isnan(H.h_terms[5])) return fail(ANKH_ENUMERIC, "non-finite input coordinate");
+    if (E_host) *E_host = H.h_terms[5];
+    return ANKH_OK;
+}
+
+}  // namespace ankh
+
+using namespace ankh;
+
+struct ankh_handle {
+    Handle h;
+};
+
+extern "C" {
+
+int ankh_version(void) { return 100; }
+
+const char *ankh_last_error(void) { return g_err.c_str(); }
+
+void ankh_default_params(ankh_params *p)
+{
+    if (!p) return;
+    p->xi = 0.01;
+    p->n_cells = 0;
+    p->Lu = 5;
+    p->Lc = 5;
+    p->max_order = 2;
+    p->flags = ANKH_INCLUDE_REC | ANKH_MIXED;
+}
+
+int ankh_create(double box_edge, int64_t N, const ankh_params *params, ankh_handle **out)
+{
+    if (!out) return fail(ANKH_EINVAL, "out is NULL");
+    *out = nullptr;
+    ankh_params p;
+    ankh_default_params(&p);
+    if (params) p = *params;
+    if (!(box_edge > 0.0) || !std::isfinite(box_edge)) return fail(ANKH_EINVAL, "box edge must be finite and > 0");
+    if (N < 1 || N > (int64_t)1 << 30) return fail(ANKH_EINVAL, "N out of range [1, 2^30]");
+    if (p.Lu == 0) p.Lu = 5;
+    if (p.Lc == 0) p.Lc = p.Lu;
+    if (p.Lu < 2 || p.Lu > kMaxLu) return fail(ANKH_EINVAL, "Lu out of range [2, 8]");
+    if (p.Lc < 2 || p.Lc > kMaxLc) return fail(ANKH_EINVAL, "Lc out of range [2, 16]");
+    if (!(p.xi > 0.0) || !std::isfinite(p.xi)) return fail(ANKH_EINVAL, "xi must be > 0");
+    if (p.max_order < 0 || p.max_order > 2) return fail(ANKH_EINVAL, "max_order out of range [0, 2]");
+    int n = p.n_cells ? p.n_cells : choose_n(box_edge, p.Lu);
+    if (n < 3) return fail(ANKH_EINVAL, "at least 3 leaves per axis are needed");
+    if ((int64_t)n * (p.Lu - 1) > 1024) return fail(ANKH_EINVAL, "merged grid larger than 1024 points per axis");
+
+    auto t0 = std::chrono::steady_clock::now();
+    ankh_handle *hh = new (std::nothrow) ankh_handle();
+    if (!hh) return fail(ANKH_ENOMEM, "host allocation");
+    Handle &H = hh->h;
+    std::memset(&H, 0, sizeof(Handle));
+    cudaGetDevice(&H.device);
+    H.N = N;
+    H.max_order = p.max_order;
+    H.flags = p.flags;
+    Geo &g = H.g;
+    g.n = n;
+    g.ncell = n * n * n;
+    g.Lu = p.Lu;
+    g.Lc = p.Lc;
+    g.P = p.Lu * p.Lu * p.Lu;
+    g.ldm = ((g.P + 31) / 32) * 32;
+    g.nf = n * (p.Lu - 1);
+    g.nfh = g.nf / 2 + 1;
+    g.M = (int64_t)g.nf * g.nf * g.nf;
+    g.box = box_edge;
+    g.rB = box_edge / 2.0;
+    g.inv_box = 1.0 / box_edge;
+    g.h = box_edge / n;
+    g.hf = (float)g.h;
+    g.two_over_h = (float)(2.0 / g.h);
+    g.xi = (float)p.xi;
+
+    auto bail = [&](int code, const std::string &msg) {
+        free_device(&H);
+        delete hh;
+        return fail(code, msg);
+    };
+#define ANKH_AL(ptr, cnt)                                                               \
+    do {                                                                                \
+        cudaError_t _e = dalloc(&H, &(ptr), (size_t)(cnt));                             \
+        if (_e != cudaSuccess) return bail(ANKH_ENOMEM, std::string("cudaMalloc ") + #ptr); \
+    } while (0)
+
+    const int64_t nspec = (int64_t)g.nf * g.nf * g.nfh;
+    ANKH_AL(H.d_cellid, N);
+    ANKH_AL(H.d_rank, N);
+    ANKH_AL(H.d_count, g.ncell);
+    ANKH_AL(H.d_start, g.ncell + 1);
+    ANKH_AL(H.d_perm, N);
+    ANKH_AL(H.d_scell, N);
+    ANKH_AL(H.d_flag, 4);
+    ANKH_AL(H.d_A0, N);
+    ANKH_AL(H.d_A1, N);
+    ANKH_AL(H.d_A2, N);
+    ANKH_AL(H.d_A3, N);
+    ANKH_AL(H.d_W, 4 * g.Lu * g.Lc);
+    ANKH_AL(H.d_M, (int64_t)g.ncell * g.ldm);
+    ANKH_AL(H.d_rho, g.M);
+    ANKH_AL(H.d_rhohat, nspec);
+    ANKH_AL(H.d_D, nspec);
+    ANKH_AL(H.d_phi, g.M);
+    ANKH_AL(H.d_C, (int64_t)27 * g.ldm * g.ldm);
+    ANKH_AL(H.d_psi, (int64_t)g.ncell * g.ldm);
+    ANKH_AL(H.d_gfar, 13 * N);
+    ANKH_AL(H.d_gnear, 13 * N);
+    // energy partial layout
+    int nb[kPartCount];
+    nb[kPartNear] = near_blocks(H);
+    nb[kPartGlob] = spectral_blocks(H);
+    nb[kPartCorr] = corr_blocks(H);
+    nb[kPartSelf] = self_blocks(H);
+    nb[kPartQ] = self_blocks(H);
+    H.part_off[0] = 0;
+    for (int k = 0; k < kPartCount; ++k) H.part_off[k + 1] = H.part_off[k] + nb[k];
+    ANKH_AL(H.d_part, H.part_off[kPartCount]);
+    ANKH_AL(H.d_partoff, kPartCount + 1);
+    ANKH_AL(H.d_terms, 8);
+    if (cudaMallocHost(&H.h_terms, 8 * sizeof(double)) != cudaSuccess)
+        return bail(ANKH_ENOMEM, "cudaMallocHost");
+    if (cudaMemcpy(H.d_partoff, H.part_off, sizeof(int) * (kPartCount + 1), cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(ANKH_ECUDA, "upload part offsets");
+    cudaMemset(H.d_part, 0, sizeof(double) * H.part_off[kPartCount]);
+    cudaMemset(H.d_terms, 0, 8 * sizeof(double));
+    cudaMemset(H.d_psi, 0, sizeof(float) * (size_t)g.ncell * g.ldm);
+
+    // tables
+    {
+        std::vector<double> W = make_W(g.Lu, g.Lc, g.h);
+        std::vector<float> Wf(W.begin(), W.end());
+        if (cudaMemcpy(H.d_W, Wf.data(), Wf.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(ANKH_ECUDA, "upload W");
+        std::vector<double> C = make_C(g.Lu, g.ldm, g.h / (g.Lu - 1), p.xi);
+        std::vector<float> Cf(C.begin(), C.end());
+        if (cudaMemcpy(H.d_C, Cf.data(), Cf.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(ANKH_ECUDA, "upload C");
+    }
+    std::string perr;
+    if (precompute_kernel_spectrum(H, &H.D0, perr) != cudaSuccess) return bail(ANKH_ECUDA, perr);
+    if (cufftPlan3d(&H.plan_r2c, g.nf, g.nf, g.nf, CUFFT_R2C) != CUFFT_SUCCESS)
+        return bail(ANKH_ECUDA, "cufftPlan3d R2C");
+    if (cufftPlan3d(&H.plan_c2r, g.nf, g.nf, g.nf, CUFFT_C2R) != CUFFT_SUCCESS) {
+        cufftDestroy(H.plan_r2c);
+        return bail(ANKH_ECUDA, "cufftPlan3d C2R");
+    }
+    H.have_plans = 1;
+    if (cudaDeviceSynchronize() != cudaSuccess) return bail(ANKH_ECUDA, "precompute synchronize");
+    auto t1 = std::chrono::steady_clock::now();
+    H.precompute_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+#undef ANKH_AL
+    *out = hh;
+    set_error("");
+    return ANKH_OK;
+}
+
+void ankh_destroy(ankh_handle *h)
+{
+    if (!h) return;
+    free_device(&h->h);
+    delete h;
+}
+
+static int check_inputs(ankh_handle *h, const float *x, const float *q)
+{
+    if (!h) return fail(ANKH_EINVAL, "handle is NULL");
+    if (!x || !q) return fail(ANKH_EINVAL, "x and q are required");
+    return ANKH_OK;
+}
+
+int ankh_energy(ankh_handle *h, const float *x, const float *q, const float *mu, const float *theta,
+                double *E_host, void *cuda_stream)
+{
+    int rc = check_inputs(h, x, q);
+    if (rc) return rc;
+    if (!E_host) return fail(ANKH_EINVAL, "E_host is NULL");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    rc = run_sequence(h->h, x, q, mu, theta, false, nullptr, nullptr, nullptr, nullptr, nullptr, s);
+    if (rc) return rc;
+    return fetch_terms(h->h, E_host, s);
+}
+
+int ankh_energy_forces(ankh_handle *h, const float *x, const float *q, const float *mu,
+                       const float *theta, double *E_host, float *dEdx, float *dEdq, float *dEdmu,
+                       float *dEdtheta, float *torque, void *cuda_stream)
+{
+    int rc = check_inputs(h, x, q);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    rc = run_sequence(h->h, x, q, mu, theta, true, dEdx, dEdq, dEdmu, dEdtheta, torque, s);
+    if (rc) return rc;
+    if (E_host) return fetch_terms(h->h, E_host, s);
+    return ANKH_OK;
+}
+
+int ankh_energy_forces_host(ankh_handle *h, const float *x, const float *q, const float *mu,
+                            const float *theta, double *E, float *dEdx, float *dEdq, float *dEdmu,
+                            float *dEdtheta, float *torque, void *cuda_stream)
+{
+    int rc = check_inputs(h, x, q);
+    if (rc) return rc;
+    Handle &H = h->h;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const int64_t N = H.N;
+    // staging layout (floats): x 3N, q N, mu 3N, theta 6N | dEdx 3N, dEdq N, dEdmu 3N, dEdtheta 6N, torque 3N
+    const int64_t need = (13 + 16) * N * (int64_t)sizeof(float);
+    if (H.hostbuf_bytes < need) {
+        if (H.d_hostbuf) cudaFree(H.d_hostbuf);
+        H.d_hostbuf = nullptr;
+        H.hostbuf_bytes = 0;
+        ANKH_CU(cudaMalloc(&H.d_hostbuf, need), "cudaMalloc staging");
+        H.hostbuf_bytes = need;
+    }
+    float *dx = H.d_hostbuf, *dq = dx + 3 * N, *dmu = dq + N, *dth = dmu + 3 * N;
+    float *ox = dth + 6 * N, *oq = ox + 3 * N, *omu = oq + N, *oth = omu + 3 * N, *otq = oth + 6 * N;
+    ANKH_CU(cudaMemcpyAsync(dx, x, 3 * N * sizeof(float), cudaMemcpyHostToDevice, s), "H2D x");
+    ANKH_CU(cudaMemcpyAsync(dq, q, N * sizeof(float), cudaMemcpyHostToDevice, s), "H2D q");
+    if (mu) ANKH_CU(cudaMemcpyAsync(dmu, mu, 3 * N * sizeof(float), cudaMemcpyHostToDevice, s), "H2D mu");
+    if (theta) ANKH_CU(cudaMemcpyAsync(dth, theta, 6 * N * sizeof(float), cudaMemcpyHostToDevice, s), "H2D theta");
+    rc = run_sequence(H, dx, dq, mu ? dmu : nullptr, theta ? dth : nullptr, true, ox, oq, omu, oth, otq, s);
+    if (rc) return rc;
+    if (dEdx) ANKH_CU(cudaMemcpyAsync(dEdx, ox, 3 * N * sizeof(float), cudaMemcpyDeviceToHost, s), "D2H dEdx");
+    if (dEdq) ANKH_CU(cudaMemcpyAsync(dEdq, oq, N * sizeof(float), cudaMemcpyDeviceToHost, s), "D2H dEdq");
+    if (dEdmu) ANKH_CU(cudaMemcpyAsync(dEdmu, omu, 3 * N * sizeof(float), cudaMemcpyDeviceToHost, s), "D2H dEdmu");
+    if (dEdtheta)
+        ANKH_CU(cudaMemcpyAsync(dEdtheta, oth, 6 * N * sizeof(float), cudaMemcpyDeviceToHost, s), "D2H dEdtheta");
+    if (torque) ANKH_CU(cudaMemcpyAsync(torque, otq, 3 * N * sizeof(float), cudaMemcpyDeviceToHost, s), "D2H torque");
+    double Ed = 0.0;
+    rc = fetch_terms(H, &Ed, s);
+    if (rc) return rc;
+    if (E) *E = Ed;
+    return ANKH_OK;
+}
+
+int ankh_last_terms(const ankh_handle *h, double terms[6])
+{
+    if (!h || !terms) return fail(ANKH_EINVAL, "NULL argument");
+    for (int k = 0; k < 6; ++k) terms[k] = h->h.last_terms[k];
+    return ANKH_OK;
+}
+
+int ankh_get_info(const ankh_handle *h, ankh_info *info)
+{
+    if (!h || !info) return fail(ANKH_EINVAL, "NULL argument");
+    const Handle &H = h->h;
+    info->n_cells = H.g.n;
+    info->Lu = H.g.Lu;
+    info->Lc = H.g.Lc;
+    info->nf = H.g.nf;
+    info->n_atoms = H.N;
+    info->box = H.g.box;
+    info->h = H.g.h;
+    info->xi = H.g.xi;
+    info->precompute_ms = H.precompute_ms;
+    info->device_bytes = H.device_bytes;
+    return ANKH_OK;
+}
+
+int ankh_ldm(const ankh_handle *h) { return h ? h->h.g.ldm : 0; }
+
+int ankh_debug_copy(const ankh_handle *h, int which, void *dst, int64_t *bytes, void *cuda_stream)
+{
+    if (!h || !bytes) return fail(ANKH_EINVAL, "NULL argument");
+    const Handle &H = h->h;
+    const void *src = nullptr;
+    int64_t nb = 0;
+    switch (which) {
+    case 0: src = H.d_perm; nb = H.N * 4; break;
+    case 1: src = H.d_start; nb = (int64_t)(H.g.ncell + 1) * 4; break;
+    case 2: src = H.d_M; nb = (int64_t)H.g.ncell * H.g.ldm * 4; break;
+    case 3: src = H.d_rho; nb = H.g.M * 4; break;
+    case 4: src = H.d_psi; nb = (int64_t)H.g.ncell * H.g.ldm * 4; break;
+    case 5: src = H.d_scell; nb = H.N * 4; break;
+    default: return fail(ANKH_EINVAL, "unknown buffer id");
+    }
+    *bytes = nb;
+    if (!dst) return ANKH_OK;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    ANKH_CU(cudaMemcpyAsync(dst, src, nb, cudaMemcpyDeviceToDevice, s), "debug copy");
+    ANKH_CU(cudaStreamSynchronize(s), "synchronize");
+    return ANKH_OK;
+}
+
+}  // extern "C"

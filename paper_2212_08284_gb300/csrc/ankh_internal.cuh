@@ -1,0 +1,99 @@
+// Internal declarations of libankh (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <cstdint>
+#include <string>
+
+#include "../../include/ankh.h"
+
+namespace ankh {
+
+constexpr int kMaxLu = 8;
+constexpr int kMaxLc = 16;
+
+// Device-side view of one handle's geometry and buffers, passed by value to kernels.
+struct Geo {
+    int n;            // leaves per axis
+    int ncell;        // n^3
+    int Lu, Lc;       // interpolation orders
+    int P;            // Lu^3 nodes per leaf
+    int ldm;          // padded leading dimension of per-leaf node arrays (multiple of 32)
+    int nf;           // merged equispaced grid points per axis, n (Lu - 1)
+    int nfh;          // nf / 2 + 1
+    int64_t M;        // nf^3
+    double box, rB, inv_box, h;
+    float hf;         // leaf edge (float)
+    float two_over_h; // chain-rule factor of x_hat = 2 (x - ctr) / h
+    float xi;
+};
+
+// Energy partial slots (FP64 per block, reduced in a fixed order).
+enum PartSlot { kPartNear = 0, kPartGlob = 1, kPartCorr = 2, kPartSelf = 3, kPartQ = 4, kPartCount = 5 };
+
+struct Handle {
+    Geo g;
+    int64_t N;
+    int max_order;
+    unsigned flags;
+    int device;
+    double D0;              // k = 0 value of the far-field kernel spectrum (FP64)
+    double precompute_ms;
+    int64_t device_bytes;
+
+    // atoms (sorted by leaf)
+    int *d_cellid, *d_rank, *d_count, *d_start, *d_perm, *d_scell, *d_flag;
+    float4 *d_A0, *d_A1, *d_A2, *d_A3;   // (lx, ly, lz, q) (mu, 0) (txx, txy, txz, tyy) (tyz, tzz, 0, 0)
+    // interpolation
+    float *d_W;             // [4][Lu][Lc] fused Chebyshev->equispaced derivative matrices, scaled by (2/h)^p
+    float *d_M;             // [ncell][ldm] equispaced modified charges
+    float *d_rho;           // [nf^3] merged grid charges
+    cufftComplex *d_rhohat; // [nf][nf][nfh]
+    float *d_D;             // [nf][nf][nfh] real spectrum of the far-field kernel (k = 0 removed)
+    float *d_phi;           // [nf^3] merged grid potential (unnormalised c2r output)
+    float *d_C;             // [27][ldm][ldm] adjacent-leaf correction blocks (FP32)
+    float *d_Chi, *d_Clo;   // same, split into TF32 high / low parts for the tensor-core path
+    float *d_psi;           // [ncell][ldm] correction potential
+    float *d_gfar;          // [13][Nslot] far-field gradient per sorted slot
+    float *d_gnear;         // [13][Nslot] near-field gradient per sorted slot
+    double *d_part;         // energy partials
+    int part_off[kPartCount + 1];
+    int *d_partoff;         // device copy of part_off
+    double *d_terms;        // [8] reduced energy terms
+    double *h_terms;        // pinned host copy
+    float *d_hostbuf;       // staging for the host-buffer entry point
+    int64_t hostbuf_bytes;
+    double last_terms[6];
+    cufftHandle plan_r2c, plan_c2r;
+    int have_plans;
+};
+
+// error reporting (thread-local message)
+void set_error(const std::string &msg);
+
+// kernels launchers (each returns cudaGetLastError())
+cudaError_t launch_bin(Handle &H, const float *x, cudaStream_t s);
+cudaError_t launch_scan(Handle &H, cudaStream_t s);
+cudaError_t launch_scatter_sort_gather(Handle &H, const float *x, const float *q, const float *mu,
+                                       const float *theta, cudaStream_t s);
+cudaError_t launch_p2m(Handle &H, cudaStream_t s);
+cudaError_t launch_fine_gather(Handle &H, cudaStream_t s);
+cudaError_t launch_spectral(Handle &H, bool forces, cudaStream_t s);
+cudaError_t launch_corr(Handle &H, bool forces, cudaStream_t s);
+cudaError_t launch_near(Handle &H, bool forces, cudaStream_t s);
+cudaError_t launch_l2p(Handle &H, cudaStream_t s);
+cudaError_t launch_self_dc(Handle &H, cudaStream_t s);
+cudaError_t launch_finalize(Handle &H, float *dEdx, float *dEdq, float *dEdmu, float *dEdtheta,
+                            float *torque, cudaStream_t s);
+cudaError_t launch_reduce(Handle &H, cudaStream_t s);
+
+// precomputation on the device (FP64)
+cudaError_t precompute_kernel_spectrum(Handle &H, double *D0_out, std::string &err);
+
+int near_blocks(const Handle &H);
+int spectral_blocks(const Handle &H);
+int corr_blocks(const Handle &H);
+int self_blocks(const Handle &H);
+
+}  // namespace ankh

@@ -1,0 +1,171 @@
+// Leaf binning and stable sort of the atoms by leaf (step 1 of the ANKH
+// method, Sec. 3.2: the leaves of a perfect octree form a uniform n^3 grid).
+//
+// Bit-exact contract: the leaf of atom i is computed in correctly rounded
+// FP64 without fused operations,
+//     s = (x + r_B) * (1/L);  s = s - floor(s);  c = min(floor(s * n), n - 1),
+// and the atoms are ordered by (leaf, original index).  Counting uses
+// atomics (any order), then each leaf's slots are sorted by atom index, so the
+// final permutation is deterministic.
+#include "ankh_internal.cuh"
+
+namespace ankh {
+
+__device__ __forceinline__ int leaf_coord(double xv, const Geo &g, double *frac_times_n)
+{
+    double s = __dmul_rn(__dadd_rn(xv, g.rB), g.inv_box);
+    s = __dadd_rn(s, -floor(s));
+    double sn = __dmul_rn(s, (double)g.n);
+    int c = (int)floor(sn);
+    if (c > g.n - 1) c = g.n - 1;
+    *frac_times_n = sn;
+    return c;
+}
+
+__global__ void k_bin(int N, const float *__restrict__ x, Geo g, int *__restrict__ cellid,
+                      int *__restrict__ rank, int *__restrict__ count, int *__restrict__ flag)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int c[3];
+    bool bad = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double xv = (double)x[3 * (int64_t)i + a];
+        if (!isfinite(xv)) { bad = true; xv = 0.0; }
+        double sn;
+        c[a] = leaf_coord(xv, g, &sn);
+    }
+    if (bad) atomicOr(flag, 1);
+    int cell = (c[0] * g.n + c[1]) * g.n + c[2];
+    cellid[i] = cell;
+    rank[i] = atomicAdd(&count[cell], 1);
+}
+
+// Exclusive scan of the per-leaf counts (single block, 1024 threads).
+__global__ void k_scan(int ncell, const int *__restrict__ count, int *__restrict__ start)
+{
+    __shared__ int warp_tot[32];
+    const int nt = blockDim.x;
+    const int tid = threadIdx.x;
+    const int chunk = (ncell + nt - 1) / nt;
+    const int b = min(tid * chunk, ncell), e = min(b + chunk, ncell);
+    int sum = 0;
+    for (int k = b; k < e; ++k) sum += count[k];
+    // inclusive warp scan
+    int v = sum;
+    const int lane = tid & 31, wid = tid >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    if (lane == 31) warp_tot[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        int w = (lane < (nt >> 5)) ? warp_tot[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        warp_tot[lane] = w;
+    }
+    __syncthreads();
+    int excl = v - sum + (wid > 0 ? warp_tot[wid - 1] : 0);
+    for (int k = b; k < e; ++k) {
+        start[k] = excl;
+        excl += count[k];
+    }
+    if (tid == nt - 1) start[ncell] = excl;
+}
+
+__global__ void k_scatter(int N, const int *__restrict__ cellid, const int *__restrict__ rank,
+                          const int *__restrict__ start, int *__restrict__ perm)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    perm[start[cellid[i]] + rank[i]] = i;
+}
+
+// One thread per leaf: insertion sort of its slots by original atom index.
+__global__ void k_leafsort(int ncell, const int *__restrict__ start, int *__restrict__ perm)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    int b = start[c], e = start[c + 1];
+    for (int k = b + 1; k < e; ++k) {
+        int v = perm[k];
+        int j = k - 1;
+        while (j >= b && perm[j] > v) {
+            perm[j + 1] = perm[j];
+            --j;
+        }
+        perm[j + 1] = v;
+    }
+}
+
+// Gather the atoms into leaf order; coordinates relative to the leaf centre
+// (computed in FP64, rounded once to FP32).
+__global__ void k_gather(int N, const int *__restrict__ perm, const float *__restrict__ x,
+                         const float *__restrict__ q, const float *__restrict__ mu,
+                         const float *__restrict__ th, Geo g, int *__restrict__ scell,
+                         float4 *__restrict__ A0, float4 *__restrict__ A1, float4 *__restrict__ A2,
+                         float4 *__restrict__ A3)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    int i = perm[s];
+    float l[3];
+    int c[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double xv = (double)x[3 * (int64_t)i + a];
+        if (!isfinite(xv)) xv = 0.0;
+        double sn;
+        c[a] = leaf_coord(xv, g, &sn);
+        double loc = __dmul_rn(__dadd_rn(sn, -((double)c[a] + 0.5)), g.h);
+        l[a] = (float)loc;
+    }
+    scell[s] = (c[0] * g.n + c[1]) * g.n + c[2];
+    A0[s] = make_float4(l[0], l[1], l[2], q[i]);
+    if (mu) A1[s] = make_float4(mu[3 * (int64_t)i], mu[3 * (int64_t)i + 1], mu[3 * (int64_t)i + 2], 0.f);
+    else A1[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (th) {
+        const float *t = th + 6 * (int64_t)i;
+        A2[s] = make_float4(t[0], t[1], t[2], t[3]);
+        A3[s] = make_float4(t[4], t[5], 0.f, 0.f);
+    } else {
+        A2[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+        A3[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+cudaError_t launch_bin(Handle &H, const float *x, cudaStream_t s)
+{
+    cudaMemsetAsync(H.d_count, 0, sizeof(int) * H.g.ncell, s);
+    cudaMemsetAsync(H.d_flag, 0, sizeof(int), s);
+    int N = (int)H.N;
+    k_bin<<<(N + 255) / 256, 256, 0, s>>>(N, x, H.g, H.d_cellid, H.d_rank, H.d_count, H.d_flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan(Handle &H, cudaStream_t s)
+{
+    k_scan<<<1, 1024, 0, s>>>(H.g.ncell, H.d_count, H.d_start);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_sort_gather(Handle &H, const float *x, const float *q, const float *mu,
+                                       const float *theta, cudaStream_t s)
+{
+    int N = (int)H.N;
+    k_scatter<<<(N + 255) / 256, 256, 0, s>>>(N, H.d_cellid, H.d_rank, H.d_start, H.d_perm);
+    k_leafsort<<<(H.g.ncell + 127) / 128, 128, 0, s>>>(H.g.ncell, H.d_start, H.d_perm);
+    k_gather<<<(N + 255) / 256, 256, 0, s>>>(N, H.d_perm, x, q, H.max_order >= 1 ? mu : nullptr,
+                                              H.max_order >= 2 ? theta : nullptr, H.g, H.d_scell,
+                                              H.d_A0, H.d_A1, H.d_A2, H.d_A3);
+    return cudaGetLastError();
+}
+
+}  // namespace ankh

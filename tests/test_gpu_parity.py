@@ -1,0 +1,242 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Bars (FP32 arithmetic on the GPU; derived from FP32 rounding, ~6e-8 per
+operation accumulated over a few hundred terms per atom and the FP32 FFT):
+  * binning / sort: bit-exact permutation and leaf offsets;
+  * modified charges M: max error <= 2e-6 of max |M|;
+  * energy vs the literal FP64 ANKH-FFT at the same (n, L_u, L_c, xi):
+    relative error <= 2e-6;
+  * gradient vs the oracle's analytic adjoint: RMS error <= 3e-5 of the RMS
+    value, per group (dE/dx, dE/dq, dE/dmu, dE/dTheta);
+  * vs the FP64 Ewald energy of the workload: relative error <= 1e-5
+    (the target of the method), RMS force error <= 1e-4 of the RMS force.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+from oracle import ankh_ref as ar          # noqa: E402
+from oracle import ewald as ew             # noqa: E402
+from paper_2212_08284_gb300 import synth   # noqa: E402
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def api(gpu):
+    from paper_2212_08284_gb300 import api as A, build
+    build.build()
+    A.load_library()
+    return A
+
+
+def to_dev(b):
+    import torch
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+    return t(b.x), t(b.q), t(b.mu), t(b.theta)
+
+
+def run_gpu(api, b, n, Lu, Lc=0, xi=0.01, max_order=2, mixed=False, include_rec=True, forces=True):
+    m = api.Ankh(b.box, b.n, xi=xi, n_cells=n, Lu=Lu, Lc=Lc, max_order=max_order, mixed=mixed,
+                 include_rec=include_rec)
+    x, q, mu, th = to_dev(b)
+    if forces:
+        E, g = m.energy_forces(x, q, mu, th, torques=True)
+        g = {k: v.cpu().numpy().astype(np.float64) for k, v in g.items()}
+    else:
+        E, g = m.energy(x, q, mu, th), None
+    return m, E, g
+
+
+def grad13(g):
+    return np.concatenate([g["dEdx"], g["dEdq"][:, None], g["dEdmu"], g["dEdtheta"]], axis=1)
+
+
+def rms_rel(a, b):
+    return float(np.sqrt(np.mean((a - b) ** 2)) / max(np.sqrt(np.mean(b ** 2)), 1e-300))
+
+
+GROUPS = {"dEdx": slice(0, 3), "dEdq": slice(3, 4), "dEdmu": slice(4, 7), "dEdtheta": slice(7, 13)}
+
+
+def test_binning_is_bit_exact(api):
+    import torch
+    b = synth.config_box(1)
+    # adversarial coordinates: exactly on leaf faces, on the box faces, outside the box
+    x = b.x.copy()
+    h = b.box / 5
+    x[0] = [-b.box / 2, -b.box / 2 + h, 0.0]
+    x[1] = [b.box / 2, 2 * h - b.box / 2, -1e-7]
+    x[2] = [np.nextafter(np.float32(b.box / 2), 0), 3.5 * b.box, -2.25 * b.box]
+    x[3] = [h * 1.0000001 - b.box / 2, -h, h]
+    b.x = x.astype(np.float32)
+    m, _, _ = run_gpu(api, b, n=5, Lu=5, max_order=0, forces=False)
+    perm = api.ankh_debug_copy(m.h, api.BUF_PERM).cpu().numpy()
+    start = api.ankh_debug_copy(m.h, api.BUF_START).cpu().numpy()
+    cell, cvec, xw, operm = ar.bin_atoms(b.x, b.box, 5)
+    ostart = np.concatenate([[0], np.cumsum(np.bincount(cell, minlength=125))])
+    assert np.array_equal(perm, operm)
+    assert np.array_equal(start, ostart)
+    scell = api.ankh_debug_copy(m.h, api.BUF_SCELL).cpu().numpy()
+    assert np.array_equal(scell, cell[operm])
+    del torch
+
+
+def test_modified_charges_match_alg2(api):
+    b = synth.small_box(1000, 31, box=31.1)
+    n, Lu, Lc = 7, 5, 6
+    m, _, _ = run_gpu(api, b, n=n, Lu=Lu, Lc=Lc, forces=False)
+    M = api.ankh_debug_copy(m.h, api.BUF_M).cpu().numpy().reshape(n ** 3, -1)[:, :Lu ** 3]
+    o = ar.ankh_energy(b.x, b.q, b.mu, b.theta, ar.Params(b.box, n, Lu, Lc), grad=False)
+    Mo = o["M"].reshape(n ** 3, -1)
+    assert np.max(np.abs(M - Mo)) <= 2e-6 * np.max(np.abs(Mo))
+    # merged grid: every fine point is the sum of its (up to 8) leaf nodes
+    rho = api.ankh_debug_copy(m.h, api.BUF_RHO).cpu().numpy()
+    assert abs(rho.sum() - Mo.sum()) <= 1e-5 * np.abs(Mo).sum()
+    assert rho.sum() == pytest.approx(float(np.sum(b.q.astype(np.float64))), abs=1e-3)
+
+
+CASES = [
+    # (name, box factory, n, Lu, Lc, max_order)
+    ("water648_q_n5_Lu5", lambda: synth.config_box(1), 5, 5, 5, 0),
+    ("water648_q_n4_Lu6", lambda: synth.config_box(1), 4, 6, 6, 0),
+    ("water3000_n7_Lu5", lambda: synth.small_box(1000, 31, box=31.1), 7, 5, 5, 2),
+    ("water3000_n8_Lu4", lambda: synth.small_box(1000, 32, box=31.1), 8, 4, 6, 2),
+    ("water1500_n3_Lu3", lambda: synth.small_box(500, 33, box=24.7), 3, 3, 3, 2),
+    ("water24000_n14_Lu5", lambda: synth.config_box(2), 14, 5, 5, 2),
+]
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_energy_and_gradient_match_fp64_ankh(api, case, mixed):
+    name, mk, n, Lu, Lc, order = case
+    b = mk()
+    if order == 0:
+        b.mu[:] = 0
+        b.theta[:] = 0
+    m, E, g = run_gpu(api, b, n=n, Lu=Lu, Lc=Lc, max_order=order, mixed=mixed)
+    o = ar.ankh_energy(b.x, b.q, b.mu, b.theta, ar.Params(b.box, n, Lu, Lc))
+    assert E == pytest.approx(o["E"], rel=2e-6)
+    t = m.terms()
+    assert t["near"] == pytest.approx(o["E_near"], rel=2e-6)
+    far_gpu = t["far"] + t["far_k0"] + t["correction"]
+    assert far_gpu == pytest.approx(o["E_far"] + o["E_neut"], rel=1e-5, abs=2e-6 * abs(o["E"]))
+    G = grad13(g)
+    for k, sl in GROUPS.items():
+        if order == 0 and k in ("dEdmu", "dEdtheta"):
+            continue
+        assert rms_rel(G[:, sl], o["grad"][:, sl]) < 3e-5, k
+    tau = ar.torques(ew.pack_multipoles(b.q, b.mu, b.theta), o["grad"])
+    if order > 0:
+        assert rms_rel(g["torque"], tau) < 3e-5
+
+
+def golden(name):
+    p = os.path.join(HERE, "golden", f"ewald_{name}.json")
+    if not os.path.exists(p):
+        pytest.skip(f"golden file {p} missing")
+    return json.load(open(p))
+
+
+@pytest.mark.parametrize("cfg", [1, 2, 3])
+def test_against_fp64_ewald(api, cfg):
+    """The method's target: <= 1e-5 relative energy error and <= 1e-4 relative
+    RMS force error against the FP64 Ewald oracle, with default parameters."""
+    b = synth.config_box(cfg)
+    gd = golden(b.name)
+    m, E, g = run_gpu(api, b, n=0, Lu=5 if cfg > 1 else 6, max_order=0 if cfg == 1 else 2, mixed=True)
+    assert abs(E - gd["E"]) / abs(gd["E"]) <= 1e-5
+    idx = np.array(gd["sample_idx"])
+    ref = np.array(gd["sample_grad"])
+    G = grad13(g)[idx]
+    err = np.sqrt(np.mean((G[:, 0:3] - ref[:, 0:3]) ** 2)) / gd["rms_all"]["dEdx"]
+    if cfg > 1:
+        assert err <= 1e-4
+
+
+def test_single_atom_and_empty_leaves(api):
+    import torch
+    box = 14.0
+    b = synth.Box(x=np.array([[1.3, -2.2, 0.7]], np.float32), q=np.array([0.7], np.float32),
+                  mu=np.array([[0.1, -0.2, 0.3]], np.float32),
+                  theta=np.array([[0.2, 0.1, -0.05, -0.3, 0.04, 0.1]], np.float32), box=box)
+    m, E, g = run_gpu(api, b, n=4, Lu=5)
+    o = ar.ankh_energy(b.x, b.q, b.mu, b.theta, ar.Params(box, 4, 5, 5))
+    assert E == pytest.approx(o["E"], rel=2e-6)
+    del torch
+
+
+def test_zero_multipoles_give_zero(api):
+    b = synth.small_box(300, 5, box=20.0)
+    b.q[:] = 0
+    b.mu[:] = 0
+    b.theta[:] = 0
+    _, E, g = run_gpu(api, b, n=5, Lu=5)
+    assert E == 0.0
+    assert np.all(g["dEdx"] == 0)
+
+
+def test_wrapping_and_determinism(api):
+    import torch
+    # positions on a 2^-10 A lattice and a box of 32 A: x + k L is exact in FP32
+    b = synth.small_box(1000, 41, box=32.0)
+    b.x = (np.round(b.x.astype(np.float64) * 1024.0) / 1024.0).astype(np.float32)
+    b.x = np.where(b.x >= 16.0, b.x - 32.0, b.x).astype(np.float32)
+    m, E1, g1 = run_gpu(api, b, n=7, Lu=5)
+    x, q, mu, th = to_dev(b)
+    E2, g2 = m.energy_forces(x, q, mu, th, torques=True)
+    assert E2 == E1
+    for k in g1:
+        assert np.array_equal(g2[k].cpu().numpy().astype(np.float64), g1[k])
+    # shifting atoms by whole box vectors only moves them to another image
+    shift = np.random.default_rng(0).integers(-2, 3, size=b.x.shape).astype(np.float32) * np.float32(32.0)
+    xs_np = (b.x + shift).astype(np.float32)
+    assert np.array_equal(xs_np.astype(np.float64) - shift.astype(np.float64), b.x.astype(np.float64))
+    E3 = m.energy(torch.from_numpy(xs_np).cuda(), q, mu, th)
+    assert E3 == pytest.approx(E1, rel=1e-9)
+
+
+def test_nonfinite_input_reports_enumeric(api):
+    import torch
+    b = synth.small_box(100, 3, box=14.0)
+    m = api.Ankh(b.box, b.n, n_cells=3)
+    x, q, mu, th = to_dev(b)
+    x[5, 1] = float("nan")
+    with pytest.raises(api.AnkhError) as e:
+        m.energy(x, q, mu, th)
+    assert e.value.code == api.ANKH_ENUMERIC
+    del torch
+
+
+def test_host_entry_point_matches_device(api):
+    b = synth.small_box(600, 8, box=26.0)
+    m, E, g = run_gpu(api, b, n=6, Lu=5)
+    outs = {k: np.zeros(v.shape, np.float32) for k, v in g.items()}
+    Eh = api.ankh_energy_forces_host(m.h, b.x, b.q, b.mu, b.theta, outs["dEdx"], outs["dEdq"], outs["dEdmu"],
+                                     outs["dEdtheta"], outs["torque"])
+    assert Eh == E
+    for k in g:
+        assert np.array_equal(outs[k].astype(np.float64), g[k])
+
+
+def test_autograd_backward_is_the_adjoint(api):
+    import torch
+    b = synth.small_box(400, 9, box=23.0)
+    m = api.Ankh(b.box, b.n, n_cells=5, Lu=5)
+    x, q, mu, th = to_dev(b)
+    for t in (x, q, mu, th):
+        t.requires_grad_(True)
+    E = api.ankh_energy_autograd(m, x, q, mu, th)
+    (3.0 * E).backward()
+    E2, g = m.energy_forces(x.detach(), q.detach(), mu.detach(), th.detach())
+    assert float(E) == E2
+    assert torch.allclose(x.grad, 3.0 * g["dEdx"])
+    assert torch.allclose(q.grad, 3.0 * g["dEdq"])
+    assert torch.allclose(mu.grad, 3.0 * g["dEdmu"])
+    assert torch.allclose(th.grad, 3.0 * g["dEdtheta"])
