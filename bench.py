@@ -1,0 +1,354 @@
+"""Benchmark: ANKH energy + forces evaluations per second on a synthetic
+1,008,000-atom water box with charges, dipoles and quadrupoles.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload water_1008000|water_96000|water_24000] [--plain]
+
+One "step" is one full evaluation (bin/sort, P2M, merged-grid FFT far field,
+adjacent-leaf correction, near field, L2P, gradient assembly, FP64 energy)
+on inputs already resident in HBM; L2 is flushed (256 MiB write) between
+timed steps and the step is timed with CUDA events on the launch stream.
+Under torchrun each rank evaluates its own independent box (replicas; no
+data-path collective), and the value is the whole-job rate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {"water_1008000": 4, "water_96000": 3, "water_24000": 2}
+METRIC = "energy+force evals/s and Matoms/s at <=1e-5 rel. energy error vs FP64 Ewald"
+UNIT = "evals/s"
+# FP32 operations per UNORDERED near-field pair of the energy + gradient + field
+# evaluation in the mutual formulation of the pair formula (counted from the
+# code: ~190 for the energy, ~120 for the shared force, ~2 x 130 for the
+# potential / field / field gradient of both atoms; FMA = 2).
+NEAR_FLOPS_PER_PAIR = 560
+FP32_LANES_PER_SM = 128
+N_SM = 152
+
+
+def env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p)), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+def unordered_near_pairs(start: np.ndarray, n: int) -> int:
+    cnt = np.diff(start.astype(np.int64)).reshape(n, n, n)
+    tot = 0
+    for dx in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dz in (-1, 0, 1):
+                tot += int(np.sum(cnt * np.roll(cnt, (-dx, -dy, -dz), axis=(0, 1, 2))))
+    return (tot - int(cnt.sum())) // 2
+
+
+def oracle_sample(box, seconds_hint: float = 12.0, nthreads: int | None = None, rows: int = 1000,
+                  kstride: int = 400):
+    """Time the FP64 Ewald oracle on a bounded sample of the workload and
+    extrapolate to one full energy + gradient evaluation."""
+    from oracle import ewald as ew
+    x = box.x.astype(np.float64)
+    mp = ew.pack_multipoles(box.q, box.mu, box.theta)
+    alpha, rc, kc = ew.ewald_params(box.box, box.n, tol=1e-11)
+    rng = np.random.default_rng(7)
+    tgt = np.sort(rng.choice(box.n, size=min(rows, box.n), replace=False))
+    t0 = time.perf_counter()
+    ew.ewald_real_rows(x, mp, box.box, alpha, rc, tgt, grad=True, nthreads=nthreads)
+    t1 = time.perf_counter()
+    ew.ewald_rec_only(x, mp, box.box, alpha, kc, grad=True, kstride=kstride, nthreads=nthreads)
+    t2 = time.perf_counter()
+    full = (t1 - t0) * box.n / len(tgt) + (t2 - t1) * kstride
+    return {"seconds_full_eval": full, "sample": (f"FP64 Ewald (alpha={alpha:.4f}, rc={rc:.1f} A, tol 1e-11): "
+                                                 f"real-space rows of {len(tgt)} of {box.n} atoms + every "
+                                                 f"{kstride}-th reciprocal k-vector, energy + gradient, "
+                                                 f"extrapolated to one full evaluation"),
+            "sample_seconds": t2 - t0}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the CPU oracle as it stands, on the host cores."""
+    from paper_2212_08284_gb300 import synth
+    if rank != 0:
+        return
+    cfg = WORKLOADS[args.workload]
+    box = synth.config_box(cfg)
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle_sample(box, rows=200, kstride=2000)
+    times, samples = [], []
+    for _ in range(args.steps):
+        r = oracle_sample(box, rows=200, kstride=2000)
+        times.append(r["seconds_full_eval"])
+        samples.append(r["sample_seconds"])
+    per_eval = statistics.median(times)
+    value = 1.0 / per_eval
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_eval * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": box.name + "_energy_forces", "n_atoms": box.n,
+                                             "box_A": box.box},
+            "matoms_per_s": value * box.n / 1e6,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="water_1008000", choices=sorted(WORKLOADS))
+    ap.add_argument("--plain", action="store_true", help="plain FP32 adjacent-leaf correction")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    args = ap.parse_args()
+
+    rank, world, local = env_int("RANK", 0), env_int("WORLD_SIZE", 1), env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    from paper_2212_08284_gb300 import api, build, synth
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if rank == 0 or world == 1:
+        build.build()
+    if dist:
+        dist.barrier()
+    api.load_library()
+
+    cfg = WORKLOADS[args.workload]
+    box = synth.config_box(cfg) if rank == 0 else synth.water_box(
+        synth.CONFIGS[cfg]["n_waters"], synth.SEED_BASE + cfg + 1000 * rank, multipoles=True,
+        name=synth.CONFIGS[cfg]["name"])
+    N = box.n
+    t_pre0 = time.perf_counter()
+    model = api.Ankh(box.box, N, Lu=5, Lc=5, mixed=not args.plain)
+    t_pre = time.perf_counter() - t_pre0
+    info = model.info
+    f32 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
+    x, q, mu, th = f32(box.x), f32(box.q), f32(box.mu), f32(box.theta)
+    out = {"dEdx": torch.empty((N, 3), device=dev), "dEdq": torch.empty(N, device=dev),
+           "dEdmu": torch.empty((N, 3), device=dev), "dEdtheta": torch.empty((N, 6), device=dev),
+           "torque": torch.empty((N, 3), device=dev)}
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
+    stream = torch.cuda.current_stream()
+
+    def step():
+        api.ankh_energy_forces(model.h, x, q, mu, th, sync=False, stream=stream, **out)
+
+    api.ankh_set_timing(model.h, True)
+    for _ in range(max(args.warmup, 3)):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize()
+    E = api.ankh_energy_forces(model.h, x, q, mu, th, stream=stream, **out)
+
+    clocks = ClockSampler(dev.index)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stage_sum = {k: 0.0 for k in api.STAGES}
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev0[k].record(stream)
+        step()
+        ev1[k].record(stream)
+        st = api.ankh_stage_times(model.h)     # waits for this step's events
+        for s_, v in st.items():
+            stage_sum[s_] += v
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    t_dev = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1)) / 1e3   # seconds, device time
+    t_max = t_dev
+    if dist:
+        tt = torch.tensor([t_dev], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = world * args.steps / t_max
+    ms_step = t_max / args.steps * 1e3
+    stage_ms = {k: v / args.steps for k, v in stage_sum.items()}
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).pin_memory()
+    hx, hq, hmu, hth = pin(box.x), pin(box.q), pin(box.mu), pin(box.theta)
+    ho = {k: torch.empty(tuple(v.shape), dtype=torch.float32).pin_memory() for k, v in out.items()}
+    api.ankh_set_timing(model.h, False)
+    api.ankh_energy_forces_host(model.h, hx, hq, hmu, hth, stream=stream, **ho)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        api.ankh_energy_forces_host(model.h, hx, hq, hmu, hth, stream=stream, **ho)
+    t_e2e = time.perf_counter() - t0
+    if dist:
+        tt = torch.tensor([t_e2e], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_e2e = float(tt.item())
+    h2d = 4 * N * (3 + 1 + 3 + 6)
+    d2h = 4 * N * (3 + 1 + 3 + 6 + 3) + 8
+
+    # accuracy against the FP64 Ewald reference of this workload (rank 0 box)
+    acc = None
+    gpath = os.path.join(ROOT, "tests", "golden", f"ewald_{box.name}.json")
+    if rank == 0 and os.path.exists(gpath):
+        gd = json.load(open(gpath))
+        idx = np.array(gd["sample_idx"])
+        ref = np.array(gd["sample_grad"])
+        gx = out["dEdx"].cpu().numpy().astype(np.float64)[idx]
+        acc = {"rel_energy_error": abs(E - gd["E"]) / abs(gd["E"]),
+               "rel_rms_force_error_sample": float(np.sqrt(np.mean((gx - ref[:, :3]) ** 2))
+                                                   / gd["rms_all"]["dEdx"]),
+               "reference": "FP64 Ewald oracle (tests/golden)"}
+
+    # roofline of the dominant kernel
+    peaks, peak_kind = measured_peaks()
+    start = api.ankh_debug_copy(model.h, api.BUF_START).cpu().numpy()
+    n = info["n_cells"]
+    pairs = unordered_near_pairs(start, n)
+    dom = max(stage_ms, key=stage_ms.get)
+    sm_mhz = clk["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12   # TF/s at the sampled clock
+    P = info["Lu"] ** 3
+    ncell = n ** 3
+    models = {
+        "near": ("alu", pairs * NEAR_FLOPS_PER_PAIR / 1e12, fp32_peak, "TFLOP/s"),
+        "corr": ("tensor" if not args.plain else "alu", 2 * 27 * P * P * ncell / 1e12,
+                 (peaks["bf16_tflops"] / 2.0) if not args.plain else fp32_peak, "TFLOP/s"),
+        "p2m": ("hbm", (52 * N + 4 * ncell * P) / 1e9, peaks["hbm_gbs"], "GB/s"),
+        "l2p": ("hbm", (52 * N + 8 * ncell * P + 52 * N) / 1e9, peaks["hbm_gbs"], "GB/s"),
+    }
+    roof = None
+    if dom in models:
+        bound, work, peak, unit = models[dom]
+        achieved = work / (stage_ms[dom] / 1e3)
+        roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": (f"FP32: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz "
+                                f"(sampled clock)" if bound == "alu" else f"{peak_kind} MEASURED_PEAKS")}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r = oracle_sample(box)
+        cpu = {"value": 1.0 / r["seconds_full_eval"], "unit": UNIT, "cores": os.cpu_count() or 1,
+               "kind": "oracle", "sample": r["sample"]}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": box.name + "_energy_forces", "n_atoms": N, "box_A": round(box.box, 4),
+                       "n_cells": n, "Lu": info["Lu"], "Lc": info["Lc"], "nf": info["nf"], "xi": 0.01,
+                       "precision": "plain_fp32" if args.plain else "mixed_3xtf32_correction",
+                       "l2": "flushed: 256 MiB write between timed steps", "parallelism": f"replicas{world}"},
+            "matoms_per_s": value * N / 1e6,
+            "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+            "near_pairs_unordered": pairs,
+            "precompute_s": t_pre,
+            "accuracy": acc,
+            "clocks": clk,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * args.e2e_steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": 15 * args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    model.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -125,6 +125,17 @@ int ankh_get_info(const ankh_handle *h, ankh_info *info);
 int ankh_debug_copy(const ankh_handle *h, int which, void *dst, int64_t *bytes, void *cuda_stream);
 int ankh_ldm(const ankh_handle *h);
 
+/* Optional per-stage timing with CUDA events recorded on the call's stream
+ * (off by default).  Stages: 0 bin+sort, 1 self term, 2 P2M, 3 merge onto
+ * the equispaced grid, 4 forward FFT, 5 spectral product, 6 adjacent-leaf
+ * correction, 7 near field, 8 inverse FFT, 9 L2P, 10 gradient assembly,
+ * 11 energy reduction.  ankh_stage_times waits for the last call's events
+ * and returns each stage's duration in milliseconds (0 for stages that did
+ * not run). */
+#define ANKH_NUM_STAGES 12
+int ankh_set_timing(ankh_handle *h, int enable);
+int ankh_stage_times(const ankh_handle *h, double ms[ANKH_NUM_STAGES]);
+
 /* Free everything the handle owns.  NULL is ignored. */
 void ankh_destroy(ankh_handle *h);
 

@@ -27,7 +27,10 @@ BUF_PERM, BUF_START, BUF_M, BUF_RHO, BUF_PSI, BUF_SCELL = range(6)
 
 EXPORTED = ["ankh_default_params", "ankh_create", "ankh_energy", "ankh_energy_forces",
             "ankh_energy_forces_host", "ankh_last_terms", "ankh_get_info", "ankh_debug_copy",
-            "ankh_ldm", "ankh_destroy", "ankh_last_error", "ankh_version"]
+            "ankh_ldm", "ankh_set_timing", "ankh_stage_times", "ankh_destroy", "ankh_last_error",
+            "ankh_version"]
+STAGES = ["sort", "self", "p2m", "merge", "fft_fwd", "spectral", "corr", "near", "fft_inv", "l2p",
+          "finalize", "reduce"]
 
 
 class AnkhError(RuntimeError):
@@ -82,6 +85,10 @@ def load_library(path: str = LIB_PATH):
         lib.ankh_debug_copy.restype = ctypes.c_int
         lib.ankh_ldm.argtypes = [vp]
         lib.ankh_ldm.restype = ctypes.c_int
+        lib.ankh_set_timing.argtypes = [vp, ctypes.c_int]
+        lib.ankh_set_timing.restype = ctypes.c_int
+        lib.ankh_stage_times.argtypes = [vp, dp]
+        lib.ankh_stage_times.restype = ctypes.c_int
         lib.ankh_destroy.argtypes = [vp]
         lib.ankh_destroy.restype = None
         lib.ankh_last_error.argtypes = []
@@ -187,6 +194,17 @@ def ankh_last_terms(h):
     _check(load_library().ankh_last_terms(h, t))
     keys = ["near", "far", "far_k0", "correction", "self", "total"]
     return dict(zip(keys, list(t)))
+
+
+def ankh_set_timing(h, enable: bool = True) -> None:
+    _check(load_library().ankh_set_timing(h, 1 if enable else 0))
+
+
+def ankh_stage_times(h) -> dict:
+    """Per-stage device milliseconds of the last call (timing must be on)."""
+    t = (ctypes.c_double * len(STAGES))()
+    _check(load_library().ankh_stage_times(h, t))
+    return dict(zip(STAGES, list(t)))
 
 
 def ankh_get_info(h) -> dict:

@@ -163,6 +163,9 @@ static void free_device(Handle *H)
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (H->h_terms) cudaFreeHost(H->h_terms);
+    if (H->have_events)
+        for (int k = 0; k <= kNumStages; ++k) cudaEventDestroy(H->ev[k]);
+    H->have_events = 0;
     if (H->have_plans) {
         cufftDestroy(H->plan_r2c);
         cufftDestroy(H->plan_c2r);
@@ -179,29 +182,51 @@ static cudaError_t dalloc(Handle *H, T **p, size_t count)
     return e;
 }
 
+static void mark(Handle &H, int stage_done, cudaStream_t s)
+{
+    if (!H.timing || !H.have_events || H.nrec > kNumStages) return;
+    cudaEventRecord(H.ev[H.nrec], s);
+    H.ev_stage[H.nrec] = stage_done;
+    H.nrec++;
+}
+
 static int run_sequence(Handle &H, const float *x, const float *q, const float *mu, const float *theta,
                         bool forces, float *dEdx, float *dEdq, float *dEdmu, float *dEdtheta, float *torque,
                         cudaStream_t s)
 {
+    H.nrec = 0;
+    mark(H, -1, s);
     ANKH_CU(launch_bin(H, x, s), "bin");
     ANKH_CU(launch_scan(H, s), "scan");
     ANKH_CU(launch_scatter_sort_gather(H, x, q, mu, theta, s), "sort");
+    mark(H, kStSort, s);
     ANKH_CU(launch_self_dc(H, s), "self");
+    mark(H, kStSelf, s);
     ANKH_CU(launch_p2m(H, s), "p2m");
+    mark(H, kStP2M, s);
     ANKH_CU(launch_fine_gather(H, s), "merge");
+    mark(H, kStMerge, s);
     if (cufftSetStream(H.plan_r2c, s) != CUFFT_SUCCESS) return fail(ANKH_ECUDA, "cufftSetStream");
     if (cufftExecR2C(H.plan_r2c, H.d_rho, H.d_rhohat) != CUFFT_SUCCESS) return fail(ANKH_ECUDA, "cufftExecR2C");
+    mark(H, kStFFTf, s);
     ANKH_CU(launch_spectral(H, forces, s), "spectral");
+    mark(H, kStSpectral, s);
     ANKH_CU(launch_corr(H, forces, s), "corr");
+    mark(H, kStCorr, s);
     ANKH_CU(launch_near(H, forces, s), "near");
+    mark(H, kStNear, s);
     if (forces) {
         if (cufftSetStream(H.plan_c2r, s) != CUFFT_SUCCESS) return fail(ANKH_ECUDA, "cufftSetStream");
         if (cufftExecC2R(H.plan_c2r, H.d_rhohat, H.d_phi) != CUFFT_SUCCESS)
             return fail(ANKH_ECUDA, "cufftExecC2R");
+        mark(H, kStFFTi, s);
         ANKH_CU(launch_l2p(H, s), "l2p");
+        mark(H, kStL2P, s);
         ANKH_CU(launch_finalize(H, dEdx, dEdq, dEdmu, dEdtheta, torque, s), "finalize");
+        mark(H, kStFinal, s);
     }
     ANKH_CU(launch_reduce(H, s), "reduce");
+    mark(H, kStReduce, s);
     return ANKH_OK;
 }
 
@@ -471,6 +496,35 @@ int ankh_get_info(const ankh_handle *h, ankh_info *info)
 }
 
 int ankh_ldm(const ankh_handle *h) { return h ? h->h.g.ldm : 0; }
+
+int ankh_set_timing(ankh_handle *h, int enable)
+{
+    if (!h) return fail(ANKH_EINVAL, "handle is NULL");
+    Handle &H = h->h;
+    if (enable && !H.have_events) {
+        for (int k = 0; k <= kNumStages; ++k) ANKH_CU(cudaEventCreate(&H.ev[k]), "cudaEventCreate");
+        H.have_events = 1;
+    }
+    H.timing = enable ? 1 : 0;
+    H.nrec = 0;
+    return ANKH_OK;
+}
+
+int ankh_stage_times(const ankh_handle *h, double ms[ANKH_NUM_STAGES])
+{
+    if (!h || !ms) return fail(ANKH_EINVAL, "NULL argument");
+    const Handle &H = h->h;
+    for (int k = 0; k < ANKH_NUM_STAGES; ++k) ms[k] = 0.0;
+    if (!H.timing || H.nrec < 2) return ANKH_OK;
+    ANKH_CU(cudaEventSynchronize(H.ev[H.nrec - 1]), "cudaEventSynchronize");
+    for (int k = 1; k < H.nrec; ++k) {
+        float t = 0.f;
+        ANKH_CU(cudaEventElapsedTime(&t, H.ev[k - 1], H.ev[k]), "cudaEventElapsedTime");
+        const int st = H.ev_stage[k];
+        if (st >= 0 && st < ANKH_NUM_STAGES) ms[st] += t;
+    }
+    return ANKH_OK;
+}
 
 int ankh_debug_copy(const ankh_handle *h, int which, void *dst, int64_t *bytes, void *cuda_stream)
 {

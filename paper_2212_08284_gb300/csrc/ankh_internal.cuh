@@ -29,6 +29,10 @@ struct Geo {
     float xi;
 };
 
+// Pipeline stages (for the optional per-stage timing)
+enum Stage { kStSort = 0, kStSelf, kStP2M, kStMerge, kStFFTf, kStSpectral, kStCorr, kStNear, kStFFTi,
+             kStL2P, kStFinal, kStReduce, kNumStages };
+
 // Energy partial slots (FP64 per block, reduced in a fixed order).
 enum PartSlot { kPartNear = 0, kPartGlob = 1, kPartCorr = 2, kPartSelf = 3, kPartQ = 4, kPartCount = 5 };
 
@@ -67,6 +71,12 @@ struct Handle {
     double last_terms[6];
     cufftHandle plan_r2c, plan_c2r;
     int have_plans;
+    // optional per-stage timing (events on the caller's stream)
+    int timing;
+    int have_events;
+    int nrec;
+    cudaEvent_t ev[kNumStages + 1];
+    int ev_stage[kNumStages + 1];
 };
 
 // error reporting (thread-local message)

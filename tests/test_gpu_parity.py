@@ -198,8 +198,10 @@ def test_wrapping_and_determinism(api):
     shift = np.random.default_rng(0).integers(-2, 3, size=b.x.shape).astype(np.float32) * np.float32(32.0)
     xs_np = (b.x + shift).astype(np.float32)
     assert np.array_equal(xs_np.astype(np.float64) - shift.astype(np.float64), b.x.astype(np.float64))
+    E1e = m.energy(x, q, mu, th)
     E3 = m.energy(torch.from_numpy(xs_np).cuda(), q, mu, th)
-    assert E3 == pytest.approx(E1, rel=1e-9)
+    assert E3 == E1e
+    assert E1e == pytest.approx(E1, rel=1e-7)
 
 
 def test_nonfinite_input_reports_enumeric(api):
