@@ -136,6 +136,32 @@ int ankh_ldm(const ankh_handle *h);
 int ankh_set_timing(ankh_handle *h, int enable);
 int ankh_stage_times(const ankh_handle *h, double ms[ANKH_NUM_STAGES]);
 
+/* Leaf binning and stable sort without any allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc (an engine that plans all device memory at start-up, code that
+ * runs while its stream is captured into a CUDA graph, a host whose device
+ * allocator belongs to another runtime).  It runs the same kernels as the
+ * sort stage of ankh_energy, with its scratch in a static device array of
+ * the library instead of allocated memory.
+ *   x: N x 3 device positions; n_cells leaves per axis of a cubic box of edge
+ *   box_edge; outputs (device, caller-owned): perm[N] = atom index of each
+ *   sorted slot (ordered by leaf, then by atom index), leaf_start[n^3 + 1] =
+ *   first slot of each leaf.
+ *   Limits: N <= ANKH_NOALLOC_MAX_ATOMS, n_cells^3 <= ANKH_NOALLOC_MAX_LEAVES;
+ *   larger sizes return ANKH_EINVAL with a message naming the limit.
+ *   The static array (9 MiB + 256 B) is held by every GPU that loads the
+ *   library until the process exits.  The first call on a device looks up
+ *   the array's device address (cudaGetSymbolAddress); make that first call
+ *   before any stream capture.  All calls share the one array, which keeps
+ *   the last call's contents: each call clears what must start at zero, but
+ *   calls that overlap on the GPU (other streams, other threads) race.
+ *   Non-finite coordinates are binned as 0 and not reported.  The call is
+ *   asynchronous on cuda_stream. */
+#define ANKH_NOALLOC_MAX_ATOMS 1048576
+#define ANKH_NOALLOC_MAX_LEAVES 262144
+int ankh_bin_sort_noalloc(const float *x, int64_t N, double box_edge, int n_cells, int32_t *perm,
+                          int32_t *leaf_start, void *cuda_stream);
+
 /* Free everything the handle owns.  NULL is ignored. */
 void ankh_destroy(ankh_handle *h);
 

@@ -27,8 +27,8 @@ BUF_PERM, BUF_START, BUF_M, BUF_RHO, BUF_PSI, BUF_SCELL = range(6)
 
 EXPORTED = ["ankh_default_params", "ankh_create", "ankh_energy", "ankh_energy_forces",
             "ankh_energy_forces_host", "ankh_last_terms", "ankh_get_info", "ankh_debug_copy",
-            "ankh_ldm", "ankh_set_timing", "ankh_stage_times", "ankh_destroy", "ankh_last_error",
-            "ankh_version"]
+            "ankh_ldm", "ankh_set_timing", "ankh_stage_times", "ankh_bin_sort_noalloc", "ankh_destroy",
+            "ankh_last_error", "ankh_version"]
 STAGES = ["sort", "self", "p2m", "merge", "fft_fwd", "spectral", "corr", "near", "fft_inv", "l2p",
           "finalize", "reduce"]
 
@@ -89,6 +89,8 @@ def load_library(path: str = LIB_PATH):
         lib.ankh_set_timing.restype = ctypes.c_int
         lib.ankh_stage_times.argtypes = [vp, dp]
         lib.ankh_stage_times.restype = ctypes.c_int
+        lib.ankh_bin_sort_noalloc.argtypes = [vp, ctypes.c_int64, ctypes.c_double, ctypes.c_int, vp, vp, vp]
+        lib.ankh_bin_sort_noalloc.restype = ctypes.c_int
         lib.ankh_destroy.argtypes = [vp]
         lib.ankh_destroy.restype = None
         lib.ankh_last_error.argtypes = []
@@ -205,6 +207,13 @@ def ankh_stage_times(h) -> dict:
     t = (ctypes.c_double * len(STAGES))()
     _check(load_library().ankh_stage_times(h, t))
     return dict(zip(STAGES, list(t)))
+
+
+def ankh_bin_sort_noalloc(x, box_edge: float, n_cells: int, perm, leaf_start, stream=None) -> None:
+    """Leaf binning + stable sort into caller tensors (int32 perm[N],
+    leaf_start[n^3+1]) using the library's static scratch (no allocation)."""
+    _check(load_library().ankh_bin_sort_noalloc(_ptr(x), int(x.shape[0]), float(box_edge), int(n_cells),
+                                                _ptr(perm), _ptr(leaf_start), _stream_ptr(stream)))
 
 
 def ankh_get_info(h) -> dict:

@@ -87,6 +87,8 @@ cudaError_t launch_bin(Handle &H, const float *x, cudaStream_t s);
 cudaError_t launch_scan(Handle &H, cudaStream_t s);
 cudaError_t launch_scatter_sort_gather(Handle &H, const float *x, const float *q, const float *mu,
                                        const float *theta, cudaStream_t s);
+cudaError_t launch_bin_sort_raw(int N, const float *x, const Geo &g, int *cellid, int *rank, int *count,
+                                int *flag, int *start, int *perm, cudaStream_t s);
 cudaError_t launch_p2m(Handle &H, cudaStream_t s);
 cudaError_t launch_fine_gather(Handle &H, cudaStream_t s);
 cudaError_t launch_spectral(Handle &H, bool forces, cudaStream_t s);

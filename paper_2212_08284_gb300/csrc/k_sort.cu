@@ -168,4 +168,20 @@ cudaError_t launch_scatter_sort_gather(Handle &H, const float *x, const float *q
     return cudaGetLastError();
 }
 
+// Same kernels on caller-provided buffers (used by the allocation-free entry
+// point): count and flag are cleared here; start receives ncell + 1 offsets.
+cudaError_t launch_bin_sort_raw(int N, const float *x, const Geo &g, int *cellid, int *rank, int *count,
+                                int *flag, int *start, int *perm, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * g.ncell, s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(flag, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    k_bin<<<(N + 255) / 256, 256, 0, s>>>(N, x, g, cellid, rank, count, flag);
+    k_scan<<<1, 1024, 0, s>>>(g.ncell, count, start);
+    k_scatter<<<(N + 255) / 256, 256, 0, s>>>(N, cellid, rank, start, perm);
+    k_leafsort<<<(g.ncell + 127) / 128, 128, 0, s>>>(g.ncell, start, perm);
+    return cudaGetLastError();
+}
+
 }  // namespace ankh
