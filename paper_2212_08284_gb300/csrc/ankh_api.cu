@@ -129,6 +129,21 @@ static std::vector<double> make_C(int Lu, int ldm, double delta, double xi)
     return C;
 }
 
+// Round an FP32 value to TF32 (10 explicit mantissa bits), nearest, ties away
+// from zero -- the rounding of cvt.rna.tf32.f32.
+static float tf32_round(float x)
+{
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    if ((u & 0x7f800000u) != 0x7f800000u) {
+        u += 0x1000u;
+        u &= 0xffffe000u;
+    }
+    float r;
+    std::memcpy(&r, &u, 4);
+    return r;
+}
+
 static bool good_fft_size(int m)
 {
     for (int p : {2, 3, 5, 7})
@@ -159,7 +174,7 @@ static void free_device(Handle *H)
     void *ptrs[] = {H->d_cellid, H->d_rank, H->d_count, H->d_start, H->d_perm, H->d_scell, H->d_flag,
                     H->d_A0, H->d_A1, H->d_A2, H->d_A3, H->d_W, H->d_M, H->d_rho, H->d_rhohat, H->d_D,
                     H->d_phi, H->d_C, H->d_Chi, H->d_Clo, H->d_psi, H->d_gfar, H->d_gnear, H->d_part,
-                    H->d_partoff, H->d_terms, H->d_hostbuf};
+                    H->d_partoff, H->d_terms, H->d_hostbuf, H->d_Mhi, H->d_Mlo};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (H->h_terms) cudaFreeHost(H->h_terms);
@@ -211,7 +226,10 @@ static int run_sequence(Handle &H, const float *x, const float *q, const float *
     mark(H, kStFFTf, s);
     ANKH_CU(launch_spectral(H, forces, s), "spectral");
     mark(H, kStSpectral, s);
-    ANKH_CU(launch_corr(H, forces, s), "corr");
+    if (H.tc.enabled && (H.flags & ANKH_MIXED))
+        ANKH_CU(launch_corr_tc(H, forces, s), "corr (tensor cores)");
+    else
+        ANKH_CU(launch_corr(H, forces, s), "corr");
     mark(H, kStCorr, s);
     ANKH_CU(launch_near(H, forces, s), "near");
     mark(H, kStNear, s);
@@ -232,10 +250,12 @@ static int run_sequence(Handle &H, const float *x, const float *q, const float *
 
 static int fetch_terms(Handle &H, double *E_host, cudaStream_t s)
 {
-    ANKH_CU(cudaMemcpyAsync(H.h_terms, H.d_terms, 8 * sizeof(double), cudaMemcpyDeviceToHost, s), "copy E");
+    ANKH_CU(cudaMemcpyAsync(H.h_terms, H.d_terms, 9 * sizeof(double), cudaMemcpyDeviceToHost, s), "copy E");
     ANKH_CU(cudaStreamSynchronize(s), "synchronize");
     for (int k = 0; k < 6; ++k) H.last_terms[k] = H.h_terms[k];
-    if (std::isnan(H.h_terms[5])) return fail(ANKH_ENUMERIC, "non-finite input coordinate");
+    const int flag = (int)H.h_terms[8];
+    if (flag & 2) return fail(ANKH_ETIMEOUT, "a bounded wait of the tensor-core correction ran out");
+    if (flag & 1) return fail(ANKH_ENUMERIC, "non-finite input coordinate");
     if (E_host) *E_host = H.h_terms[5];
     return ANKH_OK;
 }
@@ -348,20 +368,24 @@ int ankh_create(double box_edge, int64_t N, const ankh_params *params, ankh_hand
     int nb[kPartCount];
     nb[kPartNear] = near_blocks(H);
     nb[kPartGlob] = spectral_blocks(H);
-    nb[kPartCorr] = corr_blocks(H);
+    {
+        // tensor-core tiles: ceil(n^2 / R) with R z-rows of S = roundup16(n) leaves
+        const int S = ((n + 15) / 16) * 16, R = std::max(1, 128 / S);
+        nb[kPartCorr] = std::max(corr_blocks(H), (n * n + R - 1) / R);
+    }
     nb[kPartSelf] = self_blocks(H);
     nb[kPartQ] = self_blocks(H);
     H.part_off[0] = 0;
     for (int k = 0; k < kPartCount; ++k) H.part_off[k + 1] = H.part_off[k] + nb[k];
     ANKH_AL(H.d_part, H.part_off[kPartCount]);
     ANKH_AL(H.d_partoff, kPartCount + 1);
-    ANKH_AL(H.d_terms, 8);
-    if (cudaMallocHost(&H.h_terms, 8 * sizeof(double)) != cudaSuccess)
+    ANKH_AL(H.d_terms, 9);
+    if (cudaMallocHost(&H.h_terms, 9 * sizeof(double)) != cudaSuccess)
         return bail(ANKH_ENOMEM, "cudaMallocHost");
     if (cudaMemcpy(H.d_partoff, H.part_off, sizeof(int) * (kPartCount + 1), cudaMemcpyHostToDevice) != cudaSuccess)
         return bail(ANKH_ECUDA, "upload part offsets");
     cudaMemset(H.d_part, 0, sizeof(double) * H.part_off[kPartCount]);
-    cudaMemset(H.d_terms, 0, 8 * sizeof(double));
+    cudaMemset(H.d_terms, 0, 9 * sizeof(double));
     cudaMemset(H.d_psi, 0, sizeof(float) * (size_t)g.ncell * g.ldm);
 
     // tables
@@ -374,6 +398,32 @@ int ankh_create(double box_edge, int64_t N, const ankh_params *params, ankh_hand
         std::vector<float> Cf(C.begin(), C.end());
         if (cudaMemcpy(H.d_C, Cf.data(), Cf.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
             return bail(ANKH_ECUDA, "upload C");
+    }
+    if ((p.flags & ANKH_MIXED) && g.ldm == 128 && n <= 128) {
+        const int S = ((n + 15) / 16) * 16;
+        const int64_t rows = (int64_t)n * n * (S + 2);
+        ANKH_AL(H.d_Mhi, rows * 128);
+        ANKH_AL(H.d_Mlo, rows * 128);
+        ANKH_AL(H.d_Chi, (int64_t)27 * 128 * 128);
+        ANKH_AL(H.d_Clo, (int64_t)27 * 128 * 128);
+        cudaMemset(H.d_Mhi, 0, sizeof(float) * rows * 128);
+        cudaMemset(H.d_Mlo, 0, sizeof(float) * rows * 128);
+        // A = [C_0 | ... | C_26] as [128 rows][27*128], split hi/lo (round to nearest TF32)
+        std::vector<double> C = make_C(g.Lu, g.ldm, g.h / (g.Lu - 1), p.xi);
+        std::vector<float> Ah((size_t)128 * 27 * 128), Al((size_t)128 * 27 * 128);
+        for (int d = 0; d < 27; ++d)
+            for (int m = 0; m < 128; ++m)
+                for (int l = 0; l < 128; ++l) {
+                    const float v = (float)C[((size_t)d * 128 + m) * 128 + l];
+                    const float hi = tf32_round(v);
+                    Ah[(size_t)m * 27 * 128 + d * 128 + l] = hi;
+                    Al[(size_t)m * 27 * 128 + d * 128 + l] = tf32_round(v - hi);
+                }
+        if (cudaMemcpy(H.d_Chi, Ah.data(), Ah.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(H.d_Clo, Al.data(), Al.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(ANKH_ECUDA, "upload tensor-core blocks");
+        std::string terr;
+        if (!tc_prepare(H, terr)) return bail(ANKH_ECUDA, terr);
     }
     std::string perr;
     if (precompute_kernel_spectrum(H, &H.D0, perr) != cudaSuccess) return bail(ANKH_ECUDA, perr);

@@ -1,6 +1,7 @@
 // Internal declarations of libankh (not part of the ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cufft.h>
 #include <cstdint>
@@ -36,8 +37,18 @@ enum Stage { kStSort = 0, kStSelf, kStP2M, kStMerge, kStFFTf, kStSpectral, kStCo
 // Energy partial slots (FP64 per block, reduced in a fixed order).
 enum PartSlot { kPartNear = 0, kPartGlob = 1, kPartCorr = 2, kPartSelf = 3, kPartQ = 4, kPartCount = 5 };
 
+// Tensor-core correction (k_corr_tc.cu): tile geometry and TMA descriptors.
+struct TcPlan {
+    int enabled;
+    int S, R, rowstride, N, tiles;
+    uint32_t tmem_cols;
+    CUtensorMap mAhi, mAlo, mBhi, mBlo;
+};
+
 struct Handle {
     Geo g;
+    TcPlan tc;
+    float *d_Mhi, *d_Mlo;   // [n*n*rowstride][128] TF32 split of M, z-halo padded (tensor-core path)
     int64_t N;
     int max_order;
     unsigned flags;
@@ -102,6 +113,10 @@ cudaError_t launch_reduce(Handle &H, cudaStream_t s);
 
 // precomputation on the device (FP64)
 cudaError_t precompute_kernel_spectrum(Handle &H, double *D0_out, std::string &err);
+
+bool tc_prepare(Handle &H, std::string &err);
+int corr_tc_blocks(const Handle &H);
+cudaError_t launch_corr_tc(Handle &H, bool forces, cudaStream_t s);
 
 int near_blocks(const Handle &H);
 int spectral_blocks(const Handle &H);

@@ -177,6 +177,7 @@ __global__ void k_reduce(const double *__restrict__ part, const int *__restrict_
         terms[3] = corr;
         terms[4] = self;
         terms[5] = near + glob + dc + corr + self;
+        terms[8] = (double)(*flag);
         if (*flag) terms[5] = __longlong_as_double(0x7ff8000000000000LL);
     }
 }

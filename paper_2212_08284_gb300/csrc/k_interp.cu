@@ -42,11 +42,19 @@ __device__ __forceinline__ void basis_1d(float xh, const float *__restrict__ W, 
     }
 }
 
+__device__ __forceinline__ float tf32_rna(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
 template <int LU>
 __global__ void __launch_bounds__(((LU * LU * LU + 31) / 32) * 32)
 k_p2m(Geo g, const int *__restrict__ start, const float4 *__restrict__ A0,
       const float4 *__restrict__ A1, const float4 *__restrict__ A2, const float4 *__restrict__ A3,
-      const float *__restrict__ W, float *__restrict__ M)
+      const float *__restrict__ W, float *__restrict__ M, float *__restrict__ Mhi, float *__restrict__ Mlo,
+      int rowstride)
 {
     constexpr int P = LU * LU * LU;
     constexpr int CH = 32;
@@ -94,7 +102,27 @@ k_p2m(Geo g, const int *__restrict__ start, const float4 *__restrict__ A0,
             }
         }
     }
-    if (node < g.ldm) M[(int64_t)cell * g.ldm + node] = node < P ? acc : 0.f;
+    if (node < g.ldm) {
+        const float v = node < P ? acc : 0.f;
+        M[(int64_t)cell * g.ldm + node] = v;
+        if (Mhi) {
+            // split for the tensor-core correction: rows of each z-row with a one-leaf halo
+            const float hi = tf32_rna(v), lo = tf32_rna(v - hi);
+            const int n = g.n;
+            const int cz = cell % n, zr = cell / n;
+            const int64_t base = (int64_t)zr * rowstride;
+            Mhi[(base + 1 + cz) * g.ldm + node] = hi;
+            Mlo[(base + 1 + cz) * g.ldm + node] = lo;
+            if (cz == n - 1) {
+                Mhi[base * g.ldm + node] = hi;
+                Mlo[base * g.ldm + node] = lo;
+            }
+            if (cz == 0) {
+                Mhi[(base + n + 1) * g.ldm + node] = hi;
+                Mlo[(base + n + 1) * g.ldm + node] = lo;
+            }
+        }
+    }
 }
 
 // Merged periodic grid: rho[g] = sum of M over the (up to 8) leaf nodes at g.
@@ -229,7 +257,8 @@ cudaError_t launch_p2m(Handle &H, cudaStream_t s)
 {
     ANKH_LU_SWITCH(H.g.Lu,
         k_p2m<LU><<<H.g.ncell, ((LU * LU * LU + 31) / 32) * 32, 0, s>>>(
-            H.g, H.d_start, H.d_A0, H.d_A1, H.d_A2, H.d_A3, H.d_W, H.d_M));
+            H.g, H.d_start, H.d_A0, H.d_A1, H.d_A2, H.d_A3, H.d_W, H.d_M,
+            H.tc.enabled ? H.d_Mhi : nullptr, H.tc.enabled ? H.d_Mlo : nullptr, H.tc.rowstride));
     return cudaGetLastError();
 }
 
