@@ -1,205 +1,284 @@
 // Near field of ANKH (Alg. 5 step 3; Sec. 3.2 N_real): every pair of atoms in
 // the same or in adjacent leaves (26 neighbours, periodic, one image per
 // offset), kernel H = erfc(xi r)/r, with the full multipole operator
-//   e_ik = (q_i + mu_i.grad + Theta_i:grad grad)(q_k - mu_k.grad + Theta_k:grad grad) H(r),
-//   r = x_i - x_k.
-// N_real = 1/2 sum_i sum_k e_ik.  Each thread owns one target atom and visits
-// all 27 leaves (both orders of every pair are evaluated), so every output is
-// written by exactly one thread -- no atomics, deterministic results.
+//   e_ik = (q_i + mu_i.grad + Theta_i:grad grad) V_k(r),   r = x_i - x_k,
+//   V_k(r) = (q_k - mu_k.grad + Theta_k:grad grad) H(r),
+//   N_real = 1/2 sum_i sum_k e_ik.
 //
-// The derivatives of the radial kernel are taken through the screened
-// functions B_0 = H, B_l = -(1/r) dB_{l-1}/dr, computed upward:
-//   B_l = [(2l-1) B_{l-1} + (2 xi^2)^l exp(-xi^2 r^2)/(xi sqrt(pi))] / r^2.
-// In terms of s_i = mu_i.r, s_k = mu_k.r, t = tr Theta, u = r.Theta.r:
-//   e = sum_{l=0..4} c_l B_l with
-//   c0 = q_i q_k
-//   c1 = q_i (s_k - t_k) - q_k (s_i + t_i) + mu_i.mu_k
-//   c2 = q_i u_k + q_k u_i - (s_i + t_i)(s_k - t_k) + 2 mu_i.Theta_k r - 2 mu_k.Theta_i r
-//        + 2 Theta_i:Theta_k
-//   c3 = (s_k - t_k) u_i - (s_i + t_i) u_k - 4 (Theta_i r).(Theta_k r)
-//   c4 = u_i u_k
-// and grad e = sum_l (grad c_l) B_l - r sum_l c_l B_{l+1}; the potential,
-// field and field gradient of the source at the target give dE/dq_i,
-// dE/dmu_i and dE/dTheta_i.
+// Source-field formulation: each target i accumulates, over all its near
+// sources k, the potential V_k and its derivatives up to third order,
+//   V, dV_a, G_ab = d_a d_b V, T_abc = d_a d_b d_c V,
+// which depend on the source's multipoles only.  The target's multipoles
+// enter once per atom at the end:
+//   e_i = q_i V + mu_i.dV + Theta_i:G,       dE/dq_i = V, dE/dmu_i = dV,
+//   dE/dTheta_i = G (stored-entry convention),
+//   dE/dx_i = q_i dV + mu_i.G + Theta_i:T.
+// With B_0 = H, B_l = -(1/r) dB_{l-1}/dr (upward recurrence
+// B_l = [(2l-1) B_{l-1} + (2 xi^2)^l exp(-xi^2 r^2)/(xi sqrt(pi))]/r^2) and
+// s = mu_k.r - tr Theta_k, u = r.Theta_k.r, Q = Theta_k r:
+//   V    = q B0 + s B1 + u B2
+//   A    = -(q B1 + s B2 + u B3),  A2 = q B2 + s B3 + u B4,  A3 = q B3 + s B4 + u B5
+//   dV_a = mu_a B1 + 2 Q_a B2 + r_a A
+//   G_ab = delta_ab A + r_a r_b A2 - (r_a P_b + r_b P_a) + 2 Theta_ab B2,   P = mu B2 + 2 Q B3
+//   T_abc = sym3(delta_ab W_c) - r_a r_b r_c A3 + sym3(r_a r_b Z_c) - 2 B3 sym3(Theta_ab r_c),
+//           W = r A2 - mu B2 - 2 Q B3,  Z = mu B3 + 2 Q B4
+// (sym3 sums the three distinct placements of the index pair).
+//
+// Work layout: one warp per target leaf.  The atoms of the 27 leaves around
+// it are staged in shared memory (chunks of 64, coordinates shifted by the
+// leaf offset); the warp's lanes are split into G = 32 / n_t groups, lane
+// (i, g) accumulating target i over sources g, g + G, ...; the group partials
+// are summed in a fixed order.  Every output is written by exactly one lane:
+// no atomics, deterministic results.
 #include "ankh_internal.cuh"
 
 namespace ankh {
 
-struct MPf {
-    float q, dx, dy, dz, xx, xy, xz, yy, yz, zz, tr;
-};
-
-__device__ __forceinline__ MPf load_mp(const float4 a0, const float4 a1, const float4 a2, const float4 a3)
-{
-    MPf m;
-    m.q = a0.w;
-    m.dx = a1.x; m.dy = a1.y; m.dz = a1.z;
-    m.xx = a2.x; m.xy = a2.y; m.xz = a2.z; m.yy = a2.w; m.yz = a3.x; m.zz = a3.y;
-    m.tr = m.xx + m.yy + m.zz;
-    return m;
-}
-
 struct BCoef {
-    float xi, c1, c2, c3, c4, c5;  // c_l = (2 xi^2)^l / (xi sqrt(pi))
+    float xi, xi2;
+    float c1, c2, c3, c4, c5;   // (2 xi^2)^l / (xi sqrt(pi))
+    float e[8];                 // Maclaurin coefficients of erf(x)/x in x^2
+    int series;                 // use the series (xi * r_max <= 0.5)
 };
+
+constexpr int kNearWarps = 4;
+constexpr int kNearChunk = 64;
 
 template <bool FORCES>
-__device__ __forceinline__ void near_pair(float rx, float ry, float rz, const MPf &I, const MPf &K,
-                                          const BCoef &bc, float &e, float (&gr)[3], float &V,
-                                          float (&gV)[3], float (&ggV)[6])
+struct NAcc {
+    static constexpr int K = FORCES ? 20 : 10;   // V, dV(3), G(6) [, T(10)]
+};
+
+template <bool FORCES, bool SERIES>
+__device__ __forceinline__ void src_fields(float rx, float ry, float rz, const float4 s0, const float4 s1,
+                                           const float4 s2, const float4 s3, const BCoef &bc,
+                                           float (&acc)[NAcc<FORCES>::K])
 {
     const float r2 = rx * rx + ry * ry + rz * rz;
     const float rinv = rsqrtf(r2);
     const float r = r2 * rinv;
     const float ri2 = rinv * rinv;
-    const float ex = __expf(-bc.xi * bc.xi * r2);
-    const float B0 = erfcf(bc.xi * r) * rinv;
-    const float B1 = (B0 + bc.c1 * ex) * ri2;
-    const float B2 = (3.f * B1 + bc.c2 * ex) * ri2;
-    const float B3 = (5.f * B2 + bc.c3 * ex) * ri2;
-    const float B4 = (7.f * B3 + bc.c4 * ex) * ri2;
-
-    const float Qir0 = I.xx * rx + I.xy * ry + I.xz * rz;
-    const float Qir1 = I.xy * rx + I.yy * ry + I.yz * rz;
-    const float Qir2 = I.xz * rx + I.yz * ry + I.zz * rz;
-    const float Qkr0 = K.xx * rx + K.xy * ry + K.xz * rz;
-    const float Qkr1 = K.xy * rx + K.yy * ry + K.yz * rz;
-    const float Qkr2 = K.xz * rx + K.yz * ry + K.zz * rz;
-    const float si = I.dx * rx + I.dy * ry + I.dz * rz;
-    const float sk = K.dx * rx + K.dy * ry + K.dz * rz;
-    const float ui = rx * Qir0 + ry * Qir1 + rz * Qir2;
-    const float uk = rx * Qkr0 + ry * Qkr1 + rz * Qkr2;
-    const float didk = I.dx * K.dx + I.dy * K.dy + I.dz * K.dz;
-    const float diQkr = I.dx * Qkr0 + I.dy * Qkr1 + I.dz * Qkr2;
-    const float dkQir = K.dx * Qir0 + K.dy * Qir1 + K.dz * Qir2;
-    const float QirQkr = Qir0 * Qkr0 + Qir1 * Qkr1 + Qir2 * Qkr2;
-    const float QiQk = I.xx * K.xx + I.yy * K.yy + I.zz * K.zz
-                     + 2.f * (I.xy * K.xy + I.xz * K.xz + I.yz * K.yz);
-    const float ski = sk - K.tr, sit = si + I.tr;
-    const float c0 = I.q * K.q;
-    const float c1 = I.q * ski - K.q * sit + didk;
-    const float c2 = I.q * uk + K.q * ui - sit * ski + 2.f * (diQkr - dkQir + QiQk);
-    const float c3 = ski * ui - sit * uk - 4.f * QirQkr;
-    const float c4 = ui * uk;
-    e += c0 * B0 + c1 * B1 + c2 * B2 + c3 * B3 + c4 * B4;
-    if (!FORCES) return;
-
-    const float B5 = (9.f * B4 + bc.c5 * ex) * ri2;
-    const float cb1 = c0 * B1 + c1 * B2 + c2 * B3 + c3 * B4 + c4 * B5;
-    // Theta_k mu_i, Theta_i mu_k, Theta_i (Theta_k r), Theta_k (Theta_i r)
-    const float Qkdi0 = K.xx * I.dx + K.xy * I.dy + K.xz * I.dz;
-    const float Qkdi1 = K.xy * I.dx + K.yy * I.dy + K.yz * I.dz;
-    const float Qkdi2 = K.xz * I.dx + K.yz * I.dy + K.zz * I.dz;
-    const float Qidk0 = I.xx * K.dx + I.xy * K.dy + I.xz * K.dz;
-    const float Qidk1 = I.xy * K.dx + I.yy * K.dy + I.yz * K.dz;
-    const float Qidk2 = I.xz * K.dx + I.yz * K.dy + I.zz * K.dz;
-    const float QQ0 = I.xx * Qkr0 + I.xy * Qkr1 + I.xz * Qkr2 + K.xx * Qir0 + K.xy * Qir1 + K.xz * Qir2;
-    const float QQ1 = I.xy * Qkr0 + I.yy * Qkr1 + I.yz * Qkr2 + K.xy * Qir0 + K.yy * Qir1 + K.yz * Qir2;
-    const float QQ2 = I.xz * Qkr0 + I.yz * Qkr1 + I.zz * Qkr2 + K.xz * Qir0 + K.yz * Qir1 + K.zz * Qir2;
-    const float di[3] = {I.dx, I.dy, I.dz}, dk[3] = {K.dx, K.dy, K.dz};
-    const float Qir[3] = {Qir0, Qir1, Qir2}, Qkr[3] = {Qkr0, Qkr1, Qkr2};
-    const float Qkdi[3] = {Qkdi0, Qkdi1, Qkdi2}, Qidk[3] = {Qidk0, Qidk1, Qidk2}, QQ[3] = {QQ0, QQ1, QQ2};
-    const float rr[3] = {rx, ry, rz};
+    const float ex = __expf(-bc.xi2 * r2);
+    float B0;
+    if (SERIES) {
+        const float x = bc.xi * r, x2 = x * x;
+        float p = bc.e[7];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const float g1 = I.q * dk[a] - K.q * di[a];
-        const float g2 = 2.f * (I.q * Qkr[a] + K.q * Qir[a] + Qkdi[a] - Qidk[a]) - di[a] * ski - sit * dk[a];
-        const float g3 = 2.f * (ski * Qir[a] - sit * Qkr[a]) + ui * dk[a] - uk * di[a] - 4.f * QQ[a];
-        const float g4 = 2.f * (uk * Qir[a] + ui * Qkr[a]);
-        gr[a] += g1 * B1 + g2 * B2 + g3 * B3 + g4 * B4 - rr[a] * cb1;
+        for (int k = 6; k >= 0; --k) p = fmaf(p, x2, bc.e[k]);
+        B0 = fmaf(-x, p, 1.f) * rinv;
+    } else {
+        B0 = erfcf(bc.xi * r) * rinv;
     }
-    // potential, field and field gradient of the source at the target
-    V += K.q * B0 + ski * B1 + uk * B2;
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-        gV[a] += B1 * (dk[a] - K.q * rr[a]) + B2 * (2.f * Qkr[a] - ski * rr[a]) - B3 * uk * rr[a];
-    const float dA = -K.q * B1 - ski * B2 - uk * B3;
-    const float rrA = K.q * B2 + ski * B3 + uk * B4;
-    const float Kab[6] = {K.xx, K.xy, K.xz, K.yy, K.yz, K.zz};
-    const int PA[6] = {0, 0, 0, 1, 1, 2}, PB[6] = {0, 1, 2, 1, 2, 2};
-#pragma unroll
-    for (int m = 0; m < 6; ++m) {
-        const int a = PA[m], b = PB[m];
-        float G = rr[a] * rr[b] * rrA - (dk[a] * rr[b] + rr[a] * dk[b]) * B2 + 2.f * Kab[m] * B2
-                - 2.f * (rr[a] * Qkr[b] + Qkr[a] * rr[b]) * B3;
-        if (a == b) G += dA;
-        ggV[m] += (a == b) ? G : 2.f * G;
+    const float B1 = fmaf(bc.c1, ex, B0) * ri2;
+    const float B2 = fmaf(bc.c2, ex, 3.f * B1) * ri2;
+    const float B3 = fmaf(bc.c3, ex, 5.f * B2) * ri2;
+    const float B4 = fmaf(bc.c4, ex, 7.f * B3) * ri2;
+    // source multipoles: s0 = (x, y, z, q), s1 = (mu, tr Theta), s2 = (xx, xy, xz, yy), s3 = (yz, zz, -, -)
+    const float q = s0.w, mx = s1.x, my = s1.y, mz = s1.z;
+    const float txx = s2.x, txy = s2.y, txz = s2.z, tyy = s2.w, tyz = s3.x, tzz = s3.y;
+    const float Qx = txx * rx + txy * ry + txz * rz;
+    const float Qy = txy * rx + tyy * ry + tyz * rz;
+    const float Qz = txz * rx + tyz * ry + tzz * rz;
+    const float s = mx * rx + my * ry + mz * rz - s1.w;
+    const float u = rx * Qx + ry * Qy + rz * Qz;
+    const float A = -(q * B1 + s * B2 + u * B3);
+    const float A2 = q * B2 + s * B3 + u * B4;
+    acc[0] += q * B0 + s * B1 + u * B2;
+    const float twoB2 = 2.f * B2;
+    acc[1] += mx * B1 + twoB2 * Qx + rx * A;
+    acc[2] += my * B1 + twoB2 * Qy + ry * A;
+    acc[3] += mz * B1 + twoB2 * Qz + rz * A;
+    const float twoB3 = 2.f * B3;
+    const float Px = mx * B2 + twoB3 * Qx, Py = my * B2 + twoB3 * Qy, Pz = mz * B2 + twoB3 * Qz;
+    const float rxA2 = rx * A2, ryA2 = ry * A2, rzA2 = rz * A2;
+    acc[4] += A + rx * rxA2 - 2.f * rx * Px + twoB2 * txx;
+    acc[5] += rx * ryA2 - (rx * Py + ry * Px) + twoB2 * txy;
+    acc[6] += rx * rzA2 - (rx * Pz + rz * Px) + twoB2 * txz;
+    acc[7] += A + ry * ryA2 - 2.f * ry * Py + twoB2 * tyy;
+    acc[8] += ry * rzA2 - (ry * Pz + rz * Py) + twoB2 * tyz;
+    acc[9] += A + rz * rzA2 - 2.f * rz * Pz + twoB2 * tzz;
+    if (FORCES) {
+        const float B5 = fmaf(bc.c5, ex, 9.f * B4) * ri2;
+        const float A3 = q * B3 + s * B4 + u * B5;
+        const float twoB4 = 2.f * B4;
+        const float Wx = rxA2 - Px, Wy = ryA2 - Py, Wz = rzA2 - Pz;   // r A2 - mu B2 - 2 Q B3
+        const float Zx = mx * B3 + twoB4 * Qx, Zy = my * B3 + twoB4 * Qy, Zz = mz * B3 + twoB4 * Qz;
+        const float Yxx = twoB3 * txx, Yxy = twoB3 * txy, Yxz = twoB3 * txz;
+        const float Yyy = twoB3 * tyy, Yyz = twoB3 * tyz, Yzz = twoB3 * tzz;
+        const float xx = rx * rx, yy = ry * ry, zz = rz * rz, xy = rx * ry, xz = rx * rz, yz = ry * rz;
+        // T_abc, a <= b <= c: xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz
+        acc[10] += 3.f * Wx - xx * rx * A3 + 3.f * xx * Zx - 3.f * Yxx * rx;
+        acc[11] += Wy - xx * ry * A3 + xx * Zy + 2.f * xy * Zx - (Yxx * ry + 2.f * Yxy * rx);
+        acc[12] += Wz - xx * rz * A3 + xx * Zz + 2.f * xz * Zx - (Yxx * rz + 2.f * Yxz * rx);
+        acc[13] += Wx - yy * rx * A3 + yy * Zx + 2.f * xy * Zy - (Yyy * rx + 2.f * Yxy * ry);
+        acc[14] += -xy * rz * A3 + xy * Zz + xz * Zy + yz * Zx - (Yxy * rz + Yxz * ry + Yyz * rx);
+        acc[15] += Wx - zz * rx * A3 + zz * Zx + 2.f * xz * Zz - (Yzz * rx + 2.f * Yxz * rz);
+        acc[16] += 3.f * Wy - yy * ry * A3 + 3.f * yy * Zy - 3.f * Yyy * ry;
+        acc[17] += Wz - yy * rz * A3 + yy * Zz + 2.f * yz * Zy - (Yyy * rz + 2.f * Yyz * ry);
+        acc[18] += Wy - zz * ry * A3 + zz * Zy + 2.f * yz * Zz - (Yzz * ry + 2.f * Yyz * rz);
+        acc[19] += 3.f * Wz - zz * rz * A3 + 3.f * zz * Zz - 3.f * Yzz * rz;
     }
 }
 
-template <bool FORCES>
-__global__ void __launch_bounds__(128)
-k_near(Geo g, int N, const int *__restrict__ start, const int *__restrict__ scell,
-       const float4 *__restrict__ A0, const float4 *__restrict__ A1, const float4 *__restrict__ A2,
-       const float4 *__restrict__ A3, BCoef bc, float *__restrict__ gnear, double *__restrict__ part)
+template <bool FORCES, bool SERIES>
+__global__ void __launch_bounds__(kNearWarps * 32)
+k_near(Geo g, const int *__restrict__ start, const float4 *__restrict__ A0, const float4 *__restrict__ A1,
+       const float4 *__restrict__ A2, const float4 *__restrict__ A3, BCoef bc, float *__restrict__ gnear,
+       int64_t Nslot, double *__restrict__ part)
 {
-    __shared__ double sh[32];
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    float e = 0.f;
-    float gr[3] = {0.f, 0.f, 0.f}, V = 0.f, gV[3] = {0.f, 0.f, 0.f};
-    float ggV[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (s < N) {
-        const float4 t0 = A0[s];
-        const MPf I = load_mp(t0, A1[s], A2[s], A3[s]);
-        const int cell = scell[s];
-        const int n = g.n;
-        const int cx = cell / (n * n), cy = (cell / n) % n, cz = cell % n;
-        for (int dx = -1; dx <= 1; ++dx) {
-            const int nx = (cx + dx + n) % n;
-            for (int dy = -1; dy <= 1; ++dy) {
-                const int ny = (cy + dy + n) % n;
-                for (int dz = -1; dz <= 1; ++dz) {
-                    const int nz = (cz + dz + n) % n;
-                    const int nc = (nx * n + ny) * n + nz;
-                    const float ox = dx * g.hf, oy = dy * g.hf, oz = dz * g.hf;
-                    const bool same = (dx == 0 && dy == 0 && dz == 0);
-                    const int jb = start[nc], je = start[nc + 1];
-                    for (int j = jb; j < je; ++j) {
-                        if (same && j == s) continue;
-                        const float4 k0 = A0[j];
-                        const MPf K = load_mp(k0, A1[j], A2[j], A3[j]);
-                        const float rx = (t0.x - k0.x) - ox;
-                        const float ry = (t0.y - k0.y) - oy;
-                        const float rz = (t0.z - k0.z) - oz;
-                        near_pair<FORCES>(rx, ry, rz, I, K, bc, e, gr, V, gV, ggV);
+    constexpr int K = NAcc<FORCES>::K;
+    __shared__ float4 sSrc[kNearWarps][kNearChunk][4];
+    __shared__ int sSlot[kNearWarps][kNearChunk];
+    __shared__ int sBeg[kNearWarps][28], sPre[kNearWarps][28];
+    __shared__ float sRed[kNearWarps][K][32];
+    __shared__ double sE[kNearWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n = g.n;
+    const float h = g.hf;
+    double ew = 0.0;
+    for (int t = blockIdx.x * kNearWarps + warp; t < g.ncell; t += gridDim.x * kNearWarps) {
+        const int tb = start[t], nt_all = start[t + 1] - tb;
+        if (nt_all == 0) continue;
+        const int cx = t / (n * n), cy = (t / n) % n, cz = t % n;
+        // neighbour leaves: begin offsets and exclusive prefix of their counts
+        int cnt = 0, beg = 0;
+        if (lane < 27) {
+            const int dx = lane / 9 - 1, dy = (lane / 3) % 3 - 1, dz = lane % 3 - 1;
+            const int nc = (((cx + dx + n) % n) * n + (cy + dy + n) % n) * n + (cz + dz + n) % n;
+            beg = start[nc];
+            cnt = start[nc + 1] - beg;
+        }
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int ns = __shfl_sync(0xffffffffu, incl, 26);
+        if (lane < 27) {
+            sBeg[warp][lane] = beg;
+            sPre[warp][lane] = incl - cnt;
+        }
+        if (lane == 27) sPre[warp][27] = ns;
+        __syncwarp();
+        for (int t0 = 0; t0 < nt_all; t0 += 32) {
+            const int nt = min(32, nt_all - t0);
+            const int G = 32 / nt;
+            const int il = lane % nt, grp = lane / nt;
+            const bool active = grp < G;
+            const int si = tb + t0 + il;
+            const float4 ti = A0[si];
+            float acc[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc[k] = 0.f;
+            for (int c0 = 0; c0 < ns; c0 += kNearChunk) {
+                const int cs = min(kNearChunk, ns - c0);
+                __syncwarp();
+                for (int k = lane; k < cs; k += 32) {
+                    const int f = c0 + k;
+                    // leaf d with sPre[d] <= f < sPre[d+1]
+                    int lo = 0, hi = 27;
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (sPre[warp][mid] <= f) lo = mid;
+                        else hi = mid;
+                    }
+                    const int d = lo;
+                    const int slot = sBeg[warp][d] + (f - sPre[warp][d]);
+                    float4 a0 = A0[slot];
+                    const float4 a1 = A1[slot], a2 = A2[slot], a3 = A3[slot];
+                    a0.x += (d / 9 - 1) * h;
+                    a0.y += ((d / 3) % 3 - 1) * h;
+                    a0.z += (d % 3 - 1) * h;
+                    sSrc[warp][k][0] = a0;
+                    sSrc[warp][k][1] = make_float4(a1.x, a1.y, a1.z, a2.x + a2.w + a3.y);
+                    sSrc[warp][k][2] = a2;
+                    sSrc[warp][k][3] = a3;
+                    sSlot[warp][k] = slot;
+                }
+                __syncwarp();
+                if (active) {
+                    for (int k = grp; k < cs; k += G) {
+                        if (sSlot[warp][k] == si) continue;
+                        const float4 s0 = sSrc[warp][k][0];
+                        src_fields<FORCES, SERIES>(ti.x - s0.x, ti.y - s0.y, ti.z - s0.z, s0, sSrc[warp][k][1],
+                                                   sSrc[warp][k][2], sSrc[warp][k][3], bc, acc);
                     }
                 }
             }
-        }
-        if (FORCES) {
-            const int64_t S = N;
-            gnear[0 * S + s] = gr[0];
-            gnear[1 * S + s] = gr[1];
-            gnear[2 * S + s] = gr[2];
-            gnear[3 * S + s] = V;
-            gnear[4 * S + s] = gV[0];
-            gnear[5 * S + s] = gV[1];
-            gnear[6 * S + s] = gV[2];
+            // sum the group partials of each target in a fixed order
+            __syncwarp();
 #pragma unroll
-            for (int m = 0; m < 6; ++m) gnear[(7 + m) * S + s] = ggV[m];
+            for (int k = 0; k < K; ++k) sRed[warp][k][lane] = active ? acc[k] : 0.f;
+            __syncwarp();
+            if (lane < nt) {
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    float v = sRed[warp][k][lane];
+                    for (int gq = 1; gq < G; ++gq) v += sRed[warp][k][lane + gq * nt];
+                    acc[k] = v;
+                }
+                const float4 a1 = A1[si], a2 = A2[si], a3 = A3[si];
+                const float q = ti.w, mx = a1.x, my = a1.y, mz = a1.z;
+                const float txx = a2.x, txy = a2.y, txz = a2.z, tyy = a2.w, tyz = a3.x, tzz = a3.y;
+                // e_i = q V + mu.dV + Theta:G
+                const float ei = q * acc[0] + mx * acc[1] + my * acc[2] + mz * acc[3] + txx * acc[4] +
+                                 tyy * acc[7] + tzz * acc[9] + 2.f * (txy * acc[5] + txz * acc[6] + tyz * acc[8]);
+                ew += 0.5 * (double)ei;
+                if (FORCES) {
+                    const int64_t S = Nslot;
+                    // dE/dx = q dV + mu.G + Theta:T
+                    const float Gm[3][3] = {{acc[4], acc[5], acc[6]}, {acc[5], acc[7], acc[8]}, {acc[6], acc[8], acc[9]}};
+                    const float Tm[3][6] = {{acc[10], acc[11], acc[12], acc[13], acc[14], acc[15]},
+                                            {acc[11], acc[13], acc[14], acc[16], acc[17], acc[18]},
+                                            {acc[12], acc[14], acc[15], acc[17], acc[18], acc[19]}};
+                    // T_c(ab) in the order xx xy xz yy yz zz
+                    const float mu[3] = {mx, my, mz};
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        float f = q * acc[1 + c] + mu[0] * Gm[0][c] + mu[1] * Gm[1][c] + mu[2] * Gm[2][c];
+                        f += txx * Tm[c][0] + 2.f * txy * Tm[c][1] + 2.f * txz * Tm[c][2] + tyy * Tm[c][3] +
+                             2.f * tyz * Tm[c][4] + tzz * Tm[c][5];
+                        gnear[(int64_t)c * S + si] = f;
+                    }
+                    gnear[3 * S + si] = acc[0];
+                    gnear[4 * S + si] = acc[1];
+                    gnear[5 * S + si] = acc[2];
+                    gnear[6 * S + si] = acc[3];
+                    gnear[7 * S + si] = acc[4];
+                    gnear[8 * S + si] = 2.f * acc[5];
+                    gnear[9 * S + si] = 2.f * acc[6];
+                    gnear[10 * S + si] = acc[7];
+                    gnear[11 * S + si] = 2.f * acc[8];
+                    gnear[12 * S + si] = acc[9];
+                }
+            }
         }
     }
-    // per-target energy I_i . V_i; 1/2 for the double counting of ordered pairs
-    double t = 0.5 * (double)e;
+    // fixed-order block reduction of the energy
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) sh[wid] = t;
+    for (int o = 16; o > 0; o >>= 1) ew += __shfl_down_sync(0xffffffffu, ew, o);
+    if (lane == 0) sE[warp] = ew;
     __syncthreads();
     if (threadIdx.x == 0) {
         double u = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) u += sh[w];
+        for (int w = 0; w < kNearWarps; ++w) u += sE[w];
         part[blockIdx.x] = u;
     }
 }
 
-int near_blocks(const Handle &H) { return (int)((H.N + 127) / 128); }
+int near_blocks(const Handle &H)
+{
+    (void)H;
+    return 152 * 5;
+}
 
 cudaError_t launch_near(Handle &H, bool forces, cudaStream_t s)
 {
     BCoef bc;
     const double xi = H.g.xi;
     bc.xi = (float)xi;
+    bc.xi2 = (float)(xi * xi);
     double c = 1.0 / (xi * sqrt(M_PI));
     double cl[6];
     for (int l = 1; l <= 5; ++l) {
@@ -207,14 +286,32 @@ cudaError_t launch_near(Handle &H, bool forces, cudaStream_t s)
         cl[l] = c;
     }
     bc.c1 = (float)cl[1]; bc.c2 = (float)cl[2]; bc.c3 = (float)cl[3]; bc.c4 = (float)cl[4]; bc.c5 = (float)cl[5];
-    const int N = (int)H.N;
+    // erf(x) = (2/sqrt(pi)) sum_k (-1)^k x^(2k+1) / (k! (2k+1))  (Maclaurin series)
+    double fact = 1.0;
+    for (int k = 0; k < 8; ++k) {
+        if (k > 0) fact *= k;
+        bc.e[k] = (float)((k % 2 ? -1.0 : 1.0) * 2.0 / sqrt(M_PI) / (fact * (2 * k + 1)));
+    }
+    const double rmax = 2.0 * sqrt(3.0) * H.g.h;   // farthest pair of adjacent leaves
+    bc.series = (xi * rmax <= 0.5) ? 1 : 0;
     double *part = H.d_part + H.part_off[kPartNear];
-    if (forces)
-        k_near<true><<<near_blocks(H), 128, 0, s>>>(H.g, N, H.d_start, H.d_scell, H.d_A0, H.d_A1, H.d_A2,
-                                                    H.d_A3, bc, H.d_gnear, part);
-    else
-        k_near<false><<<near_blocks(H), 128, 0, s>>>(H.g, N, H.d_start, H.d_scell, H.d_A0, H.d_A1, H.d_A2,
-                                                     H.d_A3, bc, H.d_gnear, part);
+    const int nb = near_blocks(H);
+    const int64_t S = H.N;
+    if (forces) {
+        if (bc.series)
+            k_near<true, true><<<nb, kNearWarps * 32, 0, s>>>(H.g, H.d_start, H.d_A0, H.d_A1, H.d_A2, H.d_A3, bc,
+                                                              H.d_gnear, S, part);
+        else
+            k_near<true, false><<<nb, kNearWarps * 32, 0, s>>>(H.g, H.d_start, H.d_A0, H.d_A1, H.d_A2, H.d_A3, bc,
+                                                               H.d_gnear, S, part);
+    } else {
+        if (bc.series)
+            k_near<false, true><<<nb, kNearWarps * 32, 0, s>>>(H.g, H.d_start, H.d_A0, H.d_A1, H.d_A2, H.d_A3, bc,
+                                                               H.d_gnear, S, part);
+        else
+            k_near<false, false><<<nb, kNearWarps * 32, 0, s>>>(H.g, H.d_start, H.d_A0, H.d_A1, H.d_A2, H.d_A3,
+                                                                bc, H.d_gnear, S, part);
+    }
     return cudaGetLastError();
 }
 
