@@ -176,6 +176,7 @@ def main():
     ap.add_argument("--plain", action="store_true", help="plain FP32 adjacent-leaf correction")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--n-cells", type=int, default=0, help="leaves per axis (0 = library choice)")
     args = ap.parse_args()
 
     rank, world, local = env_int("RANK", 0), env_int("WORLD_SIZE", 1), env_int("LOCAL_RANK", 0)
@@ -206,7 +207,7 @@ def main():
         name=synth.CONFIGS[cfg]["name"])
     N = box.n
     t_pre0 = time.perf_counter()
-    model = api.Ankh(box.box, N, Lu=5, Lc=5, mixed=not args.plain)
+    model = api.Ankh(box.box, N, n_cells=args.n_cells, Lu=5, Lc=5, mixed=not args.plain)
     t_pre = time.perf_counter() - t_pre0
     info = model.info
     f32 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)

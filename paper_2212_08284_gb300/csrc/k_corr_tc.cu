@@ -18,12 +18,13 @@
 // correction potential psi and form -1/2 sum M.psi in FP64.
 //
 // The tensor core rounds toward zero as it accumulates; over the 27 x 48 MMA
-// steps of a tile that bias reaches ~4e-5.  So the products of one stage
-// (K = 32) go to TMEM and are drained after the stage into FP32 registers
-// with round-to-nearest additions, while the next stage accumulates into the
-// other of two buffers.  The large C_hi.M_hi products and the small
-// C_hi.M_lo + C_lo.M_hi corrections use separate accumulators, so only four
-// truncating steps act on the large sum between drains.
+// steps of a tile that bias reaches ~4e-5.  So the large C_hi.M_hi products
+// of one stage (K = 32, four MMAs) go to one of two TMEM buffers and are
+// drained after the stage into FP32 registers with round-to-nearest
+// additions, while the next stage accumulates into the other buffer.  The
+// small C_hi.M_lo + C_lo.M_hi corrections (2^-11 of the large ones) stay in a
+// third TMEM accumulator for the whole tile; their truncation bias is
+// relative to their own small size and negligible.
 //
 // Every wait is bounded (clock64 budget); on timeout the kernel raises bit 2
 // of the error flag, waits (bounded) for its own copies in flight, frees its
@@ -141,6 +142,22 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t *r)
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 }  // namespace tcg
 
 template <bool FORCES>
@@ -219,9 +236,10 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
             *issued = it + 1;
         }
     } else if (warp == 5 && lane == 0) {
-        // MMA issuer: each stage accumulates into one of two TMEM buffers
-        // (large products | small corrections), drained by the epilogue warps
+        // MMA issuer: large products of each stage into one of two TMEM buffers
+        // (drained by the epilogue warps), small corrections into a third one
         const uint32_t idesc = idesc_tf32(kRows, N);
+        const uint32_t small = tmem + (uint32_t)(2 * N);
         int consumed = 0;
         for (int it = 0; it < kIters; ++it) {
             const int s = it % kStages, k = it / kStages, buf = it & 1;
@@ -235,14 +253,14 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
             }
             consumed = it + 1;
             fence_after();
-            const uint32_t big = tmem + (uint32_t)(buf * 2 * N), small = big + (uint32_t)N;
+            const uint32_t big = tmem + (uint32_t)(buf * N);
             const uint32_t base = su32(smem + (size_t)s * stage);
             const uint32_t ahi = base, alo = base + kABytes, bhi = base + 2 * kABytes, blo = bhi + bbytes;
 #pragma unroll
             for (int k8 = 0; k8 < kKc / 8; ++k8) {
                 const uint32_t off = k8 * 32;
                 mma_tf32(big, desc_sw128(ahi + off), desc_sw128(bhi + off), idesc, k8 > 0 ? 1u : 0u);
-                mma_tf32(small, desc_sw128(ahi + off), desc_sw128(blo + off), idesc, k8 > 0 ? 1u : 0u);
+                mma_tf32(small, desc_sw128(ahi + off), desc_sw128(blo + off), idesc, (it > 0 || k8 > 0) ? 1u : 0u);
                 mma_tf32(small, desc_sw128(alo + off), desc_sw128(bhi + off), idesc, 1u);
             }
             mma_commit(&empty[s]);
@@ -259,32 +277,53 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
     }
     double e = 0.0;
     if (warp < 4) {
-        // drain every stage's accumulators into FP32 registers (round to nearest)
+        // drain every stage's large accumulator into FP32 registers (round to nearest)
         float acc[128];
 #pragma unroll
         for (int j = 0; j < 128; ++j) acc[j] = 0.f;
         bool ok = true;
+        const uint32_t lanebase = tmem + ((uint32_t)(warp * 32) << 16);
         for (int it = 0; it < kIters; ++it) {
             const int buf = it & 1;
             bool w = mbar_wait(&acc_full[buf], (uint32_t)((it >> 1) & 1), 2 * kBudget);
             ok = __all_sync(0xffffffffu, w && !*abort_flag);
             if (!ok) break;
             fence_after();
-            const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * 2 * N);
+            const uint32_t ta = lanebase + (uint32_t)(buf * N);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
+            for (int c = 0; c < 4; c += 2) {
                 if (c * 32 < N) {
-                    float v[32], w2[32];
-                    tmem_ld32(ta + (uint32_t)(c * 32), v);
-                    tmem_ld32(ta + (uint32_t)(N + c * 32), w2);
+                    uint32_t v[64];
+                    tmem_ld32_nowait(ta + (uint32_t)(c * 32), v);
+                    if ((c + 1) * 32 < N) tmem_ld32_nowait(ta + (uint32_t)((c + 1) * 32), v + 32);
+                    tmem_wait_ld();
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) acc[c * 32 + j] += v[j] + w2[j];
+                    for (int j = 0; j < 32; ++j) acc[c * 32 + j] += __uint_as_float(v[j]);
+                    if ((c + 1) * 32 < N) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) acc[(c + 1) * 32 + j] += __uint_as_float(v[32 + j]);
+                    }
                 }
             }
             fence_before();
             __syncwarp();
             if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&acc_empty[buf]))
                                         : "memory");
+        }
+        if (ok) {
+            // the small corrections, accumulated in TMEM over the whole tile (the
+            // last acc_full arrival follows every MMA of the tile)
+            const uint32_t ts = lanebase + (uint32_t)(2 * N);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                if (c * 32 < N) {
+                    uint32_t v[32];
+                    tmem_ld32_nowait(ts + (uint32_t)(c * 32), v);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) acc[c * 32 + j] += __uint_as_float(v[j]);
+                }
+            }
         }
         if (ok) {
             const int m = warp * 32 + lane;
@@ -371,7 +410,7 @@ bool tc_prepare(Handle &H, std::string &err)
     H.tc.rowstride = S + 2;
     H.tc.N = R * S;
     H.tc.tmem_cols = 32;
-    while ((int)H.tc.tmem_cols < 4 * H.tc.N) H.tc.tmem_cols <<= 1;   // 2 buffers x (large | small)
+    while ((int)H.tc.tmem_cols < 3 * H.tc.N) H.tc.tmem_cols <<= 1;   // 2 large buffers + 1 small
     H.tc.tiles = (g.n * g.n + R - 1) / R;
     const uint64_t rows = (uint64_t)g.n * g.n * H.tc.rowstride;
     if (!encode_2d(&H.tc.mAhi, H.d_Chi, 27 * 128, 128, tcg::kKc, 128, err)) return false;

@@ -198,6 +198,7 @@ k_near(Geo g, const int *__restrict__ start, const float4 *__restrict__ A0, cons
                 }
                 __syncwarp();
                 if (active) {
+#pragma unroll 2
                     for (int k = grp; k < cs; k += G) {
                         if (sSlot[warp][k] == si) continue;
                         const float4 s0 = sSrc[warp][k][0];
