@@ -171,7 +171,7 @@ static int choose_n(double box, int Lu)
 static void free_device(Handle *H)
 {
     if (!H) return;
-    void *ptrs[] = {H->d_cellid, H->d_rank, H->d_count, H->d_start, H->d_perm, H->d_scell, H->d_flag,
+    void *ptrs[] = {H->d_cellid, H->d_rank, H->d_count, H->d_start, H->d_perm, H->d_scell, H->d_flag, H->d_bsum,
                     H->d_A0, H->d_A1, H->d_A2, H->d_A3, H->d_W, H->d_M, H->d_rho, H->d_rhohat, H->d_D,
                     H->d_phi, H->d_C, H->d_Chi, H->d_Clo, H->d_psi, H->d_gfar, H->d_gnear, H->d_part,
                     H->d_partoff, H->d_terms, H->d_hostbuf, H->d_Mhi, H->d_Mlo};
@@ -238,10 +238,8 @@ static int run_sequence(Handle &H, const float *x, const float *q, const float *
         if (cufftExecC2R(H.plan_c2r, H.d_rhohat, H.d_phi) != CUFFT_SUCCESS)
             return fail(ANKH_ECUDA, "cufftExecC2R");
         mark(H, kStFFTi, s);
-        ANKH_CU(launch_l2p(H, s), "l2p");
+        ANKH_CU(launch_l2p(H, dEdx, dEdq, dEdmu, dEdtheta, torque, s), "l2p");
         mark(H, kStL2P, s);
-        ANKH_CU(launch_finalize(H, dEdx, dEdq, dEdmu, dEdtheta, torque, s), "finalize");
-        mark(H, kStFinal, s);
     }
     ANKH_CU(launch_reduce(H, s), "reduce");
     mark(H, kStReduce, s);
@@ -347,6 +345,7 @@ int ankh_create(double box_edge, int64_t N, const ankh_params *params, ankh_hand
     ANKH_AL(H.d_rank, N);
     ANKH_AL(H.d_count, g.ncell);
     ANKH_AL(H.d_start, g.ncell + 1);
+    ANKH_AL(H.d_bsum, (g.ncell + 1023) / 1024 + 1);
     ANKH_AL(H.d_perm, N);
     ANKH_AL(H.d_scell, N);
     ANKH_AL(H.d_flag, 4);
@@ -362,7 +361,6 @@ int ankh_create(double box_edge, int64_t N, const ankh_params *params, ankh_hand
     ANKH_AL(H.d_phi, g.M);
     ANKH_AL(H.d_C, (int64_t)27 * g.ldm * g.ldm);
     ANKH_AL(H.d_psi, (int64_t)g.ncell * g.ldm);
-    ANKH_AL(H.d_gfar, 13 * N);
     ANKH_AL(H.d_gnear, 13 * N);
     // energy partial layout
     int nb[kPartCount];

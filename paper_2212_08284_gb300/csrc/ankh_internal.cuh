@@ -58,7 +58,7 @@ struct Handle {
     int64_t device_bytes;
 
     // atoms (sorted by leaf)
-    int *d_cellid, *d_rank, *d_count, *d_start, *d_perm, *d_scell, *d_flag;
+    int *d_cellid, *d_rank, *d_count, *d_start, *d_perm, *d_scell, *d_flag, *d_bsum;
     float4 *d_A0, *d_A1, *d_A2, *d_A3;   // (lx, ly, lz, q) (mu, 0) (txx, txy, txz, tyy) (tyz, tzz, 0, 0)
     // interpolation
     float *d_W;             // [4][Lu][Lc] fused Chebyshev->equispaced derivative matrices, scaled by (2/h)^p
@@ -105,7 +105,8 @@ cudaError_t launch_fine_gather(Handle &H, cudaStream_t s);
 cudaError_t launch_spectral(Handle &H, bool forces, cudaStream_t s);
 cudaError_t launch_corr(Handle &H, bool forces, cudaStream_t s);
 cudaError_t launch_near(Handle &H, bool forces, cudaStream_t s);
-cudaError_t launch_l2p(Handle &H, cudaStream_t s);
+cudaError_t launch_l2p(Handle &H, float *dEdx, float *dEdq, float *dEdmu, float *dEdtheta, float *torque,
+                       cudaStream_t s);
 cudaError_t launch_self_dc(Handle &H, cudaStream_t s);
 cudaError_t launch_finalize(Handle &H, float *dEdx, float *dEdq, float *dEdmu, float *dEdtheta,
                             float *torque, cudaStream_t s);

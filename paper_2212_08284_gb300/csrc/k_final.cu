@@ -1,6 +1,6 @@
-// Self term (Eq. ewald, Alg. 5 step 4), k = 0 far-field term, gradient
-// assembly and the FP64 energy reduction (Alg. 5 step 5).
-//
+// k = 0 far-field term, gradient assembly and the FP64 energy reduction
+// (Alg. 5 steps 4-5).  The self term of Eq. ewald (per atom in the gather
+// kernel, k_sort.cu) is
 // E_self = -(xi/sqrt(pi)) sum_i [q^2 + (2xi^2/3)|mu|^2 - (4xi^2/3) q tr(Theta)
 //                                + (8xi^4/5) Theta:Theta + (4xi^4/5) tr(Theta)^2]
 // (general symmetric Theta; for a traceless Theta this is the printed form).
@@ -11,61 +11,25 @@
 
 namespace ankh {
 
-__global__ void __launch_bounds__(256)
-k_self(int N, const float4 *__restrict__ A0, const float4 *__restrict__ A1,
-       const float4 *__restrict__ A2, const float4 *__restrict__ A3, double xi,
-       double *__restrict__ part_self, double *__restrict__ part_q)
-{
-    __shared__ double sh1[32], sh2[32];
-    double es = 0.0, qs = 0.0;
-    const double c = xi / sqrt(M_PI), a2 = xi * xi, a4 = a2 * a2;
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
-        const float4 a0 = A0[s], a1 = A1[s], a2v = A2[s], a3 = A3[s];
-        const double q = a0.w;
-        const double mu2 = (double)a1.x * a1.x + (double)a1.y * a1.y + (double)a1.z * a1.z;
-        const double xx = a2v.x, xy = a2v.y, xz = a2v.z, yy = a2v.w, yz = a3.x, zz = a3.y;
-        const double tr = xx + yy + zz;
-        const double TT = xx * xx + yy * yy + zz * zz + 2.0 * (xy * xy + xz * xz + yz * yz);
-        es += -c * (q * q + (2.0 * a2 / 3.0) * mu2 - (4.0 * a2 / 3.0) * q * tr + (8.0 * a4 / 5.0) * TT
-                    + (4.0 * a4 / 5.0) * tr * tr);
-        qs += q;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        es += __shfl_down_sync(0xffffffffu, es, o);
-        qs += __shfl_down_sync(0xffffffffu, qs, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        sh1[threadIdx.x >> 5] = es;
-        sh2[threadIdx.x >> 5] = qs;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double u = 0.0, v = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            u += sh1[w];
-            v += sh2[w];
-        }
-        part_self[blockIdx.x] = u;
-        part_q[blockIdx.x] = v;
-    }
-}
-
-int self_blocks(const Handle &H)
-{
-    (void)H;
-    return 152 * 2;
-}
+int self_blocks(const Handle &H) { return (int)((H.N + 255) / 256); }
 
 // total charge and the k = 0 potential D0 Q / M -> terms[6], terms[7] (Q)
-__global__ void k_dc(const double *__restrict__ part_q, int nq, double D0, double invM,
-                     double *__restrict__ terms)
+__global__ void __launch_bounds__(256) k_dc(const double *__restrict__ part_q, int nq, double D0, double invM,
+                                            double *__restrict__ terms)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    __shared__ double sh[8];
     double Q = 0.0;
-    for (int b = 0; b < nq; ++b) Q += part_q[b];
-    terms[7] = Q;
-    terms[6] = D0 * Q * invM;
+    for (int b = threadIdx.x; b < nq; b += 256) Q += part_q[b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) Q += __shfl_down_sync(0xffffffffu, Q, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = Q;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double u = 0.0;
+        for (int w = 0; w < 8; ++w) u += sh[w];
+        terms[7] = u;
+        terms[6] = D0 * u * invM;
+    }
 }
 
 // Gradient assembly per sorted slot: far + near + self (+ k = 0 potential),
@@ -182,12 +146,11 @@ __global__ void k_reduce(const double *__restrict__ part, const int *__restrict_
     }
 }
 
+// the self term and Q partials are produced by the gather kernel (k_sort.cu)
 cudaError_t launch_self_dc(Handle &H, cudaStream_t s)
 {
-    k_self<<<self_blocks(H), 256, 0, s>>>((int)H.N, H.d_A0, H.d_A1, H.d_A2, H.d_A3, (double)H.g.xi,
-                                          H.d_part + H.part_off[kPartSelf], H.d_part + H.part_off[kPartQ]);
-    k_dc<<<1, 32, 0, s>>>(H.d_part + H.part_off[kPartQ], self_blocks(H), H.D0, 1.0 / (double)H.g.M,
-                          H.d_terms);
+    k_dc<<<1, 256, 0, s>>>(H.d_part + H.part_off[kPartQ], self_blocks(H), H.D0, 1.0 / (double)H.g.M,
+                           H.d_terms);
     return cudaGetLastError();
 }
 

@@ -49,78 +49,138 @@ __device__ __forceinline__ float tf32_rna(float x)
     return __uint_as_float(r);
 }
 
+// One warp per leaf.  The ten terms of Alg. 2 factor by the x-derivative
+// order: M[a,b,c] += sum_p ux^(p)[a] G_p[b,c] with G_0 = q uy0 uz0 + mu_y uy1 uz0
+// + mu_z uy0 uz1 + Th_yy uy2 uz0 + 2 Th_yz uy1 uz1 + Th_zz uy0 uz2, G_1 = mu_x uy0 uz0
+// + 2 Th_xy uy1 uz0 + 2 Th_xz uy0 uz1, G_2 = Th_xx uy0 uz0.  Each lane owns one
+// (b, c) node column and all L_u values of a; per-atom data (basis values,
+// multipoles) sit in shared memory and are read as broadcast float4s.
+constexpr int kP2MWarps = 4;
+constexpr int kP2MChunk = 16;
+
 template <int LU>
-__global__ void __launch_bounds__(((LU * LU * LU + 31) / 32) * 32)
+struct P2MAtom {
+    static constexpr int NX = (3 * LU + 3) / 4;       // float4s for ux^(0..2)[0..LU-1]
+    float4 ux[NX];
+    float4 mp[3];                                     // q mux muy muz | xx 2xy 2xz yy | 2yz zz - -
+    float uy[3][LU];
+    float uz[3][LU];
+};
+
+template <int LU>
+__global__ void __launch_bounds__(kP2MWarps * 32)
 k_p2m(Geo g, const int *__restrict__ start, const float4 *__restrict__ A0,
       const float4 *__restrict__ A1, const float4 *__restrict__ A2, const float4 *__restrict__ A3,
       const float *__restrict__ W, float *__restrict__ M, float *__restrict__ Mhi, float *__restrict__ Mlo,
       int rowstride)
 {
     constexpr int P = LU * LU * LU;
-    constexpr int CH = 32;
-    __shared__ float sU[CH][3][3][LU];
-    __shared__ float sMp[CH][10];
-    const int cell = blockIdx.x;
+    constexpr int NBC = LU * LU;
+    constexpr int NPASS = (NBC + 31) / 32;
+    __shared__ P2MAtom<LU> sA[kP2MWarps][kP2MChunk];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cell = blockIdx.x * kP2MWarps + warp;
+    if (cell >= g.ncell) return;
     const int b = start[cell], e = start[cell + 1];
-    const int node = threadIdx.x;
-    const int na_ = node / (LU * LU), nb_ = (node / LU) % LU, nc_ = node % LU;
-    float acc = 0.f;
-    for (int c0 = b; c0 < e; c0 += CH) {
-        const int na = min(CH, e - c0);
-        __syncthreads();
-        for (int it = threadIdx.x; it < na * 3; it += blockDim.x) {
+    float acc[NPASS][LU];
+#pragma unroll
+    for (int ps = 0; ps < NPASS; ++ps)
+#pragma unroll
+        for (int a = 0; a < LU; ++a) acc[ps][a] = 0.f;
+    for (int c0 = b; c0 < e; c0 += kP2MChunk) {
+        const int na = min(kP2MChunk, e - c0);
+        __syncwarp();
+        for (int it = lane; it < na * 3; it += 32) {
             const int at = it / 3, ax = it % 3;
             const float4 a0 = A0[c0 + at];
             const float l = ax == 0 ? a0.x : (ax == 1 ? a0.y : a0.z);
             float u[3][LU];
             basis_1d<LU, 3>(l * g.two_over_h, W, g.Lc, u);
+            P2MAtom<LU> &rec = sA[warp][at];
+            if (ax == 0) {
+                float *ux = reinterpret_cast<float *>(rec.ux);
 #pragma unroll
-            for (int p = 0; p < 3; ++p)
+                for (int p = 0; p < 3; ++p)
 #pragma unroll
-                for (int a = 0; a < LU; ++a) sU[at][ax][p][a] = u[p][a];
+                    for (int a = 0; a < LU; ++a) ux[p * LU + a] = u[p][a];
+            } else {
+#pragma unroll
+                for (int p = 0; p < 3; ++p)
+#pragma unroll
+                    for (int a = 0; a < LU; ++a) (ax == 1 ? rec.uy : rec.uz)[p][a] = u[p][a];
+            }
         }
-        for (int at = threadIdx.x; at < na; at += blockDim.x) {
+        for (int at = lane; at < na; at += 32) {
             const float4 a0 = A0[c0 + at], a1 = A1[c0 + at], a2 = A2[c0 + at], a3 = A3[c0 + at];
-            sMp[at][0] = a0.w;
-            sMp[at][1] = a1.x; sMp[at][2] = a1.y; sMp[at][3] = a1.z;
-            sMp[at][4] = a2.x; sMp[at][5] = 2.f * a2.y; sMp[at][6] = 2.f * a2.z;
-            sMp[at][7] = a2.w; sMp[at][8] = 2.f * a3.x; sMp[at][9] = a3.y;
+            sA[warp][at].mp[0] = make_float4(a0.w, a1.x, a1.y, a1.z);
+            sA[warp][at].mp[1] = make_float4(a2.x, 2.f * a2.y, 2.f * a2.z, a2.w);
+            sA[warp][at].mp[2] = make_float4(2.f * a3.x, a3.y, 0.f, 0.f);
         }
-        __syncthreads();
-        if (node < P) {
-            for (int at = 0; at < na; ++at) {
-                const float ux0 = sU[at][0][0][na_], ux1 = sU[at][0][1][na_], ux2 = sU[at][0][2][na_];
-                const float uy0 = sU[at][1][0][nb_], uy1 = sU[at][1][1][nb_], uy2 = sU[at][1][2][nb_];
-                const float uz0 = sU[at][2][0][nc_], uz1 = sU[at][2][1][nc_], uz2 = sU[at][2][2][nc_];
-                const float *m = sMp[at];
-                // terms of Alg. 2 grouped by the x-derivative order
-                float g0 = m[0] * uy0 * uz0 + m[2] * uy1 * uz0 + m[3] * uy0 * uz1
-                         + m[7] * uy2 * uz0 + m[8] * uy1 * uz1 + m[9] * uy0 * uz2;
-                float g1 = m[1] * uy0 * uz0 + m[5] * uy1 * uz0 + m[6] * uy0 * uz1;
-                float g2 = m[4] * uy0 * uz0;
-                acc += ux0 * g0 + ux1 * g1 + ux2 * g2;
+        __syncwarp();
+        for (int at = 0; at < na; ++at) {
+            const P2MAtom<LU> &rec = sA[warp][at];
+            const float4 m0 = rec.mp[0], m1 = rec.mp[1], m2 = rec.mp[2];
+            float ux[P2MAtom<LU>::NX * 4];
+#pragma unroll
+            for (int k = 0; k < P2MAtom<LU>::NX; ++k) {
+                const float4 v = rec.ux[k];
+                ux[4 * k] = v.x; ux[4 * k + 1] = v.y; ux[4 * k + 2] = v.z; ux[4 * k + 3] = v.w;
+            }
+#pragma unroll
+            for (int ps = 0; ps < NPASS; ++ps) {
+                const int bc = lane + 32 * ps;
+                if (bc < NBC) {
+                    const int bb = bc / LU, cc = bc % LU;
+                    const float uy0 = rec.uy[0][bb], uy1 = rec.uy[1][bb], uy2 = rec.uy[2][bb];
+                    const float uz0 = rec.uz[0][cc], uz1 = rec.uz[1][cc], uz2 = rec.uz[2][cc];
+                    const float y0z0 = uy0 * uz0;
+                    const float G0 = m0.x * y0z0 + m0.z * uy1 * uz0 + m0.w * uy0 * uz1 + m1.w * uy2 * uz0
+                                   + m2.x * uy1 * uz1 + m2.y * uy0 * uz2;
+                    const float G1 = m0.y * y0z0 + m1.y * uy1 * uz0 + m1.z * uy0 * uz1;
+                    const float G2 = m1.x * y0z0;
+#pragma unroll
+                    for (int a = 0; a < LU; ++a)
+                        acc[ps][a] += ux[a] * G0 + ux[LU + a] * G1 + ux[2 * LU + a] * G2;
+                }
             }
         }
     }
-    if (node < g.ldm) {
-        const float v = node < P ? acc : 0.f;
-        M[(int64_t)cell * g.ldm + node] = v;
+    const int n = g.n;
+    const int cz = cell % n, zr = cell / n;
+    const int64_t base = (int64_t)zr * rowstride;
+    float *Mrow = M + (int64_t)cell * g.ldm;
+    // nodes a*LU^2 + bc: this lane's column; zero padding beyond P
+#pragma unroll
+    for (int ps = 0; ps < NPASS; ++ps) {
+        const int bc = lane + 32 * ps;
+        if (bc < NBC) {
+#pragma unroll
+            for (int a = 0; a < LU; ++a) {
+                const int node = a * NBC + bc;
+                const float v = acc[ps][a];
+                Mrow[node] = v;
+                if (Mhi) {
+                    // split for the tensor-core correction: rows of each z-row with a one-leaf halo
+                    const float hi = tf32_rna(v), lo = tf32_rna(v - hi);
+                    Mhi[(base + 1 + cz) * g.ldm + node] = hi;
+                    Mlo[(base + 1 + cz) * g.ldm + node] = lo;
+                    if (cz == n - 1) {
+                        Mhi[base * g.ldm + node] = hi;
+                        Mlo[base * g.ldm + node] = lo;
+                    }
+                    if (cz == 0) {
+                        Mhi[(base + n + 1) * g.ldm + node] = hi;
+                        Mlo[(base + n + 1) * g.ldm + node] = lo;
+                    }
+                }
+            }
+        }
+    }
+    for (int node = P + lane; node < g.ldm; node += 32) {
+        Mrow[node] = 0.f;
         if (Mhi) {
-            // split for the tensor-core correction: rows of each z-row with a one-leaf halo
-            const float hi = tf32_rna(v), lo = tf32_rna(v - hi);
-            const int n = g.n;
-            const int cz = cell % n, zr = cell / n;
-            const int64_t base = (int64_t)zr * rowstride;
-            Mhi[(base + 1 + cz) * g.ldm + node] = hi;
-            Mlo[(base + 1 + cz) * g.ldm + node] = lo;
-            if (cz == n - 1) {
-                Mhi[base * g.ldm + node] = hi;
-                Mlo[base * g.ldm + node] = lo;
-            }
-            if (cz == 0) {
-                Mhi[(base + n + 1) * g.ldm + node] = hi;
-                Mlo[(base + n + 1) * g.ldm + node] = lo;
-            }
+            Mhi[(base + 1 + cz) * g.ldm + node] = 0.f;
+            Mlo[(base + 1 + cz) * g.ldm + node] = 0.f;
         }
     }
 }
@@ -155,90 +215,145 @@ __global__ void k_fine(Geo g, const float *__restrict__ M, float *__restrict__ r
     rho[idx] = s;
 }
 
-// L2P: far-field gradient of each sorted atom from the node potentials of its leaf,
-//   Pi_t[k] = phi[g(t,k)] / M - psi_t[k].
+// L2P fused with the gradient assembly, one thread per sorted atom: node
+// potentials of its leaf Pi_t[k] = phi[g(t,k)] / M - psi_t[k] (read through
+// the cache, shared by the leaf's atoms), far-field gradient by the adjoint
+// of P2M, plus the near-field gradient, the self-term gradient and the k = 0
+// potential; torques; write to the caller's atom order.
 template <int LU>
 __global__ void __launch_bounds__(128)
-k_l2p(Geo g, int N, const int *__restrict__ scell, const float4 *__restrict__ A0,
+k_l2p(Geo g, const int *__restrict__ scell, const int *__restrict__ perm, const float4 *__restrict__ A0,
       const float4 *__restrict__ A1, const float4 *__restrict__ A2, const float4 *__restrict__ A3,
-      const float *__restrict__ W, const float *__restrict__ phi, float invM,
-      const float *__restrict__ psi, float *__restrict__ gfar)
+      const float *__restrict__ W, const float *__restrict__ phi, float invM, const float *__restrict__ psi,
+      const float *__restrict__ gnear, int64_t Nslot, const double *__restrict__ terms,
+      float *__restrict__ dEdx, float *__restrict__ dEdq, float *__restrict__ dEdmu,
+      float *__restrict__ dEdth, float *__restrict__ torque)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= N) return;
+    if (s >= Nslot) return;
     const int cell = scell[s];
     const int n = g.n, nf = g.nf, Lm = LU - 1;
     const int cx = cell / (n * n), cy = (cell / n) % n, cz = cell % n;
-    const float4 a0 = A0[s], a1 = A1[s], a2 = A2[s], a3 = A3[s];
-    float ux[4][LU], uy[4][LU], uz[4][LU];
-    basis_1d<LU, 4>(a0.x * g.two_over_h, W, g.Lc, ux);
-    basis_1d<LU, 4>(a0.y * g.two_over_h, W, g.Lc, uy);
-    basis_1d<LU, 4>(a0.z * g.two_over_h, W, g.Lc, uz);
-    // V[px][py][pz] = sum_k Pi[k] ux^(px) uy^(py) uz^(pz), px + py + pz <= 3
-    float V[4][4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) V[i][j][k] = 0.f;
     const float *ps = psi + (int64_t)cell * g.ldm;
-#pragma unroll 1
-    for (int c = 0; c < LU; ++c) {
-        const int gzz = (cz * Lm + c) % nf;
-        float Y[4][4];
+    const float dcpot = (float)terms[6];
+    const float xi = g.xi;
+    {
+        const float4 a0 = A0[s], a1 = A1[s], a2 = A2[s], a3 = A3[s];
+        float ux[4][LU], uy[4][LU], uz[4][LU];
+        basis_1d<LU, 4>(a0.x * g.two_over_h, W, g.Lc, ux);
+        basis_1d<LU, 4>(a0.y * g.two_over_h, W, g.Lc, uy);
+        basis_1d<LU, 4>(a0.z * g.two_over_h, W, g.Lc, uz);
+        // V[px][py][pz] = sum_k Pi[k] ux^(px) uy^(py) uz^(pz), px + py + pz <= 3
+        float V[4][4][4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) Y[i][j] = 0.f;
+            for (int j = 0; j < 4; ++j)
 #pragma unroll
-        for (int bb = 0; bb < LU; ++bb) {
-            const int gyy = (cy * Lm + bb) % nf;
-            float X[4] = {0.f, 0.f, 0.f, 0.f};
+                for (int k = 0; k < 4; ++k) V[i][j][k] = 0.f;
 #pragma unroll
-            for (int a = 0; a < LU; ++a) {
-                const int gxx = (cx * Lm + a) % nf;
-                const float pi = __ldg(&phi[((int64_t)gxx * nf + gyy) * nf + gzz]) * invM
-                               - __ldg(&ps[(a * LU + bb) * LU + c]);
+        for (int c = 0; c < LU; ++c) {
+            float Y[4][4];
 #pragma unroll
-                for (int p = 0; p < 4; ++p) X[p] = fmaf(pi, ux[p][a], X[p]);
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) Y[i][j] = 0.f;
+#pragma unroll
+            for (int bb = 0; bb < LU; ++bb) {
+                float X[4] = {0.f, 0.f, 0.f, 0.f};
+                const int gyy = (cy * Lm + bb) % nf, gzz = (cz * Lm + c) % nf;
+#pragma unroll
+                for (int a = 0; a < LU; ++a) {
+                    const int gxx = (cx * Lm + a) % nf;
+                    const float pi = __ldg(&phi[((int64_t)gxx * nf + gyy) * nf + gzz]) * invM
+                                   - __ldg(&ps[(a * LU + bb) * LU + c]);
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) X[p] = fmaf(pi, ux[p][a], X[p]);
+                }
+#pragma unroll
+                for (int p = 0; p < 4; ++p)
+#pragma unroll
+                    for (int q = 0; q < 4 - p; ++q) Y[p][q] = fmaf(X[p], uy[q][bb], Y[p][q]);
             }
 #pragma unroll
             for (int p = 0; p < 4; ++p)
 #pragma unroll
-                for (int q = 0; q < 4 - p; ++q) Y[p][q] = fmaf(X[p], uy[q][bb], Y[p][q]);
+                for (int q = 0; q < 4 - p; ++q)
+#pragma unroll
+                    for (int r = 0; r < 4 - p - q; ++r) V[p][q][r] = fmaf(Y[p][q], uz[r][c], V[p][q][r]);
         }
+        const float q = a0.w, mx = a1.x, my = a1.y, mz = a1.z;
+        const float xx = a2.x, xy = a2.y, xz = a2.z, yy = a2.w, yz = a3.x, zz = a3.y;
+        const float txy2 = 2.f * xy, txz2 = 2.f * xz, tyz2 = 2.f * yz;
+        float gv[13];
 #pragma unroll
-        for (int p = 0; p < 4; ++p)
+        for (int ax = 0; ax < 3; ++ax) {
+            const int ex = ax == 0, ey = ax == 1, ez = ax == 2;
+            gv[ax] = q * V[ex][ey][ez] + mx * V[1 + ex][ey][ez] + my * V[ex][1 + ey][ez] + mz * V[ex][ey][1 + ez]
+                   + xx * V[2 + ex][ey][ez] + txy2 * V[1 + ex][1 + ey][ez] + txz2 * V[1 + ex][ey][1 + ez]
+                   + yy * V[ex][2 + ey][ez] + tyz2 * V[ex][1 + ey][1 + ez] + zz * V[ex][ey][2 + ez];
+        }
+        gv[3] = V[0][0][0];
+        gv[4] = V[1][0][0];
+        gv[5] = V[0][1][0];
+        gv[6] = V[0][0][1];
+        gv[7] = V[2][0][0];
+        gv[8] = 2.f * V[1][1][0];
+        gv[9] = 2.f * V[1][0][1];
+        gv[10] = V[0][2][0];
+        gv[11] = 2.f * V[0][1][1];
+        gv[12] = V[0][0][2];
 #pragma unroll
-            for (int q = 0; q < 4 - p; ++q)
+        for (int k = 0; k < 13; ++k) gv[k] += gnear[(int64_t)k * Nslot + s];
+        // self-term gradient (Eq. ewald, general symmetric Theta) and k = 0 potential
+        const float tr = xx + yy + zz;
+        const float cc = xi * 0.56418958354775628f, x2 = xi * xi, x4 = x2 * x2;
+        gv[3] += -cc * (2.f * q - (4.f * x2 / 3.f) * tr) + dcpot;
+        gv[4] += -cc * (4.f * x2 / 3.f) * mx;
+        gv[5] += -cc * (4.f * x2 / 3.f) * my;
+        gv[6] += -cc * (4.f * x2 / 3.f) * mz;
+        const float dg = -(4.f * x2 / 3.f) * q + (8.f * x4 / 5.f) * tr;
+        const float k16 = 16.f * x4 / 5.f;
+        gv[7] += -cc * (dg + k16 * xx);
+        gv[8] += -cc * 2.f * k16 * xy;
+        gv[9] += -cc * 2.f * k16 * xz;
+        gv[10] += -cc * (dg + k16 * yy);
+        gv[11] += -cc * 2.f * k16 * yz;
+        gv[12] += -cc * (dg + k16 * zz);
+        const int64_t ii = perm[s];
+        if (dEdx) {
+            dEdx[3 * ii] = gv[0];
+            dEdx[3 * ii + 1] = gv[1];
+            dEdx[3 * ii + 2] = gv[2];
+        }
+        if (dEdq) dEdq[ii] = gv[3];
+        if (dEdmu) {
+            dEdmu[3 * ii] = gv[4];
+            dEdmu[3 * ii + 1] = gv[5];
+            dEdmu[3 * ii + 2] = gv[6];
+        }
+        if (dEdth) {
 #pragma unroll
-                for (int r = 0; r < 4 - p - q; ++r) V[p][q][r] = fmaf(Y[p][q], uz[r][c], V[p][q][r]);
+            for (int k = 0; k < 6; ++k) dEdth[6 * ii + k] = gv[7 + k];
+        }
+        if (torque) {
+            // tau = -(mu x g) - 2 axial(G Theta), G = dE/dTheta with each of the nine
+            // entries independent (stored off-diagonal derivative / 2)
+            const float gx = gv[4], gy = gv[5], gz = gv[6];
+            const float G[3][3] = {{gv[7], 0.5f * gv[8], 0.5f * gv[9]},
+                                   {0.5f * gv[8], gv[10], 0.5f * gv[11]},
+                                   {0.5f * gv[9], 0.5f * gv[11], gv[12]}};
+            const float T[3][3] = {{xx, xy, xz}, {xy, yy, yz}, {xz, yz, zz}};
+            float X[3][3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) X[a][c] = G[a][0] * T[0][c] + G[a][1] * T[1][c] + G[a][2] * T[2][c];
+            torque[3 * ii] = -(my * gz - mz * gy) - 2.f * (X[2][1] - X[1][2]);
+            torque[3 * ii + 1] = -(mz * gx - mx * gz) - 2.f * (X[0][2] - X[2][0]);
+            torque[3 * ii + 2] = -(mx * gy - my * gx) - 2.f * (X[1][0] - X[0][1]);
+        }
     }
-    const float q = a0.w, mx = a1.x, my = a1.y, mz = a1.z;
-    const float txx = a2.x, txy = 2.f * a2.y, txz = 2.f * a2.z, tyy = a2.w, tyz = 2.f * a3.x, tzz = a3.y;
-    float gx_[3];
-#pragma unroll
-    for (int ax = 0; ax < 3; ++ax) {
-        const int ex = ax == 0, ey = ax == 1, ez = ax == 2;
-        gx_[ax] = q * V[ex][ey][ez] + mx * V[1 + ex][ey][ez] + my * V[ex][1 + ey][ez] + mz * V[ex][ey][1 + ez]
-                + txx * V[2 + ex][ey][ez] + txy * V[1 + ex][1 + ey][ez] + txz * V[1 + ex][ey][1 + ez]
-                + tyy * V[ex][2 + ey][ez] + tyz * V[ex][1 + ey][1 + ez] + tzz * V[ex][ey][2 + ez];
-    }
-    const int64_t S = N;
-    gfar[0 * S + s] = gx_[0];
-    gfar[1 * S + s] = gx_[1];
-    gfar[2 * S + s] = gx_[2];
-    gfar[3 * S + s] = V[0][0][0];
-    gfar[4 * S + s] = V[1][0][0];
-    gfar[5 * S + s] = V[0][1][0];
-    gfar[6 * S + s] = V[0][0][1];
-    gfar[7 * S + s] = V[2][0][0];
-    gfar[8 * S + s] = 2.f * V[1][1][0];
-    gfar[9 * S + s] = 2.f * V[1][0][1];
-    gfar[10 * S + s] = V[0][2][0];
-    gfar[11 * S + s] = 2.f * V[0][1][1];
-    gfar[12 * S + s] = V[0][0][2];
 }
 
 #define ANKH_LU_SWITCH(LUV, ...)                                   \
@@ -256,7 +371,7 @@ k_l2p(Geo g, int N, const int *__restrict__ scell, const float4 *__restrict__ A0
 cudaError_t launch_p2m(Handle &H, cudaStream_t s)
 {
     ANKH_LU_SWITCH(H.g.Lu,
-        k_p2m<LU><<<H.g.ncell, ((LU * LU * LU + 31) / 32) * 32, 0, s>>>(
+        k_p2m<LU><<<(H.g.ncell + kP2MWarps - 1) / kP2MWarps, kP2MWarps * 32, 0, s>>>(
             H.g, H.d_start, H.d_A0, H.d_A1, H.d_A2, H.d_A3, H.d_W, H.d_M,
             H.tc.enabled ? H.d_Mhi : nullptr, H.tc.enabled ? H.d_Mlo : nullptr, H.tc.rowstride));
     return cudaGetLastError();
@@ -269,13 +384,15 @@ cudaError_t launch_fine_gather(Handle &H, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_l2p(Handle &H, cudaStream_t s)
+cudaError_t launch_l2p(Handle &H, float *dEdx, float *dEdq, float *dEdmu, float *dEdtheta, float *torque,
+                       cudaStream_t s)
 {
-    const int N = (int)H.N;
     const float invM = (float)(1.0 / (double)H.g.M);
+    const int nb = (int)((H.N + 127) / 128);
     ANKH_LU_SWITCH(H.g.Lu,
-        k_l2p<LU><<<(N + 127) / 128, 128, 0, s>>>(H.g, N, H.d_scell, H.d_A0, H.d_A1, H.d_A2,
-                                                   H.d_A3, H.d_W, H.d_phi, invM, H.d_psi, H.d_gfar));
+        k_l2p<LU><<<nb, 128, 0, s>>>(H.g, H.d_scell, H.d_perm, H.d_A0, H.d_A1, H.d_A2, H.d_A3, H.d_W,
+                                                H.d_phi, invM, H.d_psi, H.d_gnear, H.N, H.d_terms, dEdx, dEdq,
+                                                dEdmu, dEdtheta, torque));
     return cudaGetLastError();
 }
 

@@ -80,6 +80,63 @@ __global__ void k_scan(int ncell, const int *__restrict__ count, int *__restrict
     if (tid == nt - 1) start[ncell] = excl;
 }
 
+// Multi-block exclusive scan: (1) per-block totals, (2) every block adds the
+// totals of the blocks before it and scans its own 1024 counts.
+__device__ __forceinline__ int block_excl_scan_1024(int v, int *warp_tot, int *total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += t;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int w = warp_tot[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        warp_tot[lane] = w;
+    }
+    __syncthreads();
+    *total = warp_tot[31];
+    return x - v + (wid > 0 ? warp_tot[wid - 1] : 0);
+}
+
+__global__ void __launch_bounds__(1024) k_scan_totals(int ncell, const int *__restrict__ count, int *__restrict__ bsum)
+{
+    __shared__ int wt[32];
+    const int i = blockIdx.x * 1024 + threadIdx.x;
+    int tot;
+    block_excl_scan_1024(i < ncell ? count[i] : 0, wt, &tot);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_apply(int ncell, const int *__restrict__ count,
+                                                     const int *__restrict__ bsum, int *__restrict__ start)
+{
+    __shared__ int wt[32];
+    __shared__ int base;
+    if (threadIdx.x < 32) {
+        int s = 0;
+        for (int b = threadIdx.x; b < (int)blockIdx.x; b += 32) s += bsum[b];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) base = s;
+    }
+    const int i = blockIdx.x * 1024 + threadIdx.x;
+    const int c = i < ncell ? count[i] : 0;
+    int tot;
+    const int ex = block_excl_scan_1024(c, wt, &tot);
+    __syncthreads();
+    if (i < ncell) start[i] = base + ex;
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 1023) start[ncell] = base + tot;
+}
+
 __global__ void k_scatter(int N, const int *__restrict__ cellid, const int *__restrict__ rank,
                           const int *__restrict__ start, int *__restrict__ perm)
 {
@@ -107,15 +164,29 @@ __global__ void k_leafsort(int ncell, const int *__restrict__ start, int *__rest
 
 // Gather the atoms into leaf order; coordinates relative to the leaf centre
 // (computed in FP64, rounded once to FP32).
-__global__ void k_gather(int N, const int *__restrict__ perm, const float *__restrict__ x,
-                         const float *__restrict__ q, const float *__restrict__ mu,
-                         const float *__restrict__ th, Geo g, int *__restrict__ scell,
-                         float4 *__restrict__ A0, float4 *__restrict__ A1, float4 *__restrict__ A2,
-                         float4 *__restrict__ A3)
+// Self term of Eq. ewald per atom (general symmetric Theta), FP32:
+//   -(xi/sqrt(pi)) [q^2 + (2xi^2/3)|mu|^2 - (4xi^2/3) q tr + (8xi^4/5) Theta:Theta + (4xi^4/5) tr^2]
+__device__ __forceinline__ float self_energy_atom(float q, float mx, float my, float mz, const float *t, float xi)
 {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= N) return;
-    int i = perm[s];
+    const float c = xi * 0.56418958354775628f, a2 = xi * xi, a4 = a2 * a2;
+    const float tr = t[0] + t[3] + t[5];
+    const float TT = t[0] * t[0] + t[3] * t[3] + t[5] * t[5] + 2.f * (t[1] * t[1] + t[2] * t[2] + t[4] * t[4]);
+    return -c * (q * q + (2.f * a2 / 3.f) * (mx * mx + my * my + mz * mz) - (4.f * a2 / 3.f) * q * tr
+                 + (8.f * a4 / 5.f) * TT + (4.f * a4 / 5.f) * tr * tr);
+}
+
+__global__ void __launch_bounds__(256)
+k_gather(int N, const int *__restrict__ perm, const float *__restrict__ x,
+         const float *__restrict__ q, const float *__restrict__ mu,
+         const float *__restrict__ th, Geo g, int *__restrict__ scell,
+         float4 *__restrict__ A0, float4 *__restrict__ A1, float4 *__restrict__ A2,
+         float4 *__restrict__ A3, double *__restrict__ part_self, double *__restrict__ part_q)
+{
+    __shared__ double sh1[8], sh2[8];
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    double es = 0.0, qs = 0.0;
+    if (s < N) {
+    const int i = perm[s];
     float l[3];
     int c[3];
 #pragma unroll
@@ -128,16 +199,41 @@ __global__ void k_gather(int N, const int *__restrict__ perm, const float *__res
         l[a] = (float)loc;
     }
     scell[s] = (c[0] * g.n + c[1]) * g.n + c[2];
-    A0[s] = make_float4(l[0], l[1], l[2], q[i]);
-    if (mu) A1[s] = make_float4(mu[3 * (int64_t)i], mu[3 * (int64_t)i + 1], mu[3 * (int64_t)i + 2], 0.f);
-    else A1[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float qi = q[i];
+    A0[s] = make_float4(l[0], l[1], l[2], qi);
+    float m3[3] = {0.f, 0.f, 0.f}, t6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (mu) {
+        m3[0] = mu[3 * (int64_t)i]; m3[1] = mu[3 * (int64_t)i + 1]; m3[2] = mu[3 * (int64_t)i + 2];
+    }
     if (th) {
         const float *t = th + 6 * (int64_t)i;
-        A2[s] = make_float4(t[0], t[1], t[2], t[3]);
-        A3[s] = make_float4(t[4], t[5], 0.f, 0.f);
-    } else {
-        A2[s] = make_float4(0.f, 0.f, 0.f, 0.f);
-        A3[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) t6[k] = t[k];
+    }
+    A1[s] = make_float4(m3[0], m3[1], m3[2], 0.f);
+    A2[s] = make_float4(t6[0], t6[1], t6[2], t6[3]);
+    A3[s] = make_float4(t6[4], t6[5], 0.f, 0.f);
+    es = (double)self_energy_atom(qi, m3[0], m3[1], m3[2], t6, g.xi);
+    qs = (double)qi;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        es += __shfl_down_sync(0xffffffffu, es, o);
+        qs += __shfl_down_sync(0xffffffffu, qs, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sh1[threadIdx.x >> 5] = es;
+        sh2[threadIdx.x >> 5] = qs;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double u = 0.0, v = 0.0;
+        for (int w = 0; w < 8; ++w) {
+            u += sh1[w];
+            v += sh2[w];
+        }
+        part_self[blockIdx.x] = u;
+        part_q[blockIdx.x] = v;
     }
 }
 
@@ -152,7 +248,9 @@ cudaError_t launch_bin(Handle &H, const float *x, cudaStream_t s)
 
 cudaError_t launch_scan(Handle &H, cudaStream_t s)
 {
-    k_scan<<<1, 1024, 0, s>>>(H.g.ncell, H.d_count, H.d_start);
+    const int nb = (H.g.ncell + 1023) / 1024;
+    k_scan_totals<<<nb, 1024, 0, s>>>(H.g.ncell, H.d_count, H.d_bsum);
+    k_scan_apply<<<nb, 1024, 0, s>>>(H.g.ncell, H.d_count, H.d_bsum, H.d_start);
     return cudaGetLastError();
 }
 
@@ -164,7 +262,8 @@ cudaError_t launch_scatter_sort_gather(Handle &H, const float *x, const float *q
     k_leafsort<<<(H.g.ncell + 127) / 128, 128, 0, s>>>(H.g.ncell, H.d_start, H.d_perm);
     k_gather<<<(N + 255) / 256, 256, 0, s>>>(N, H.d_perm, x, q, H.max_order >= 1 ? mu : nullptr,
                                               H.max_order >= 2 ? theta : nullptr, H.g, H.d_scell,
-                                              H.d_A0, H.d_A1, H.d_A2, H.d_A3);
+                                              H.d_A0, H.d_A1, H.d_A2, H.d_A3, H.d_part + H.part_off[kPartSelf],
+                                              H.d_part + H.part_off[kPartQ]);
     return cudaGetLastError();
 }
 
