@@ -7,7 +7,7 @@
 #include <cstdint>
 #include <string>
 
-#include "../../include/ankh.h"
+#include "ankh.h"
 
 namespace ankh {
 

@@ -326,20 +326,34 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
             }
         }
         if (ok) {
+            // energy dot and psi: M loads issued 16 at a time (independent), FP32
+            // partial sums per thread (128 products), FP64 across threads
             const int m = warp * 32 + lane;
             const int ldm = g.ldm;
+            float e0 = 0.f, e1 = 0.f;
 #pragma unroll
-            for (int c = 0; c < 128; ++c) {
-                if (c < N) {
-                    const int slab = c / S, z = c % S;
-                    const int zrow = blockIdx.x * R + slab;
-                    if (z < n && zrow < nrow) {
-                        const int64_t cell = (int64_t)zrow * n + z;
-                        e += (double)M[cell * ldm + m] * (double)acc[c];
-                        if (FORCES) psi[cell * ldm + m] = acc[c];
+            for (int c0 = 0; c0 < 128; c0 += 16) {
+                if (c0 < N) {
+                    float mv[16];
+                    int64_t ofs[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int c = c0 + j;
+                        const int slab = c / S, z = c % S;
+                        const int zrow = blockIdx.x * R + slab;
+                        const bool valid = (c < N) && (z < n) && (zrow < nrow);
+                        ofs[j] = valid ? ((int64_t)zrow * n + z) * ldm + m : -1;
+                        mv[j] = valid ? __ldg(&M[ofs[j]]) : 0.f;
+                    }
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        if (j & 1) e1 = fmaf(mv[j], acc[c0 + j], e1);
+                        else e0 = fmaf(mv[j], acc[c0 + j], e0);
+                        if (FORCES && ofs[j] >= 0) psi[ofs[j]] = acc[c0 + j];
                     }
                 }
             }
+            e = (double)e0 + (double)e1;
         } else {
             *abort_flag = 1;
         }
