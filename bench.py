@@ -176,7 +176,7 @@ def main():
     ap.add_argument("--plain", action="store_true", help="plain FP32 adjacent-leaf correction")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
-    ap.add_argument("--n-cells", type=int, default=0, help="leaves per axis (0 = library choice)")
+    ap.add_argument("--n-cells", type=int, default=0, help="leaves per axis (0 = autotuned)")
     args = ap.parse_args()
 
     rank, world, local = env_int("RANK", 0), env_int("WORLD_SIZE", 1), env_int("LOCAL_RANK", 0)
@@ -206,12 +206,19 @@ def main():
         synth.CONFIGS[cfg]["n_waters"], synth.SEED_BASE + cfg + 1000 * rank, multipoles=True,
         name=synth.CONFIGS[cfg]["name"])
     N = box.n
-    t_pre0 = time.perf_counter()
-    model = api.Ankh(box.box, N, n_cells=args.n_cells, Lu=5, Lc=5, mixed=not args.plain)
-    t_pre = time.perf_counter() - t_pre0
-    info = model.info
     f32 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
     x, q, mu, th = f32(box.x), f32(box.q), f32(box.mu), f32(box.theta)
+    tune = None
+    n_cells = args.n_cells
+    if n_cells == 0:
+        # leaf count picked by measurement (outside the timed region)
+        from paper_2212_08284_gb300 import autotune
+        n_cells, tab = autotune.autotune_n(box.box, x, q, mu, th, Lu=5, Lc=5, mixed=not args.plain)
+        tune = {str(k): round(v, 4) for k, v in sorted(tab.items())}
+    t_pre0 = time.perf_counter()
+    model = api.Ankh(box.box, N, n_cells=n_cells, Lu=5, Lc=5, mixed=not args.plain)
+    t_pre = time.perf_counter() - t_pre0
+    info = model.info
     out = {"dEdx": torch.empty((N, 3), device=dev), "dEdq": torch.empty(N, device=dev),
            "dEdmu": torch.empty((N, 3), device=dev), "dEdtheta": torch.empty((N, 6), device=dev),
            "torque": torch.empty((N, 3), device=dev)}
@@ -332,7 +339,8 @@ def main():
             "config": {"workload": box.name + "_energy_forces", "n_atoms": N, "box_A": round(box.box, 4),
                        "n_cells": n, "Lu": info["Lu"], "Lc": info["Lc"], "nf": info["nf"], "xi": 0.01,
                        "precision": "plain_fp32" if args.plain else "mixed_3xtf32_correction",
-                       "l2": "flushed: 256 MiB write between timed steps", "parallelism": f"replicas{world}"},
+                       "l2": "flushed: 256 MiB write between timed steps", "parallelism": f"replicas{world}",
+                       "leaf_count": "autotuned" if args.n_cells == 0 else "fixed", "autotune_ms": tune},
             "matoms_per_s": value * N / 1e6,
             "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
             "near_pairs_unordered": pairs,

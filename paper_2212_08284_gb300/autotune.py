@@ -1,0 +1,59 @@
+"""Leaf-size autotuner.
+
+The ANKH error is scale-free in the leaf edge h (xi h << 1), so the number
+of leaves per axis n only trades work: near-field pairs grow like h^3, the
+adjacent-leaf correction, the merged FFT grid and the P2M/L2P node work like
+h^-3, and the near-field kernel's lane use depends on the atoms per leaf.
+The autotuner measures one full energy + gradient evaluation on the device
+(CUDA events around the library call) for candidate n around a 4.0 A leaf
+edge and returns the fastest.  Results are cached per (box, N, orders,
+precision) for the life of the process.
+"""
+from __future__ import annotations
+
+import math
+
+from . import api
+
+_cache: dict = {}
+
+
+def candidates(box: float, spread: int = 4, h0: float = 4.0) -> list[int]:
+    n0 = max(3, int(round(box / h0)))
+    return sorted({max(3, n0 + d) for d in range(-spread, spread + 1)})
+
+
+def autotune_n(box: float, x, q, mu=None, theta=None, Lu: int = 5, Lc: int = 0, mixed: bool = True,
+               max_order: int = 2, cands: list[int] | None = None, reps: int = 4, warm: int = 2):
+    """Return (best n, {n: milliseconds per evaluation})."""
+    import torch
+    key = (round(box, 6), int(x.shape[0]), Lu, Lc, mixed, max_order)
+    if key in _cache:
+        return _cache[key]
+    n_atoms = int(x.shape[0])
+    dev = x.device
+    out = {"dEdx": torch.empty((n_atoms, 3), device=dev), "dEdq": torch.empty(n_atoms, device=dev),
+           "dEdmu": torch.empty((n_atoms, 3), device=dev), "dEdtheta": torch.empty((n_atoms, 6), device=dev)}
+    table = {}
+    stream = torch.cuda.current_stream()
+    for n in (cands or candidates(box)):
+        try:
+            m = api.Ankh(box, n_atoms, n_cells=n, Lu=Lu, Lc=Lc, mixed=mixed, max_order=max_order)
+        except api.AnkhError:
+            continue
+        for _ in range(warm):
+            api.ankh_energy_forces(m.h, x, q, mu, theta, sync=False, stream=stream, **out)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            api.ankh_energy_forces(m.h, x, q, mu, theta, sync=False, stream=stream, **out)
+        e1.record(stream)
+        e1.synchronize()
+        table[n] = e0.elapsed_time(e1) / reps
+        m.close()
+    if not table:
+        raise RuntimeError("no candidate leaf count could be created")
+    best = min(table, key=table.get)
+    _cache[key] = (best, table)
+    return best, table

@@ -153,9 +153,10 @@ static bool good_fft_size(int m)
 
 static int choose_n(double box, int Lu)
 {
-    // leaf edge near 4.4 A for L_u = 5 (balances near-field pairs and
-    // correction work); prefer a merged grid size with small prime factors
-    const double target = 4.4;
+    // leaf edge near 4.0 A for L_u = 5 (balances near-field pairs against
+    // correction and grid work, measured on the 1M-atom water box); prefer a
+    // merged grid size with small prime factors
+    const double target = 4.0;
     int n0 = std::max(3, (int)std::lround(box / target));
     int best = n0;
     for (int dn = 0; dn <= 3; ++dn) {

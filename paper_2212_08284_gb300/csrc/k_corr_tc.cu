@@ -19,7 +19,7 @@
 //
 // The tensor core rounds toward zero as it accumulates; over the 27 x 48 MMA
 // steps of a tile that bias reaches ~4e-5.  So the large C_hi.M_hi products
-// of one stage (K = 32, four MMAs) go to one of two TMEM buffers and are
+// of one stage (K = 32, four MMAs) go to one of three TMEM buffers and are
 // drained after the stage into FP32 registers with round-to-nearest
 // additions, while the next stage accumulates into the other buffer.  The
 // small C_hi.M_lo + C_lo.M_hi corrections (2^-11 of the large ones) stay in a
@@ -38,6 +38,7 @@ namespace ankh {
 namespace tcg {
 
 constexpr int kStages = 3;
+constexpr int kAccBufs = 3;            // large-product accumulator buffers in TMEM
 constexpr int kRows = 128;            // target nodes (ldm)
 constexpr int kKc = 32;               // K floats per stage (128 bytes)
 constexpr int kIters = 27 * (kRows / kKc);
@@ -176,9 +177,9 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
     const uint32_t stage = 2 * kABytes + 2 * bbytes;
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStages * stage);
     uint64_t *empty = full + kStages;
-    uint64_t *acc_full = empty + kStages;     // [2] accumulator buffer ready for draining
-    uint64_t *acc_empty = acc_full + 2;       // [2] accumulator buffer drained (4 warp arrivals)
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
+    uint64_t *acc_full = empty + kStages;     // [kAccBufs] accumulator buffer ready for draining
+    uint64_t *acc_empty = acc_full + kAccBufs; // [kAccBufs] buffer drained (4 warp arrivals)
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + kAccBufs);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     volatile int *issued = abort_flag + 1;
     __shared__ double red[4];
@@ -189,7 +190,7 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < kAccBufs; ++b) {
             mbar_init(&acc_full[b], 1);
             mbar_init(&acc_empty[b], 4);
         }
@@ -239,11 +240,12 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
         // MMA issuer: large products of each stage into one of two TMEM buffers
         // (drained by the epilogue warps), small corrections into a third one
         const uint32_t idesc = idesc_tf32(kRows, N);
-        const uint32_t small = tmem + (uint32_t)(2 * N);
+        const uint32_t small = tmem + (uint32_t)(kAccBufs * N);
         int consumed = 0;
         for (int it = 0; it < kIters; ++it) {
-            const int s = it % kStages, k = it / kStages, buf = it & 1;
-            if (it >= 2 && !mbar_wait(&acc_empty[buf], (uint32_t)(((it >> 1) - 1) & 1), kBudget)) {
+            const int s = it % kStages, k = it / kStages, buf = it % kAccBufs;
+            if (it >= kAccBufs &&
+                !mbar_wait(&acc_empty[buf], (uint32_t)(((it / kAccBufs) - 1) & 1), kBudget)) {
                 *abort_flag = 1;
                 break;
             }
@@ -268,8 +270,7 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
         }
         if (*abort_flag) {
             // release the epilogue and let every copy this CTA issued land
-            mma_commit(&acc_full[0]);
-            mma_commit(&acc_full[1]);
+            for (int b = 0; b < kAccBufs; ++b) mma_commit(&acc_full[b]);
             const int nis = *issued;
             for (int it = consumed; it < nis; ++it)
                 mbar_wait(&full[it % kStages], (uint32_t)((it / kStages) & 1), kBudget);
@@ -284,8 +285,8 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
         bool ok = true;
         const uint32_t lanebase = tmem + ((uint32_t)(warp * 32) << 16);
         for (int it = 0; it < kIters; ++it) {
-            const int buf = it & 1;
-            bool w = mbar_wait(&acc_full[buf], (uint32_t)((it >> 1) & 1), 2 * kBudget);
+            const int buf = it % kAccBufs;
+            bool w = mbar_wait(&acc_full[buf], (uint32_t)((it / kAccBufs) & 1), 2 * kBudget);
             ok = __all_sync(0xffffffffu, w && !*abort_flag);
             if (!ok) break;
             fence_after();
@@ -313,7 +314,7 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
         if (ok) {
             // the small corrections, accumulated in TMEM over the whole tile (the
             // last acc_full arrival follows every MMA of the tile)
-            const uint32_t ts = lanebase + (uint32_t)(2 * N);
+            const uint32_t ts = lanebase + (uint32_t)(kAccBufs * N);
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 if (c * 32 < N) {
@@ -424,7 +425,7 @@ bool tc_prepare(Handle &H, std::string &err)
     H.tc.rowstride = S + 2;
     H.tc.N = R * S;
     H.tc.tmem_cols = 32;
-    while ((int)H.tc.tmem_cols < 3 * H.tc.N) H.tc.tmem_cols <<= 1;   // 2 large buffers + 1 small
+    while ((int)H.tc.tmem_cols < (tcg::kAccBufs + 1) * H.tc.N) H.tc.tmem_cols <<= 1;   // large buffers + small
     H.tc.tiles = (g.n * g.n + R - 1) / R;
     const uint64_t rows = (uint64_t)g.n * g.n * H.tc.rowstride;
     if (!encode_2d(&H.tc.mAhi, H.d_Chi, 27 * 128, 128, tcg::kKc, 128, err)) return false;

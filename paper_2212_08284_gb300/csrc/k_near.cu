@@ -6,13 +6,15 @@
 //   N_real = 1/2 sum_i sum_k e_ik.
 //
 // Source-field formulation: each target i accumulates, over all its near
-// sources k, the potential V_k and its derivatives up to third order,
-//   V, dV_a, G_ab = d_a d_b V, T_abc = d_a d_b d_c V,
-// which depend on the source's multipoles only.  The target's multipoles
-// enter once per atom at the end:
+// sources k, the potential V_k and its first two derivatives,
+//   V, dV_a, G_ab = d_a d_b V,
+// which depend on the source's multipoles only, and the quadrupole part of
+// its force, F_c = sum_ab Theta_i,ab T_abc with T_abc = d_a d_b d_c V
+// (contracted per pair, cheaper than accumulating the ten T_abc).  The rest
+// of the target's multipoles enter once per atom at the end:
 //   e_i = q_i V + mu_i.dV + Theta_i:G,       dE/dq_i = V, dE/dmu_i = dV,
 //   dE/dTheta_i = G (stored-entry convention),
-//   dE/dx_i = q_i dV + mu_i.G + Theta_i:T.
+//   dE/dx_i = q_i dV + mu_i.G + F.
 // With B_0 = H, B_l = -(1/r) dB_{l-1}/dr (upward recurrence
 // B_l = [(2l-1) B_{l-1} + (2 xi^2)^l exp(-xi^2 r^2)/(xi sqrt(pi))]/r^2) and
 // s = mu_k.r - tr Theta_k, u = r.Theta_k.r, Q = Theta_k r:
@@ -20,9 +22,11 @@
 //   A    = -(q B1 + s B2 + u B3),  A2 = q B2 + s B3 + u B4,  A3 = q B3 + s B4 + u B5
 //   dV_a = mu_a B1 + 2 Q_a B2 + r_a A
 //   G_ab = delta_ab A + r_a r_b A2 - (r_a P_b + r_b P_a) + 2 Theta_ab B2,   P = mu B2 + 2 Q B3
-//   T_abc = sym3(delta_ab W_c) - r_a r_b r_c A3 + sym3(r_a r_b Z_c) - 2 B3 sym3(Theta_ab r_c),
-//           W = r A2 - mu B2 - 2 Q B3,  Z = mu B3 + 2 Q B4
-// (sym3 sums the three distinct placements of the index pair).
+//   T_abc = sym3(delta_ab W_c) - r_a r_b r_c A3 + sym3(r_a r_b Z_c) - sym3(Y_ab r_c),
+//           W = r A2 - mu B2 - 2 Q B3,  Z = mu B3 + 2 Q B4,  Y = 2 B3 Theta_k
+// (sym3 sums the three distinct placements of the index pair), so with
+// R = Theta_i r, u_i = r.R:
+//   F = tr(Theta_i) W + 2 Theta_i W + u_i (Z - r A3) + r (2 R.Z - Theta_i:Y) - 2 Y R.
 //
 // Work layout: one warp per target leaf.  The atoms of the 27 leaves around
 // it are staged in shared memory (chunks of 64, coordinates shifted by the
@@ -46,12 +50,16 @@ constexpr int kNearChunk = 64;
 
 template <bool FORCES>
 struct NAcc {
-    static constexpr int K = FORCES ? 20 : 10;   // V, dV(3), G(6) [, T(10)]
+    static constexpr int K = FORCES ? 13 : 10;   // V, dV(3), G(6) [, F(3)]
+};
+
+struct TgtQ {
+    float xx, xy, xz, yy, yz, zz, tr;            // target quadrupole
 };
 
 template <bool FORCES, bool SERIES>
 __device__ __forceinline__ void src_fields(float rx, float ry, float rz, const float4 s0, const float4 s1,
-                                           const float4 s2, const float4 s3, const BCoef &bc,
+                                           const float4 s2, const float4 s3, const BCoef &bc, const TgtQ &T,
                                            float (&acc)[NAcc<FORCES>::K])
 {
     const float r2 = rx * rx + ry * ry + rz * rz;
@@ -103,20 +111,24 @@ __device__ __forceinline__ void src_fields(float rx, float ry, float rz, const f
         const float twoB4 = 2.f * B4;
         const float Wx = rxA2 - Px, Wy = ryA2 - Py, Wz = rzA2 - Pz;   // r A2 - mu B2 - 2 Q B3
         const float Zx = mx * B3 + twoB4 * Qx, Zy = my * B3 + twoB4 * Qy, Zz = mz * B3 + twoB4 * Qz;
-        const float Yxx = twoB3 * txx, Yxy = twoB3 * txy, Yxz = twoB3 * txz;
-        const float Yyy = twoB3 * tyy, Yyz = twoB3 * tyz, Yzz = twoB3 * tzz;
-        const float xx = rx * rx, yy = ry * ry, zz = rz * rz, xy = rx * ry, xz = rx * rz, yz = ry * rz;
-        // T_abc, a <= b <= c: xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz
-        acc[10] += 3.f * Wx - xx * rx * A3 + 3.f * xx * Zx - 3.f * Yxx * rx;
-        acc[11] += Wy - xx * ry * A3 + xx * Zy + 2.f * xy * Zx - (Yxx * ry + 2.f * Yxy * rx);
-        acc[12] += Wz - xx * rz * A3 + xx * Zz + 2.f * xz * Zx - (Yxx * rz + 2.f * Yxz * rx);
-        acc[13] += Wx - yy * rx * A3 + yy * Zx + 2.f * xy * Zy - (Yyy * rx + 2.f * Yxy * ry);
-        acc[14] += -xy * rz * A3 + xy * Zz + xz * Zy + yz * Zx - (Yxy * rz + Yxz * ry + Yyz * rx);
-        acc[15] += Wx - zz * rx * A3 + zz * Zx + 2.f * xz * Zz - (Yzz * rx + 2.f * Yxz * rz);
-        acc[16] += 3.f * Wy - yy * ry * A3 + 3.f * yy * Zy - 3.f * Yyy * ry;
-        acc[17] += Wz - yy * rz * A3 + yy * Zz + 2.f * yz * Zy - (Yyy * rz + 2.f * Yyz * ry);
-        acc[18] += Wy - zz * ry * A3 + zz * Zy + 2.f * yz * Zz - (Yzz * ry + 2.f * Yyz * rz);
-        acc[19] += 3.f * Wz - zz * rz * A3 + 3.f * zz * Zz - 3.f * Yzz * rz;
+        // R = Theta_i r, u_i = r.R
+        const float Rx = T.xx * rx + T.xy * ry + T.xz * rz;
+        const float Ry = T.xy * rx + T.yy * ry + T.yz * rz;
+        const float Rz = T.xz * rx + T.yz * ry + T.zz * rz;
+        const float ui = rx * Rx + ry * Ry + rz * Rz;
+        // Theta_i W, Theta_k R, Theta_i : Theta_k
+        const float TWx = T.xx * Wx + T.xy * Wy + T.xz * Wz;
+        const float TWy = T.xy * Wx + T.yy * Wy + T.yz * Wz;
+        const float TWz = T.xz * Wx + T.yz * Wy + T.zz * Wz;
+        const float KRx = txx * Rx + txy * Ry + txz * Rz;
+        const float KRy = txy * Rx + tyy * Ry + tyz * Rz;
+        const float KRz = txz * Rx + tyz * Ry + tzz * Rz;
+        const float TK = T.xx * txx + T.yy * tyy + T.zz * tzz + 2.f * (T.xy * txy + T.xz * txz + T.yz * tyz);
+        const float sc = 2.f * (Rx * Zx + Ry * Zy + Rz * Zz) - twoB3 * TK - ui * A3;
+        const float fourB3 = 2.f * twoB3;
+        acc[10] += T.tr * Wx + 2.f * TWx + ui * Zx + rx * sc - fourB3 * KRx;
+        acc[11] += T.tr * Wy + 2.f * TWy + ui * Zy + ry * sc - fourB3 * KRy;
+        acc[12] += T.tr * Wz + 2.f * TWz + ui * Zz + rz * sc - fourB3 * KRz;
     }
 }
 
@@ -168,6 +180,12 @@ k_near(Geo g, const int *__restrict__ start, const float4 *__restrict__ A0, cons
             const bool active = grp < G;
             const int si = tb + t0 + il;
             const float4 ti = A0[si];
+            TgtQ TQ;
+            {
+                const float4 t2 = A2[si], t3 = A3[si];
+                TQ.xx = t2.x; TQ.xy = t2.y; TQ.xz = t2.z; TQ.yy = t2.w; TQ.yz = t3.x; TQ.zz = t3.y;
+                TQ.tr = t2.x + t2.w + t3.y;
+            }
             float acc[K];
 #pragma unroll
             for (int k = 0; k < K; ++k) acc[k] = 0.f;
@@ -203,7 +221,7 @@ k_near(Geo g, const int *__restrict__ start, const float4 *__restrict__ A0, cons
                         if (sSlot[warp][k] == si) continue;
                         const float4 s0 = sSrc[warp][k][0];
                         src_fields<FORCES, SERIES>(ti.x - s0.x, ti.y - s0.y, ti.z - s0.z, s0, sSrc[warp][k][1],
-                                                   sSrc[warp][k][2], sSrc[warp][k][3], bc, acc);
+                                                   sSrc[warp][k][2], sSrc[warp][k][3], bc, TQ, acc);
                     }
                 }
             }
@@ -228,18 +246,13 @@ k_near(Geo g, const int *__restrict__ start, const float4 *__restrict__ A0, cons
                 ew += 0.5 * (double)ei;
                 if (FORCES) {
                     const int64_t S = Nslot;
-                    // dE/dx = q dV + mu.G + Theta:T
+                    // dE/dx = q dV + mu.G + F
                     const float Gm[3][3] = {{acc[4], acc[5], acc[6]}, {acc[5], acc[7], acc[8]}, {acc[6], acc[8], acc[9]}};
-                    const float Tm[3][6] = {{acc[10], acc[11], acc[12], acc[13], acc[14], acc[15]},
-                                            {acc[11], acc[13], acc[14], acc[16], acc[17], acc[18]},
-                                            {acc[12], acc[14], acc[15], acc[17], acc[18], acc[19]}};
-                    // T_c(ab) in the order xx xy xz yy yz zz
                     const float mu[3] = {mx, my, mz};
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        float f = q * acc[1 + c] + mu[0] * Gm[0][c] + mu[1] * Gm[1][c] + mu[2] * Gm[2][c];
-                        f += txx * Tm[c][0] + 2.f * txy * Tm[c][1] + 2.f * txz * Tm[c][2] + tyy * Tm[c][3] +
-                             2.f * tyz * Tm[c][4] + tzz * Tm[c][5];
+                        const float f = q * acc[1 + c] + mu[0] * Gm[0][c] + mu[1] * Gm[1][c] + mu[2] * Gm[2][c]
+                                      + acc[10 + c];
                         gnear[(int64_t)c * S + si] = f;
                     }
                     gnear[3 * S + si] = acc[0];
