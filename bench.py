@@ -177,6 +177,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--n-cells", type=int, default=0, help="leaves per axis (0 = autotuned)")
+    ap.add_argument("--Lu", type=int, default=5, help="equispaced interpolation order")
     args = ap.parse_args()
 
     rank, world, local = env_int("RANK", 0), env_int("WORLD_SIZE", 1), env_int("LOCAL_RANK", 0)
@@ -213,10 +214,10 @@ def main():
     if n_cells == 0:
         # leaf count picked by measurement (outside the timed region)
         from paper_2212_08284_gb300 import autotune
-        n_cells, tab = autotune.autotune_n(box.box, x, q, mu, th, Lu=5, Lc=5, mixed=not args.plain)
+        n_cells, tab = autotune.autotune_n(box.box, x, q, mu, th, Lu=args.Lu, Lc=args.Lu, mixed=not args.plain)
         tune = {str(k): round(v, 4) for k, v in sorted(tab.items())}
     t_pre0 = time.perf_counter()
-    model = api.Ankh(box.box, N, n_cells=n_cells, Lu=5, Lc=5, mixed=not args.plain)
+    model = api.Ankh(box.box, N, n_cells=n_cells, Lu=args.Lu, Lc=args.Lu, mixed=not args.plain)
     t_pre = time.perf_counter() - t_pre0
     info = model.info
     out = {"dEdx": torch.empty((N, 3), device=dev), "dEdq": torch.empty(N, device=dev),

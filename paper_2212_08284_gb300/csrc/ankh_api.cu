@@ -368,9 +368,10 @@ int ankh_create(double box_edge, int64_t N, const ankh_params *params, ankh_hand
     nb[kPartNear] = near_blocks(H);
     nb[kPartGlob] = spectral_blocks(H);
     {
-        // tensor-core tiles: ceil(n^2 / R) with R z-rows of S = roundup16(n) leaves
+        // tensor-core tiles: ceil(n^2 / R) z-row groups (S = roundup16(n) leaves each)
+        // times the 128-row slices of the ldm target nodes
         const int S = ((n + 15) / 16) * 16, R = std::max(1, 128 / S);
-        nb[kPartCorr] = std::max(corr_blocks(H), (n * n + R - 1) / R);
+        nb[kPartCorr] = std::max(corr_blocks(H), ((n * n + R - 1) / R) * ((g.ldm + 127) / 128));
     }
     nb[kPartSelf] = self_blocks(H);
     nb[kPartQ] = self_blocks(H);
@@ -398,25 +399,27 @@ int ankh_create(double box_edge, int64_t N, const ankh_params *params, ankh_hand
         if (cudaMemcpy(H.d_C, Cf.data(), Cf.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
             return bail(ANKH_ECUDA, "upload C");
     }
-    if ((p.flags & ANKH_MIXED) && g.ldm == 128 && n <= 128) {
+    if ((p.flags & ANKH_MIXED) && g.ldm % 32 == 0 && g.ldm <= 512 && n <= 128) {
         const int S = ((n + 15) / 16) * 16;
         const int64_t rows = (int64_t)n * n * (S + 2);
-        ANKH_AL(H.d_Mhi, rows * 128);
-        ANKH_AL(H.d_Mlo, rows * 128);
-        ANKH_AL(H.d_Chi, (int64_t)27 * 128 * 128);
-        ANKH_AL(H.d_Clo, (int64_t)27 * 128 * 128);
-        cudaMemset(H.d_Mhi, 0, sizeof(float) * rows * 128);
-        cudaMemset(H.d_Mlo, 0, sizeof(float) * rows * 128);
-        // A = [C_0 | ... | C_26] as [128 rows][27*128], split hi/lo (round to nearest TF32)
+        const int halves = (g.ldm + 127) / 128;
+        const int64_t acols = (int64_t)27 * g.ldm, arows = (int64_t)halves * 128;
+        ANKH_AL(H.d_Mhi, rows * g.ldm);
+        ANKH_AL(H.d_Mlo, rows * g.ldm);
+        ANKH_AL(H.d_Chi, arows * acols);
+        ANKH_AL(H.d_Clo, arows * acols);
+        cudaMemset(H.d_Mhi, 0, sizeof(float) * rows * g.ldm);
+        cudaMemset(H.d_Mlo, 0, sizeof(float) * rows * g.ldm);
+        // A = [C_0 | ... | C_26] as [halves*128 rows][27*ldm], split hi/lo (round to nearest TF32)
         std::vector<double> C = make_C(g.Lu, g.ldm, g.h / (g.Lu - 1), p.xi);
-        std::vector<float> Ah((size_t)128 * 27 * 128), Al((size_t)128 * 27 * 128);
+        std::vector<float> Ah((size_t)(arows * acols), 0.f), Al((size_t)(arows * acols), 0.f);
         for (int d = 0; d < 27; ++d)
-            for (int m = 0; m < 128; ++m)
-                for (int l = 0; l < 128; ++l) {
-                    const float v = (float)C[((size_t)d * 128 + m) * 128 + l];
+            for (int m = 0; m < g.ldm; ++m)
+                for (int l = 0; l < g.ldm; ++l) {
+                    const float v = (float)C[((size_t)d * g.ldm + m) * g.ldm + l];
                     const float hi = tf32_round(v);
-                    Ah[(size_t)m * 27 * 128 + d * 128 + l] = hi;
-                    Al[(size_t)m * 27 * 128 + d * 128 + l] = tf32_round(v - hi);
+                    Ah[(size_t)m * acols + (size_t)d * g.ldm + l] = hi;
+                    Al[(size_t)m * acols + (size_t)d * g.ldm + l] = tf32_round(v - hi);
                 }
         if (cudaMemcpy(H.d_Chi, Ah.data(), Ah.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(H.d_Clo, Al.data(), Al.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)

@@ -40,7 +40,7 @@ enum PartSlot { kPartNear = 0, kPartGlob = 1, kPartCorr = 2, kPartSelf = 3, kPar
 // Tensor-core correction (k_corr_tc.cu): tile geometry and TMA descriptors.
 struct TcPlan {
     int enabled;
-    int S, R, rowstride, N, tiles;
+    int S, R, rowstride, N, tiles, halves;
     uint32_t tmem_cols;
     CUtensorMap mAhi, mAlo, mBhi, mBlo;
 };

@@ -1,8 +1,10 @@
 // Adjacent-leaf correction on the 5th-generation tensor cores (tcgen05).
 //
 // Same contraction as k_corr.cu (see there for the definition):
-//   Psi[128 x N] = sum_{d=0..26} C_d[128 x 128] . B_d[128 x N],
+//   Psi[ldm x N] = sum_{d=0..26} C_d[ldm x ldm] . B_d[ldm x N],
 //   B_d[:, j] = M_{t_j + d},
+// one CTA per 128-row slice of the target nodes (blockIdx.y; ldm = 128 for
+// L_u = 5, 224 for L_u = 6, rows beyond ldm are zero),
 // for a tile of N target leaves (R z-rows of the leaf grid, each padded to S
 // columns).  Split precision "3xTF32": every FP32 operand x is written as
 // x_hi + x_lo with x_hi = tf32(x) (round to nearest) and x_lo = tf32(x - x_hi);
@@ -39,9 +41,8 @@ namespace tcg {
 
 constexpr int kStages = 3;
 constexpr int kAccBufs = 3;            // large-product accumulator buffers in TMEM
-constexpr int kRows = 128;            // target nodes (ldm)
+constexpr int kRows = 128;            // target-node rows per CTA (MMA M)
 constexpr int kKc = 32;               // K floats per stage (128 bytes)
-constexpr int kIters = 27 * (kRows / kKc);
 constexpr int kThreads = 192;         // warps 0-3 epilogue, 4 TMA producer, 5 MMA issuer
 constexpr uint32_t kABytes = kRows * kKc * 4;
 constexpr long long kBudget = 4000000000LL;   // ~2 s at 2 GHz
@@ -185,6 +186,10 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
     __shared__ double red[4];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ldm = g.ldm;
+    const int kch = ldm / kKc;            // K chunks per offset d
+    const int kIters = 27 * kch;
+    const int row0 = blockIdx.y * kRows;  // first target-node row of this CTA
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&full[s], 1);
@@ -219,12 +224,12 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
                 break;
             }
             if (*abort_flag) break;
-            const int d = it / (kRows / kKc), kc = it % (kRows / kKc);
+            const int d = it / kch, kc = it % kch;
             const int dx = d / 9 - 1, dy = (d / 3) % 3 - 1, dz = d % 3 - 1;
             unsigned char *st = smem + (size_t)s * stage;
             mbar_expect_tx(&full[s], stage);
-            tma_2d(st, &tmAhi, &full[s], d * kRows + kc * kKc, 0);
-            tma_2d(st + kABytes, &tmAlo, &full[s], d * kRows + kc * kKc, 0);
+            tma_2d(st, &tmAhi, &full[s], d * ldm + kc * kKc, row0);
+            tma_2d(st + kABytes, &tmAlo, &full[s], d * ldm + kc * kKc, row0);
             for (int r = 0; r < R; ++r) {
                 int zrow = blockIdx.x * R + r;
                 if (zrow >= nrow) zrow = nrow - 1;
@@ -329,8 +334,8 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
         if (ok) {
             // energy dot and psi: M loads issued 16 at a time (independent), FP32
             // partial sums per thread (128 products), FP64 across threads
-            const int m = warp * 32 + lane;
-            const int ldm = g.ldm;
+            const int m = row0 + warp * 32 + lane;
+            const bool mrow = m < ldm;
             float e0 = 0.f, e1 = 0.f;
 #pragma unroll
             for (int c0 = 0; c0 < 128; c0 += 16) {
@@ -342,7 +347,7 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
                         const int c = c0 + j;
                         const int slab = c / S, z = c % S;
                         const int zrow = blockIdx.x * R + slab;
-                        const bool valid = (c < N) && (z < n) && (zrow < nrow);
+                        const bool valid = mrow && (c < N) && (z < n) && (zrow < nrow);
                         ofs[j] = valid ? ((int64_t)zrow * n + z) * ldm + m : -1;
                         mv[j] = valid ? __ldg(&M[ofs[j]]) : 0.f;
                     }
@@ -365,7 +370,7 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
     fence_before();
     __syncthreads();
     if (threadIdx.x == 0) {
-        part[blockIdx.x] = -0.5 * (red[0] + red[1] + red[2] + red[3]);
+        part[blockIdx.y * gridDim.x + blockIdx.x] = -0.5 * (red[0] + red[1] + red[2] + red[3]);
         if (*abort_flag) atomicOr(errflag, 2);
     }
     if (warp == 5) {
@@ -417,7 +422,7 @@ bool tc_prepare(Handle &H, std::string &err)
 {
     H.tc.enabled = 0;
     const Geo &g = H.g;
-    if (g.ldm != tcg::kRows || g.n > 128) return true;   // not applicable: plain FP32 kernel is used
+    if (g.ldm % tcg::kKc != 0 || g.ldm > 512 || g.n > 128) return true;   // plain FP32 kernel is used
     const int S = ((g.n + 15) / 16) * 16;
     const int R = std::max(1, 128 / S);
     H.tc.S = S;
@@ -427,11 +432,13 @@ bool tc_prepare(Handle &H, std::string &err)
     H.tc.tmem_cols = 32;
     while ((int)H.tc.tmem_cols < (tcg::kAccBufs + 1) * H.tc.N) H.tc.tmem_cols <<= 1;   // large buffers + small
     H.tc.tiles = (g.n * g.n + R - 1) / R;
+    H.tc.halves = (g.ldm + tcg::kRows - 1) / tcg::kRows;
     const uint64_t rows = (uint64_t)g.n * g.n * H.tc.rowstride;
-    if (!encode_2d(&H.tc.mAhi, H.d_Chi, 27 * 128, 128, tcg::kKc, 128, err)) return false;
-    if (!encode_2d(&H.tc.mAlo, H.d_Clo, 27 * 128, 128, tcg::kKc, 128, err)) return false;
-    if (!encode_2d(&H.tc.mBhi, H.d_Mhi, 128, rows, tcg::kKc, (uint32_t)S, err)) return false;
-    if (!encode_2d(&H.tc.mBlo, H.d_Mlo, 128, rows, tcg::kKc, (uint32_t)S, err)) return false;
+    const uint64_t arows = (uint64_t)H.tc.halves * tcg::kRows;
+    if (!encode_2d(&H.tc.mAhi, H.d_Chi, 27 * (uint64_t)g.ldm, arows, tcg::kKc, 128, err)) return false;
+    if (!encode_2d(&H.tc.mAlo, H.d_Clo, 27 * (uint64_t)g.ldm, arows, tcg::kKc, 128, err)) return false;
+    if (!encode_2d(&H.tc.mBhi, H.d_Mhi, g.ldm, rows, tcg::kKc, (uint32_t)S, err)) return false;
+    if (!encode_2d(&H.tc.mBlo, H.d_Mlo, g.ldm, rows, tcg::kKc, (uint32_t)S, err)) return false;
     const size_t smem = tc_smem_bytes(H.tc.N);
     if (cudaFuncSetAttribute(k_corr_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess ||
@@ -444,18 +451,19 @@ bool tc_prepare(Handle &H, std::string &err)
     return true;
 }
 
-int corr_tc_blocks(const Handle &H) { return H.tc.tiles; }
+int corr_tc_blocks(const Handle &H) { return H.tc.tiles * H.tc.halves; }
 
 cudaError_t launch_corr_tc(Handle &H, bool forces, cudaStream_t s)
 {
     const size_t smem = tc_smem_bytes(H.tc.N);
     double *part = H.d_part + H.part_off[kPartCorr];
+    const dim3 grid(H.tc.tiles, H.tc.halves);
     if (forces)
-        k_corr_tc<true><<<H.tc.tiles, tcg::kThreads, smem, s>>>(H.tc.mAhi, H.tc.mAlo, H.tc.mBhi, H.tc.mBlo, H.g,
+        k_corr_tc<true><<<grid, tcg::kThreads, smem, s>>>(H.tc.mAhi, H.tc.mAlo, H.tc.mBhi, H.tc.mBlo, H.g,
                                                                 H.tc.S, H.tc.R, H.tc.rowstride, H.tc.tmem_cols,
                                                                 H.d_M, H.d_psi, part, H.d_flag);
     else
-        k_corr_tc<false><<<H.tc.tiles, tcg::kThreads, smem, s>>>(H.tc.mAhi, H.tc.mAlo, H.tc.mBhi, H.tc.mBlo, H.g,
+        k_corr_tc<false><<<grid, tcg::kThreads, smem, s>>>(H.tc.mAhi, H.tc.mAlo, H.tc.mBhi, H.tc.mBlo, H.g,
                                                                  H.tc.S, H.tc.R, H.tc.rowstride, H.tc.tmem_cols,
                                                                  H.d_M, H.d_psi, part, H.d_flag);
     return cudaGetLastError();

@@ -244,19 +244,20 @@ def test_autograd_backward_is_the_adjoint(api):
     assert torch.allclose(th.grad, 3.0 * g["dEdtheta"])
 
 
-@pytest.mark.parametrize("boxname,n", [("w3000", 7), ("w24000", 14), ("w24000", 20), ("w24000", 36)])
-def test_tensor_core_correction_matches_fp32(api, boxname, n):
+@pytest.mark.parametrize("boxname,n,Lu", [("w3000", 7, 5), ("w24000", 14, 5), ("w24000", 20, 5),
+                                           ("w24000", 36, 5), ("w24000", 14, 6), ("w3000", 8, 4)])
+def test_tensor_core_correction_matches_fp32(api, boxname, n, Lu):
     """The tcgen05 3xTF32 correction reproduces the plain FP32 contraction:
-    psi to 1e-5 of max|psi| and the correction energy to 1e-6 (ragged tiles,
-    z-rows padded to 16/32/48 leaves)."""
+    psi to 1e-5 of max|psi| and the correction energy to 2e-6 (ragged tiles,
+    z-rows padded to 16/32/48 leaves, 64/128/224 target-node rows)."""
     b = synth.small_box(1000, 31, box=31.1) if boxname == "w3000" else synth.config_box(2)
     x, q, mu, th = to_dev(b)
     res = {}
     for mixed in (False, True):
-        m = api.Ankh(b.box, b.n, n_cells=n, Lu=5, mixed=mixed)
+        m = api.Ankh(b.box, b.n, n_cells=n, Lu=Lu, mixed=mixed)
         m.energy_forces(x, q, mu, th)
         res[mixed] = (m.terms(), api.ankh_debug_copy(m.h, api.BUF_PSI).cpu().numpy())
         m.close()
     (t0, p0), (t1, p1) = res[False], res[True]
     assert np.max(np.abs(p1 - p0)) <= 1e-5 * np.max(np.abs(p0))
-    assert t1["correction"] == pytest.approx(t0["correction"], rel=1e-6)
+    assert t1["correction"] == pytest.approx(t0["correction"], rel=2e-6)
