@@ -125,6 +125,25 @@ int ankh_get_info(const ankh_handle *h, ankh_info *info);
 int ankh_debug_copy(const ankh_handle *h, int which, void *dst, int64_t *bytes, void *cuda_stream);
 int ankh_ldm(const ankh_handle *h);
 
+/* Batched independent boxes (replicas of uneven size).  Each box has its own
+ * handle (tables depend on the box edge); one call evaluates all boxes:
+ * the per-box pipelines are recorded once into a CUDA graph with parallel
+ * branches (small boxes run concurrently) and replayed while the caller's
+ * pointers and stream stay the same (a change triggers a new capture).
+ * Inputs/outputs are the per-box arrays concatenated in box order (box i
+ * starts at atom offset sum_{j<i} n_atoms[j]); E_host receives nbox
+ * energies; the call synchronises the stream.  The first call on a stream
+ * must not itself be inside a stream capture. */
+typedef struct ankh_batch ankh_batch;
+int ankh_create_batch(int nbox, const double *box_edges, const int64_t *n_atoms, const ankh_params *params,
+                      ankh_batch **out);
+int ankh_energy_forces_batch(ankh_batch *b, const float *x, const float *q, const float *mu,
+                             const float *theta, double *E_host, float *dEdx, float *dEdq, float *dEdmu,
+                             float *dEdtheta, float *torque, void *cuda_stream);
+/* Borrow the handle of box i (owned by the batch; do not destroy it). */
+int ankh_batch_box(const ankh_batch *b, int i, ankh_handle **h);
+void ankh_destroy_batch(ankh_batch *b);
+
 /* Optional per-stage timing with CUDA events recorded on the call's stream
  * (off by default).  Stages: 0 bin+sort, 1 self term, 2 P2M, 3 merge onto
  * the equispaced grid, 4 forward FFT, 5 spectral product, 6 adjacent-leaf

@@ -28,7 +28,8 @@ BUF_PERM, BUF_START, BUF_M, BUF_RHO, BUF_PSI, BUF_SCELL = range(6)
 EXPORTED = ["ankh_default_params", "ankh_create", "ankh_energy", "ankh_energy_forces",
             "ankh_energy_forces_host", "ankh_last_terms", "ankh_get_info", "ankh_debug_copy",
             "ankh_ldm", "ankh_set_timing", "ankh_stage_times", "ankh_bin_sort_noalloc", "ankh_destroy",
-            "ankh_last_error", "ankh_version"]
+            "ankh_last_error", "ankh_version", "ankh_create_batch", "ankh_energy_forces_batch",
+            "ankh_batch_box", "ankh_destroy_batch"]
 STAGES = ["sort", "self", "p2m", "merge", "fft_fwd", "spectral", "corr", "near", "fft_inv", "l2p",
           "finalize", "reduce"]
 
@@ -91,6 +92,16 @@ def load_library(path: str = LIB_PATH):
         lib.ankh_stage_times.restype = ctypes.c_int
         lib.ankh_bin_sort_noalloc.argtypes = [vp, ctypes.c_int64, ctypes.c_double, ctypes.c_int, vp, vp, vp]
         lib.ankh_bin_sort_noalloc.restype = ctypes.c_int
+        lib.ankh_create_batch.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ankh_params),
+                                          ctypes.POINTER(vp)]
+        lib.ankh_create_batch.restype = ctypes.c_int
+        lib.ankh_energy_forces_batch.argtypes = [vp, vp, vp, vp, vp, dp, vp, vp, vp, vp, vp, vp]
+        lib.ankh_energy_forces_batch.restype = ctypes.c_int
+        lib.ankh_batch_box.argtypes = [vp, ctypes.c_int, ctypes.POINTER(vp)]
+        lib.ankh_batch_box.restype = ctypes.c_int
+        lib.ankh_destroy_batch.argtypes = [vp]
+        lib.ankh_destroy_batch.restype = None
         lib.ankh_destroy.argtypes = [vp]
         lib.ankh_destroy.restype = None
         lib.ankh_last_error.argtypes = []
@@ -286,6 +297,75 @@ class Ankh:
 
     def terms(self):
         return ankh_last_terms(self.h)
+
+
+def ankh_create_batch(box_edges, n_atoms, params: ankh_params | None = None) -> ctypes.c_void_p:
+    lib = load_library()
+    nb = len(box_edges)
+    be = (ctypes.c_double * nb)(*[float(v) for v in box_edges])
+    na = (ctypes.c_int64 * nb)(*[int(v) for v in n_atoms])
+    h = ctypes.c_void_p()
+    _check(lib.ankh_create_batch(nb, be, na, ctypes.byref(params) if params is not None else None,
+                                 ctypes.byref(h)))
+    return h
+
+
+def ankh_destroy_batch(h) -> None:
+    if h:
+        load_library().ankh_destroy_batch(h)
+
+
+def ankh_energy_forces_batch(h, nbox: int, x, q, mu=None, theta=None, dEdx=None, dEdq=None, dEdmu=None,
+                             dEdtheta=None, torque=None, stream=None):
+    """All boxes of a batch; arrays are concatenated in box order.  Returns a
+    list of nbox energies."""
+    E = (ctypes.c_double * nbox)()
+    _check(load_library().ankh_energy_forces_batch(h, _ptr(x), _ptr(q), _ptr(mu), _ptr(theta), E, _ptr(dEdx),
+                                                   _ptr(dEdq), _ptr(dEdmu), _ptr(dEdtheta), _ptr(torque),
+                                                   _stream_ptr(stream)))
+    return list(E)
+
+
+def ankh_batch_box(h, i: int) -> ctypes.c_void_p:
+    out = ctypes.c_void_p()
+    _check(load_library().ankh_batch_box(h, int(i), ctypes.byref(out)))
+    return out
+
+
+class AnkhBatch:
+    """Owning wrapper of a batch of independent boxes (replicas)."""
+
+    def __init__(self, box_edges, n_atoms, xi: float = 0.01, n_cells: int = 0, Lu: int = 5, Lc: int = 0,
+                 max_order: int = 2, include_rec: bool = True, mixed: bool = True):
+        p = ankh_default_params()
+        p.xi, p.n_cells, p.Lu, p.Lc, p.max_order = xi, n_cells, Lu, Lc, max_order
+        p.flags = (ANKH_INCLUDE_REC if include_rec else 0) | (ANKH_MIXED if mixed else 0)
+        self.n_atoms = [int(v) for v in n_atoms]
+        self.nbox = len(self.n_atoms)
+        self.h = ankh_create_batch(box_edges, self.n_atoms, p)
+
+    def close(self):
+        if self.h:
+            ankh_destroy_batch(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def energy_forces(self, x, q, mu=None, theta=None, out=None, torques: bool = False):
+        import torch
+        n = x.shape[0]
+        dev = x.device
+        if out is None:
+            out = {"dEdx": torch.empty((n, 3), device=dev), "dEdq": torch.empty(n, device=dev),
+                   "dEdmu": torch.empty((n, 3), device=dev), "dEdtheta": torch.empty((n, 6), device=dev)}
+            if torques:
+                out["torque"] = torch.empty((n, 3), device=dev)
+        E = ankh_energy_forces_batch(self.h, self.nbox, x, q, mu, theta, **out)
+        return E, out
 
 
 def _autograd():

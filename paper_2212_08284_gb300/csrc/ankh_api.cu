@@ -206,7 +206,7 @@ static void mark(Handle &H, int stage_done, cudaStream_t s)
     H.nrec++;
 }
 
-static int run_sequence(Handle &H, const float *x, const float *q, const float *mu, const float *theta,
+int run_sequence(Handle &H, const float *x, const float *q, const float *mu, const float *theta,
                         bool forces, float *dEdx, float *dEdq, float *dEdmu, float *dEdtheta, float *torque,
                         cudaStream_t s)
 {
@@ -598,6 +598,153 @@ int ankh_debug_copy(const ankh_handle *h, int which, void *dst, int64_t *bytes, 
     cudaStream_t s = (cudaStream_t)cuda_stream;
     ANKH_CU(cudaMemcpyAsync(dst, src, nb, cudaMemcpyDeviceToDevice, s), "debug copy");
     ANKH_CU(cudaStreamSynchronize(s), "synchronize");
+    return ANKH_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched independent boxes (replicas): one CUDA graph with one branch per box
+
+struct ankh_batch {
+    std::vector<ankh_handle *> boxes;
+    std::vector<int64_t> off;            // atom offsets, nbox + 1
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> joins;
+    cudaStream_t cap = nullptr;          // capture stream (the caller's may be the legacy stream)
+    cudaEvent_t fork = nullptr;
+    double *h_E = nullptr;               // pinned: per box (energy, flag)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const void *last[11] = {nullptr};
+    bool have_exec = false;
+};
+
+static void batch_free(ankh_batch *b)
+{
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (auto e : b->joins) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    for (auto st : b->streams) cudaStreamDestroy(st);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->h_E) cudaFreeHost(b->h_E);
+    for (auto h : b->boxes) ankh_destroy(h);
+    delete b;
+}
+
+extern "C" {
+
+int ankh_create_batch(int nbox, const double *box_edges, const int64_t *n_atoms, const ankh_params *params,
+                      ankh_batch **out)
+{
+    if (!out) return fail(ANKH_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (nbox < 1 || !box_edges || !n_atoms) return fail(ANKH_EINVAL, "nbox >= 1 and the size arrays are required");
+    ankh_batch *b = new (std::nothrow) ankh_batch();
+    if (!b) return fail(ANKH_ENOMEM, "host allocation");
+    b->off.push_back(0);
+    for (int i = 0; i < nbox; ++i) {
+        ankh_handle *h = nullptr;
+        const int rc = ankh_create(box_edges[i], n_atoms[i], params, &h);
+        if (rc != ANKH_OK) {
+            const std::string msg = "box " + std::to_string(i) + ": " + g_err;
+            batch_free(b);
+            return fail(rc, msg);
+        }
+        b->boxes.push_back(h);
+        b->off.push_back(b->off.back() + n_atoms[i]);
+    }
+    const int ns = std::min(nbox, 16);
+    for (int k = 0; k < ns; ++k) {
+        cudaStream_t st;
+        cudaEvent_t ev;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            batch_free(b);
+            return fail(ANKH_ECUDA, "stream/event creation");
+        }
+        b->streams.push_back(st);
+        b->joins.push_back(ev);
+    }
+    if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMallocHost(&b->h_E, sizeof(double) * 2 * nbox) != cudaSuccess) {
+        batch_free(b);
+        return fail(ANKH_ENOMEM, "batch event / pinned buffer");
+    }
+    *out = b;
+    return ANKH_OK;
+}
+
+void ankh_destroy_batch(ankh_batch *b) { batch_free(b); }
+
+int ankh_batch_box(const ankh_batch *b, int i, ankh_handle **h)
+{
+    if (!b || !h || i < 0 || i >= (int)b->boxes.size()) return fail(ANKH_EINVAL, "bad batch box index");
+    *h = b->boxes[i];
+    return ANKH_OK;
+}
+
+int ankh_energy_forces_batch(ankh_batch *b, const float *x, const float *q, const float *mu, const float *theta,
+                             double *E_host, float *dEdx, float *dEdq, float *dEdmu, float *dEdtheta,
+                             float *torque, void *cuda_stream)
+{
+    if (!b || !x || !q || !E_host) return fail(ANKH_EINVAL, "batch, x, q and E_host are required");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const void *ptrs[11] = {x, q, mu, theta, dEdx, dEdq, dEdmu, dEdtheta, torque, (const void *)s, nullptr};
+    bool same = b->have_exec;
+    for (int k = 0; k < 10 && same; ++k) same = (ptrs[k] == b->last[k]);
+    if (!same) {
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        if (b->graph) cudaGraphDestroy(b->graph);
+        b->exec = nullptr;
+        b->graph = nullptr;
+        b->have_exec = false;
+        // capture on the batch's own stream; the graph is launched on the caller's
+        ANKH_CU(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+        cudaEventRecord(b->fork, b->cap);
+        const int ns = (int)b->streams.size();
+        for (int k = 0; k < ns; ++k) cudaStreamWaitEvent(b->streams[k], b->fork, 0);
+        int rc = ANKH_OK;
+        for (size_t i = 0; i < b->boxes.size() && rc == ANKH_OK; ++i) {
+            Handle &H = b->boxes[i]->h;
+            const int64_t o = b->off[i];
+            cudaStream_t st = b->streams[i % ns];
+            auto at = [o](const float *p, int k) { return p ? p + k * o : nullptr; };
+            auto atw = [o](float *p, int k) { return p ? p + k * o : nullptr; };
+            rc = run_sequence(H, x + 3 * o, q + o, at(mu, 3), at(theta, 6), true, atw(dEdx, 3), atw(dEdq, 1),
+                              atw(dEdmu, 3), atw(dEdtheta, 6), atw(torque, 3), st);
+            if (rc == ANKH_OK) {
+                cudaMemcpyAsync(b->h_E + 2 * i, H.d_terms + 5, sizeof(double), cudaMemcpyDeviceToHost, st);
+                cudaMemcpyAsync(b->h_E + 2 * i + 1, H.d_terms + 8, sizeof(double), cudaMemcpyDeviceToHost, st);
+            }
+        }
+        for (int k = 0; k < ns; ++k) {
+            cudaEventRecord(b->joins[k], b->streams[k]);
+            cudaStreamWaitEvent(b->cap, b->joins[k], 0);
+        }
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(b->cap, &graph);
+        if (rc != ANKH_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (ce != cudaSuccess) return fail(ANKH_ECUDA, std::string("end capture: ") + cudaGetErrorString(ce));
+        b->graph = graph;
+        ANKH_CU(cudaGraphInstantiate(&b->exec, b->graph, 0), "graph instantiate");
+        for (int k = 0; k < 10; ++k) b->last[k] = ptrs[k];
+        b->have_exec = true;
+    }
+    ANKH_CU(cudaGraphLaunch(b->exec, s), "graph launch");
+    ANKH_CU(cudaStreamSynchronize(s), "synchronize");
+    for (size_t i = 0; i < b->boxes.size(); ++i) {
+        const int flag = (int)b->h_E[2 * i + 1];
+        if (flag & 2) return fail(ANKH_ETIMEOUT, "box " + std::to_string(i) + ": bounded wait ran out");
+        if (flag & 1) return fail(ANKH_ENUMERIC, "box " + std::to_string(i) + ": non-finite coordinate");
+        E_host[i] = b->h_E[2 * i];
+    }
     return ANKH_OK;
 }
 

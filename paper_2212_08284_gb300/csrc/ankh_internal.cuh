@@ -90,6 +90,9 @@ struct Handle {
     int ev_stage[kNumStages + 1];
 };
 
+int run_sequence(Handle &H, const float *x, const float *q, const float *mu, const float *theta, bool forces,
+                 float *dEdx, float *dEdq, float *dEdmu, float *dEdtheta, float *torque, cudaStream_t s);
+
 // error reporting (thread-local message)
 void set_error(const std::string &msg);
 
