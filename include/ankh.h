@@ -38,7 +38,8 @@ enum {
     ANKH_ENOMEM = 2,   /* device or host allocation failed; nothing leaked */
     ANKH_ECUDA = 3,    /* a CUDA or cuFFT call failed */
     ANKH_ETIMEOUT = 4, /* a bounded device-side wait ran out */
-    ANKH_ENUMERIC = 5  /* a non-finite input coordinate was seen */
+    ANKH_ENUMERIC = 5  /* a non-finite input coordinate was seen, or two atoms
+                          share one position (infinite energy) */
 };
 
 /* flags */
@@ -147,8 +148,9 @@ void ankh_destroy_batch(ankh_batch *b);
 /* Optional per-stage timing with CUDA events recorded on the call's stream
  * (off by default).  Stages: 0 bin+sort, 1 self term, 2 P2M, 3 merge onto
  * the equispaced grid, 4 forward FFT, 5 spectral product, 6 adjacent-leaf
- * correction, 7 near field, 8 inverse FFT, 9 L2P, 10 gradient assembly,
- * 11 energy reduction.  ankh_stage_times waits for the last call's events
+ * correction, 7 near field, 8 inverse FFT, 9 L2P fused with the gradient
+ * assembly (far + near + self terms, torques, write in the caller's order),
+ * 10 unused (always 0), 11 energy reduction.  ankh_stage_times waits for the last call's events
  * and returns each stage's duration in milliseconds (0 for stages that did
  * not run). */
 #define ANKH_NUM_STAGES 12

@@ -31,7 +31,7 @@ EXPORTED = ["ankh_default_params", "ankh_create", "ankh_energy", "ankh_energy_fo
             "ankh_last_error", "ankh_version", "ankh_create_batch", "ankh_energy_forces_batch",
             "ankh_batch_box", "ankh_destroy_batch"]
 STAGES = ["sort", "self", "p2m", "merge", "fft_fwd", "spectral", "corr", "near", "fft_inv", "l2p",
-          "finalize", "reduce"]
+          "unused", "reduce"]
 
 
 class AnkhError(RuntimeError):

@@ -174,7 +174,7 @@ static void free_device(Handle *H)
     if (!H) return;
     void *ptrs[] = {H->d_cellid, H->d_rank, H->d_count, H->d_start, H->d_perm, H->d_scell, H->d_flag, H->d_bsum,
                     H->d_A0, H->d_A1, H->d_A2, H->d_A3, H->d_W, H->d_M, H->d_rho, H->d_rhohat, H->d_D,
-                    H->d_phi, H->d_C, H->d_Chi, H->d_Clo, H->d_psi, H->d_gfar, H->d_gnear, H->d_part,
+                    H->d_phi, H->d_C, H->d_Chi, H->d_Clo, H->d_psi, H->d_gnear, H->d_part,
                     H->d_partoff, H->d_terms, H->d_hostbuf, H->d_Mhi, H->d_Mlo};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -255,6 +255,7 @@ static int fetch_terms(Handle &H, double *E_host, cudaStream_t s)
     const int flag = (int)H.h_terms[8];
     if (flag & 2) return fail(ANKH_ETIMEOUT, "a bounded wait of the tensor-core correction ran out");
     if (flag & 1) return fail(ANKH_ENUMERIC, "non-finite input coordinate");
+    if (flag & 4) return fail(ANKH_ENUMERIC, "two atoms at the same position (infinite energy)");
     if (E_host) *E_host = H.h_terms[5];
     return ANKH_OK;
 }

@@ -32,7 +32,7 @@ struct Geo {
 
 // Pipeline stages (for the optional per-stage timing)
 enum Stage { kStSort = 0, kStSelf, kStP2M, kStMerge, kStFFTf, kStSpectral, kStCorr, kStNear, kStFFTi,
-             kStL2P, kStFinal, kStReduce, kNumStages };
+             kStL2P, kStUnused, kStReduce, kNumStages };
 
 // Energy partial slots (FP64 per block, reduced in a fixed order).
 enum PartSlot { kPartNear = 0, kPartGlob = 1, kPartCorr = 2, kPartSelf = 3, kPartQ = 4, kPartCount = 5 };
@@ -70,7 +70,6 @@ struct Handle {
     float *d_C;             // [27][ldm][ldm] adjacent-leaf correction blocks (FP32)
     float *d_Chi, *d_Clo;   // same, split into TF32 high / low parts for the tensor-core path
     float *d_psi;           // [ncell][ldm] correction potential
-    float *d_gfar;          // [13][Nslot] far-field gradient per sorted slot
     float *d_gnear;         // [13][Nslot] near-field gradient per sorted slot
     double *d_part;         // energy partials
     int part_off[kPartCount + 1];
@@ -111,8 +110,6 @@ cudaError_t launch_near(Handle &H, bool forces, cudaStream_t s);
 cudaError_t launch_l2p(Handle &H, float *dEdx, float *dEdq, float *dEdmu, float *dEdtheta, float *torque,
                        cudaStream_t s);
 cudaError_t launch_self_dc(Handle &H, cudaStream_t s);
-cudaError_t launch_finalize(Handle &H, float *dEdx, float *dEdq, float *dEdmu, float *dEdtheta,
-                            float *torque, cudaStream_t s);
 cudaError_t launch_reduce(Handle &H, cudaStream_t s);
 
 // precomputation on the device (FP64)

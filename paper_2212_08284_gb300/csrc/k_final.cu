@@ -1,4 +1,4 @@
-// k = 0 far-field term, gradient assembly and the FP64 energy reduction
+// k = 0 far-field term and the FP64 energy reduction
 // (Alg. 5 steps 4-5).  The self term of Eq. ewald (per atom in the gather
 // kernel, k_sort.cu) is
 // E_self = -(xi/sqrt(pi)) sum_i [q^2 + (2xi^2/3)|mu|^2 - (4xi^2/3) q tr(Theta)
@@ -6,7 +6,7 @@
 // (general symmetric Theta; for a traceless Theta this is the printed form).
 // The k = 0 term of the far field is D_0 Q^2 / (2M) with Q = sum_i q_i exactly
 // (partition of unity of the interpolation), evaluated in FP64; its
-// potential D_0 Q / M is added to dE/dq.
+// potential D_0 Q / M is added to dE/dq by the gradient assembly (k_l2p).
 #include "ankh_internal.cuh"
 
 namespace ankh {
@@ -29,78 +29,6 @@ __global__ void __launch_bounds__(256) k_dc(const double *__restrict__ part_q, i
         for (int w = 0; w < 8; ++w) u += sh[w];
         terms[7] = u;
         terms[6] = D0 * u * invM;
-    }
-}
-
-// Gradient assembly per sorted slot: far + near + self (+ k = 0 potential),
-// torques, and the write to the caller's atom order.
-__global__ void __launch_bounds__(256)
-k_finalize(int N, const int *__restrict__ perm, const float4 *__restrict__ A0,
-           const float4 *__restrict__ A1, const float4 *__restrict__ A2, const float4 *__restrict__ A3,
-           const float *__restrict__ gfar, const float *__restrict__ gnear, const double *__restrict__ terms,
-           float xi, float *__restrict__ dEdx, float *__restrict__ dEdq, float *__restrict__ dEdmu,
-           float *__restrict__ dEdth, float *__restrict__ torque)
-{
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= N) return;
-    const int64_t S = N;
-    float gv[13];
-#pragma unroll
-    for (int k = 0; k < 13; ++k) gv[k] = gfar[k * S + s] + gnear[k * S + s];
-    const float4 a0 = A0[s], a1 = A1[s], a2 = A2[s], a3 = A3[s];
-    const float q = a0.w;
-    const float xx = a2.x, xy = a2.y, xz = a2.z, yy = a2.w, yz = a3.x, zz = a3.y;
-    const float tr = xx + yy + zz;
-    // self-term gradient
-    const float c = xi * 0.56418958354775628f;  // xi / sqrt(pi)
-    const float x2 = xi * xi, x4 = x2 * x2;
-    gv[3] += -c * (2.f * q - (4.f * x2 / 3.f) * tr) + (float)terms[6];
-    gv[4] += -c * (4.f * x2 / 3.f) * a1.x;
-    gv[5] += -c * (4.f * x2 / 3.f) * a1.y;
-    gv[6] += -c * (4.f * x2 / 3.f) * a1.z;
-    const float dg = -(4.f * x2 / 3.f) * q + (8.f * x4 / 5.f) * tr;
-    const float k16 = 16.f * x4 / 5.f;
-    gv[7] += -c * (dg + k16 * xx);
-    gv[8] += -c * 2.f * k16 * xy;
-    gv[9] += -c * 2.f * k16 * xz;
-    gv[10] += -c * (dg + k16 * yy);
-    gv[11] += -c * 2.f * k16 * yz;
-    gv[12] += -c * (dg + k16 * zz);
-
-    const int i = perm[s];
-    const int64_t ii = i;
-    if (dEdx) {
-        dEdx[3 * ii] = gv[0];
-        dEdx[3 * ii + 1] = gv[1];
-        dEdx[3 * ii + 2] = gv[2];
-    }
-    if (dEdq) dEdq[ii] = gv[3];
-    if (dEdmu) {
-        dEdmu[3 * ii] = gv[4];
-        dEdmu[3 * ii + 1] = gv[5];
-        dEdmu[3 * ii + 2] = gv[6];
-    }
-    if (dEdth) {
-#pragma unroll
-        for (int k = 0; k < 6; ++k) dEdth[6 * ii + k] = gv[7 + k];
-    }
-    if (torque) {
-        // tau = -(mu x g) - 2 axial(G Theta), G = dE/dTheta with each of the nine
-        // entries independent (stored off-diagonal derivative / 2)
-        const float gx = gv[4], gy = gv[5], gz = gv[6];
-        const float G[3][3] = {{gv[7], 0.5f * gv[8], 0.5f * gv[9]},
-                               {0.5f * gv[8], gv[10], 0.5f * gv[11]},
-                               {0.5f * gv[9], 0.5f * gv[11], gv[12]}};
-        const float T[3][3] = {{xx, xy, xz}, {xy, yy, yz}, {xz, yz, zz}};
-        float X[3][3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int b = 0; b < 3; ++b) X[a][b] = G[a][0] * T[0][b] + G[a][1] * T[1][b] + G[a][2] * T[2][b];
-        const float mx = a1.x, my = a1.y, mz = a1.z;
-        torque[3 * ii] = -(my * gz - mz * gy) - 2.f * (X[2][1] - X[1][2]);
-        torque[3 * ii + 1] = -(mz * gx - mx * gz) - 2.f * (X[0][2] - X[2][0]);
-        torque[3 * ii + 2] = -(mx * gy - my * gx) - 2.f * (X[1][0] - X[0][1]);
     }
 }
 
@@ -151,16 +79,6 @@ cudaError_t launch_self_dc(Handle &H, cudaStream_t s)
 {
     k_dc<<<1, 256, 0, s>>>(H.d_part + H.part_off[kPartQ], self_blocks(H), H.D0, 1.0 / (double)H.g.M,
                            H.d_terms);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_finalize(Handle &H, float *dEdx, float *dEdq, float *dEdmu, float *dEdtheta,
-                            float *torque, cudaStream_t s)
-{
-    const int N = (int)H.N;
-    k_finalize<<<(N + 255) / 256, 256, 0, s>>>(N, H.d_perm, H.d_A0, H.d_A1, H.d_A2, H.d_A3, H.d_gfar,
-                                               H.d_gnear, H.d_terms, H.g.xi, dEdx, dEdq, dEdmu, dEdtheta,
-                                               torque);
     return cudaGetLastError();
 }
 

@@ -33,17 +33,27 @@
 // leaf offset); the warp's lanes are split into G = 32 / n_t groups, lane
 // (i, g) accumulating target i over sources g, g + G, ...; the group partials
 // are summed in a fixed order.  Every output is written by exactly one lane:
-// no atomics, deterministic results.
+// no atomics, deterministic results.  Zero-distance pairs are counted per
+// target; a count other than one (two atoms at one position, where the
+// energy is infinite) sets bit 4 of the error flag.
 #include "ankh_internal.cuh"
 
 namespace ankh {
 
 struct BCoef {
-    float xi, xi2;
+    float xi;
+    float kap;                  // xi^2 log2(e):  y = kap r^2,  exp(-xi^2 r^2) = 2^-y
     float c1, c2, c3, c4, c5;   // (2 xi^2)^l / (xi sqrt(pi))
-    float e[8];                 // Maclaurin coefficients of erf(x)/x in x^2
-    int series;                 // use the series (xi * r_max <= 0.5)
+    float a[8];                 // erf(xi r)/r = sum_k a_k y^k (Maclaurin series of erf)
 };
+
+// How B0 = erfc(xi r)/r is evaluated (chosen per launch from xi * r_max, r_max
+// the largest distance between atoms of adjacent leaves):
+//   kErfcLib    erfcf (any xi r)
+//   kSeriesLong 8 terms of the series (xi r_max <= 0.5; the next term is
+//               below 2e-11 of B0)
+//   kSeriesShort 4 terms (xi r_max <= 0.2; the next term is below 3e-9 of B0)
+enum { kErfcLib = 0, kSeriesLong = 1, kSeriesShort = 2 };
 
 constexpr int kNearWarps = 4;
 constexpr int kNearChunk = 64;
@@ -54,28 +64,34 @@ struct NAcc {
 };
 
 struct TgtQ {
-    float xx, xy, xz, yy, yz, zz, tr;            // target quadrupole
+    float xx, xy, xz, yy, yz, zz;       // target quadrupole Theta_i
+    float wxx, wxy, wxz, wyy, wyz, wzz; // 2 Theta_i + tr(Theta_i) 1
 };
 
-template <bool FORCES, bool SERIES>
+// A pair at zero distance (the target itself; two distinct atoms at one
+// position are counted in nzero and reported by the caller) contributes 0:
+// rinv and B0 are selected to 0, which zeroes every B_l.
+template <bool FORCES, int MODE>
 __device__ __forceinline__ void src_fields(float rx, float ry, float rz, const float4 s0, const float4 s1,
                                            const float4 s2, const float4 s3, const BCoef &bc, const TgtQ &T,
-                                           float (&acc)[NAcc<FORCES>::K])
+                                           float (&acc)[NAcc<FORCES>::K], int &nzero)
 {
-    const float r2 = rx * rx + ry * ry + rz * rz;
-    const float rinv = rsqrtf(r2);
-    const float r = r2 * rinv;
+    const float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
+    const bool zero = r2 == 0.f;
+    nzero += zero ? 1 : 0;
+    const float rinv = zero ? 0.f : rsqrtf(r2);
     const float ri2 = rinv * rinv;
-    const float ex = __expf(-bc.xi2 * r2);
+    const float y = bc.kap * r2;
+    const float ex = exp2f(-y);
     float B0;
-    if (SERIES) {
-        const float x = bc.xi * r, x2 = x * x;
-        float p = bc.e[7];
-#pragma unroll
-        for (int k = 6; k >= 0; --k) p = fmaf(p, x2, bc.e[k]);
-        B0 = fmaf(-x, p, 1.f) * rinv;
+    if (MODE == kErfcLib) {
+        B0 = erfcf(bc.xi * (r2 * rinv)) * rinv;   // 0 when rinv = 0
     } else {
-        B0 = erfcf(bc.xi * r) * rinv;
+        constexpr int NT = (MODE == kSeriesShort) ? 4 : 8;
+        float p = bc.a[NT - 1];
+#pragma unroll
+        for (int k = NT - 2; k >= 0; --k) p = fmaf(p, y, bc.a[k]);
+        B0 = zero ? 0.f : rinv - p;
     }
     const float B1 = fmaf(bc.c1, ex, B0) * ri2;
     const float B2 = fmaf(bc.c2, ex, 3.f * B1) * ri2;
@@ -84,65 +100,64 @@ __device__ __forceinline__ void src_fields(float rx, float ry, float rz, const f
     // source multipoles: s0 = (x, y, z, q), s1 = (mu, tr Theta), s2 = (xx, xy, xz, yy), s3 = (yz, zz, -, -)
     const float q = s0.w, mx = s1.x, my = s1.y, mz = s1.z;
     const float txx = s2.x, txy = s2.y, txz = s2.z, tyy = s2.w, tyz = s3.x, tzz = s3.y;
-    const float Qx = txx * rx + txy * ry + txz * rz;
-    const float Qy = txy * rx + tyy * ry + tyz * rz;
-    const float Qz = txz * rx + tyz * ry + tzz * rz;
-    const float s = mx * rx + my * ry + mz * rz - s1.w;
-    const float u = rx * Qx + ry * Qy + rz * Qz;
-    const float A = -(q * B1 + s * B2 + u * B3);
-    const float A2 = q * B2 + s * B3 + u * B4;
-    acc[0] += q * B0 + s * B1 + u * B2;
+    const float Qx = fmaf(txz, rz, fmaf(txy, ry, txx * rx));
+    const float Qy = fmaf(tyz, rz, fmaf(tyy, ry, txy * rx));
+    const float Qz = fmaf(tzz, rz, fmaf(tyz, ry, txz * rx));
+    const float s = fmaf(mz, rz, fmaf(my, ry, fmaf(mx, rx, -s1.w)));
+    const float u = fmaf(rz, Qz, fmaf(ry, Qy, rx * Qx));
+    const float nA = fmaf(u, B3, fmaf(s, B2, q * B1));      // -A
+    const float A2 = fmaf(u, B4, fmaf(s, B3, q * B2));
+    acc[0] = fmaf(u, B2, fmaf(s, B1, fmaf(q, B0, acc[0])));
     const float twoB2 = 2.f * B2;
-    acc[1] += mx * B1 + twoB2 * Qx + rx * A;
-    acc[2] += my * B1 + twoB2 * Qy + ry * A;
-    acc[3] += mz * B1 + twoB2 * Qz + rz * A;
+    acc[1] = fmaf(-rx, nA, fmaf(twoB2, Qx, fmaf(mx, B1, acc[1])));
+    acc[2] = fmaf(-ry, nA, fmaf(twoB2, Qy, fmaf(my, B1, acc[2])));
+    acc[3] = fmaf(-rz, nA, fmaf(twoB2, Qz, fmaf(mz, B1, acc[3])));
     const float twoB3 = 2.f * B3;
-    const float Px = mx * B2 + twoB3 * Qx, Py = my * B2 + twoB3 * Qy, Pz = mz * B2 + twoB3 * Qz;
-    const float rxA2 = rx * A2, ryA2 = ry * A2, rzA2 = rz * A2;
-    acc[4] += A + rx * rxA2 - 2.f * rx * Px + twoB2 * txx;
-    acc[5] += rx * ryA2 - (rx * Py + ry * Px) + twoB2 * txy;
-    acc[6] += rx * rzA2 - (rx * Pz + rz * Px) + twoB2 * txz;
-    acc[7] += A + ry * ryA2 - 2.f * ry * Py + twoB2 * tyy;
-    acc[8] += ry * rzA2 - (ry * Pz + rz * Py) + twoB2 * tyz;
-    acc[9] += A + rz * rzA2 - 2.f * rz * Pz + twoB2 * tzz;
+    const float Px = fmaf(twoB3, Qx, mx * B2), Py = fmaf(twoB3, Qy, my * B2), Pz = fmaf(twoB3, Qz, mz * B2);
+    const float Wx = fmaf(rx, A2, -Px), Wy = fmaf(ry, A2, -Py), Wz = fmaf(rz, A2, -Pz);
+    // G_ab = delta_ab A + r_a W_b - r_b P_a + 2 B2 Theta_ab  (= delta A + r r A2 - r P - P r + 2 B2 Theta)
+    acc[4] = fmaf(twoB2, txx, fmaf(-rx, Px, fmaf(rx, Wx, acc[4] - nA)));
+    acc[5] = fmaf(twoB2, txy, fmaf(-ry, Px, fmaf(rx, Wy, acc[5])));
+    acc[6] = fmaf(twoB2, txz, fmaf(-rz, Px, fmaf(rx, Wz, acc[6])));
+    acc[7] = fmaf(twoB2, tyy, fmaf(-ry, Py, fmaf(ry, Wy, acc[7] - nA)));
+    acc[8] = fmaf(twoB2, tyz, fmaf(-rz, Py, fmaf(ry, Wz, acc[8])));
+    acc[9] = fmaf(twoB2, tzz, fmaf(-rz, Pz, fmaf(rz, Wz, acc[9] - nA)));
     if (FORCES) {
         const float B5 = fmaf(bc.c5, ex, 9.f * B4) * ri2;
-        const float A3 = q * B3 + s * B4 + u * B5;
+        const float A3 = fmaf(u, B5, fmaf(s, B4, q * B3));
         const float twoB4 = 2.f * B4;
-        const float Wx = rxA2 - Px, Wy = ryA2 - Py, Wz = rzA2 - Pz;   // r A2 - mu B2 - 2 Q B3
-        const float Zx = mx * B3 + twoB4 * Qx, Zy = my * B3 + twoB4 * Qy, Zz = mz * B3 + twoB4 * Qz;
-        // R = Theta_i r, u_i = r.R
-        const float Rx = T.xx * rx + T.xy * ry + T.xz * rz;
-        const float Ry = T.xy * rx + T.yy * ry + T.yz * rz;
-        const float Rz = T.xz * rx + T.yz * ry + T.zz * rz;
-        const float ui = rx * Rx + ry * Ry + rz * Rz;
-        // Theta_i W, Theta_k R, Theta_i : Theta_k
-        const float TWx = T.xx * Wx + T.xy * Wy + T.xz * Wz;
-        const float TWy = T.xy * Wx + T.yy * Wy + T.yz * Wz;
-        const float TWz = T.xz * Wx + T.yz * Wy + T.zz * Wz;
-        const float KRx = txx * Rx + txy * Ry + txz * Rz;
-        const float KRy = txy * Rx + tyy * Ry + tyz * Rz;
-        const float KRz = txz * Rx + tyz * Ry + tzz * Rz;
-        const float TK = T.xx * txx + T.yy * tyy + T.zz * tzz + 2.f * (T.xy * txy + T.xz * txz + T.yz * tyz);
-        const float sc = 2.f * (Rx * Zx + Ry * Zy + Rz * Zz) - twoB3 * TK - ui * A3;
-        const float fourB3 = 2.f * twoB3;
-        acc[10] += T.tr * Wx + 2.f * TWx + ui * Zx + rx * sc - fourB3 * KRx;
-        acc[11] += T.tr * Wy + 2.f * TWy + ui * Zy + ry * sc - fourB3 * KRy;
-        acc[12] += T.tr * Wz + 2.f * TWz + ui * Zz + rz * sc - fourB3 * KRz;
+        const float Zx = fmaf(twoB4, Qx, mx * B3), Zy = fmaf(twoB4, Qy, my * B3), Zz = fmaf(twoB4, Qz, mz * B3);
+        // R = Theta_i r, u_i = r.R, K R = Theta_k R, Theta_i : Theta_k
+        const float Rx = fmaf(T.xz, rz, fmaf(T.xy, ry, T.xx * rx));
+        const float Ry = fmaf(T.yz, rz, fmaf(T.yy, ry, T.xy * rx));
+        const float Rz = fmaf(T.zz, rz, fmaf(T.yz, ry, T.xz * rx));
+        const float ui = fmaf(rz, Rz, fmaf(ry, Ry, rx * Rx));
+        const float KRx = fmaf(txz, Rz, fmaf(txy, Ry, txx * Rx));
+        const float KRy = fmaf(tyz, Rz, fmaf(tyy, Ry, txy * Rx));
+        const float KRz = fmaf(tzz, Rz, fmaf(tyz, Ry, txz * Rx));
+        const float TK = fmaf(T.wyz, tyz, fmaf(T.wxz, txz, fmaf(T.wxy, txy,
+                         fmaf(T.zz, tzz, fmaf(T.yy, tyy, T.xx * txx)))));
+        const float RZ = fmaf(Rz, Zz, fmaf(Ry, Zy, Rx * Zx));
+        const float sc = fmaf(2.f, RZ, -fmaf(ui, A3, twoB3 * TK));   // 2 R.Z - Theta_i:Y - u_i A3
+        const float m4B3 = -2.f * twoB3;
+        // F = (2 Theta_i + tr Theta_i) W + u_i Z + r sc - 4 B3 Theta_k R
+        acc[10] = fmaf(m4B3, KRx, fmaf(rx, sc, fmaf(ui, Zx, fmaf(T.wxz, Wz, fmaf(T.wxy, Wy, fmaf(T.wxx, Wx, acc[10]))))));
+        acc[11] = fmaf(m4B3, KRy, fmaf(ry, sc, fmaf(ui, Zy, fmaf(T.wyz, Wz, fmaf(T.wyy, Wy, fmaf(T.wxy, Wx, acc[11]))))));
+        acc[12] = fmaf(m4B3, KRz, fmaf(rz, sc, fmaf(ui, Zz, fmaf(T.wzz, Wz, fmaf(T.wyz, Wy, fmaf(T.wxz, Wx, acc[12]))))));
     }
 }
 
-template <bool FORCES, bool SERIES>
-__global__ void __launch_bounds__(kNearWarps * 32)
+template <bool FORCES, int MODE>
+__global__ void __launch_bounds__(kNearWarps * 32, 7)
 k_near(Geo g, const int *__restrict__ start, const float4 *__restrict__ A0, const float4 *__restrict__ A1,
        const float4 *__restrict__ A2, const float4 *__restrict__ A3, BCoef bc, float *__restrict__ gnear,
-       int64_t Nslot, double *__restrict__ part)
+       int64_t Nslot, double *__restrict__ part, int *__restrict__ flag)
 {
     constexpr int K = NAcc<FORCES>::K;
     __shared__ float4 sSrc[kNearWarps][kNearChunk][4];
-    __shared__ int sSlot[kNearWarps][kNearChunk];
     __shared__ int sBeg[kNearWarps][28], sPre[kNearWarps][28];
     __shared__ float sRed[kNearWarps][K][32];
+    __shared__ int sZero[kNearWarps][32];
     __shared__ double sE[kNearWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n = g.n;
@@ -184,11 +199,14 @@ k_near(Geo g, const int *__restrict__ start, const float4 *__restrict__ A0, cons
             {
                 const float4 t2 = A2[si], t3 = A3[si];
                 TQ.xx = t2.x; TQ.xy = t2.y; TQ.xz = t2.z; TQ.yy = t2.w; TQ.yz = t3.x; TQ.zz = t3.y;
-                TQ.tr = t2.x + t2.w + t3.y;
+                const float tr = t2.x + t2.w + t3.y;
+                TQ.wxx = fmaf(2.f, t2.x, tr); TQ.wyy = fmaf(2.f, t2.w, tr); TQ.wzz = fmaf(2.f, t3.y, tr);
+                TQ.wxy = 2.f * t2.y; TQ.wxz = 2.f * t2.z; TQ.wyz = 2.f * t3.x;
             }
             float acc[K];
 #pragma unroll
             for (int k = 0; k < K; ++k) acc[k] = 0.f;
+            int nzero = 0;
             for (int c0 = 0; c0 < ns; c0 += kNearChunk) {
                 const int cs = min(kNearChunk, ns - c0);
                 __syncwarp();
@@ -212,16 +230,14 @@ k_near(Geo g, const int *__restrict__ start, const float4 *__restrict__ A0, cons
                     sSrc[warp][k][1] = make_float4(a1.x, a1.y, a1.z, a2.x + a2.w + a3.y);
                     sSrc[warp][k][2] = a2;
                     sSrc[warp][k][3] = a3;
-                    sSlot[warp][k] = slot;
                 }
                 __syncwarp();
                 if (active) {
 #pragma unroll 2
                     for (int k = grp; k < cs; k += G) {
-                        if (sSlot[warp][k] == si) continue;
                         const float4 s0 = sSrc[warp][k][0];
-                        src_fields<FORCES, SERIES>(ti.x - s0.x, ti.y - s0.y, ti.z - s0.z, s0, sSrc[warp][k][1],
-                                                   sSrc[warp][k][2], sSrc[warp][k][3], bc, TQ, acc);
+                        src_fields<FORCES, MODE>(ti.x - s0.x, ti.y - s0.y, ti.z - s0.z, s0, sSrc[warp][k][1],
+                                                 sSrc[warp][k][2], sSrc[warp][k][3], bc, TQ, acc, nzero);
                     }
                 }
             }
@@ -229,8 +245,13 @@ k_near(Geo g, const int *__restrict__ start, const float4 *__restrict__ A0, cons
             __syncwarp();
 #pragma unroll
             for (int k = 0; k < K; ++k) sRed[warp][k][lane] = active ? acc[k] : 0.f;
+            sZero[warp][lane] = active ? nzero : 0;
             __syncwarp();
             if (lane < nt) {
+                // exactly one zero-distance pair (the target itself) is expected
+                int z = sZero[warp][lane];
+                for (int gq = 1; gq < G; ++gq) z += sZero[warp][lane + gq * nt];
+                if (z != 1) atomicOr(flag, 4);
 #pragma unroll
                 for (int k = 0; k < K; ++k) {
                     float v = sRed[warp][k][lane];
@@ -284,15 +305,16 @@ k_near(Geo g, const int *__restrict__ start, const float4 *__restrict__ A0, cons
 int near_blocks(const Handle &H)
 {
     (void)H;
-    return 152 * 5;
+    return 152 * 7;   // 7 blocks of 128 threads per SM (<= 73 registers per thread)
 }
 
 cudaError_t launch_near(Handle &H, bool forces, cudaStream_t s)
 {
     BCoef bc;
     const double xi = H.g.xi;
+    const double log2e = 1.4426950408889634;
     bc.xi = (float)xi;
-    bc.xi2 = (float)(xi * xi);
+    bc.kap = (float)(xi * xi * log2e);
     double c = 1.0 / (xi * sqrt(M_PI));
     double cl[6];
     for (int l = 1; l <= 5; ++l) {
@@ -300,32 +322,35 @@ cudaError_t launch_near(Handle &H, bool forces, cudaStream_t s)
         cl[l] = c;
     }
     bc.c1 = (float)cl[1]; bc.c2 = (float)cl[2]; bc.c3 = (float)cl[3]; bc.c4 = (float)cl[4]; bc.c5 = (float)cl[5];
-    // erf(x) = (2/sqrt(pi)) sum_k (-1)^k x^(2k+1) / (k! (2k+1))  (Maclaurin series)
-    double fact = 1.0;
+    // erf(z) = (2/sqrt(pi)) sum_k (-1)^k z^(2k+1) / (k! (2k+1))  (Maclaurin series), z = xi r,
+    // so erf(xi r)/r = sum_k a_k y^k with y = xi^2 r^2 log2(e)
+    double fact = 1.0, l2k = 1.0;
     for (int k = 0; k < 8; ++k) {
-        if (k > 0) fact *= k;
-        bc.e[k] = (float)((k % 2 ? -1.0 : 1.0) * 2.0 / sqrt(M_PI) / (fact * (2 * k + 1)));
+        if (k > 0) {
+            fact *= k;
+            l2k *= log2e;
+        }
+        bc.a[k] = (float)((k % 2 ? -1.0 : 1.0) * 2.0 * xi / sqrt(M_PI) / (fact * (2 * k + 1) * l2k));
     }
-    const double rmax = 2.0 * sqrt(3.0) * H.g.h;   // farthest pair of adjacent leaves
-    bc.series = (xi * rmax <= 0.5) ? 1 : 0;
+    const double zmax = xi * 2.0 * sqrt(3.0) * H.g.h;   // xi times the farthest pair of adjacent leaves
+    const int mode = zmax <= 0.2 ? kSeriesShort : (zmax <= 0.5 ? kSeriesLong : kErfcLib);
     double *part = H.d_part + H.part_off[kPartNear];
     const int nb = near_blocks(H);
     const int64_t S = H.N;
+    const dim3 grid(nb), block(kNearWarps * 32);
+#define ANKH_NEAR_LAUNCH(F, M) \
+    k_near<F, M><<<grid, block, 0, s>>>(H.g, H.d_start, H.d_A0, H.d_A1, H.d_A2, H.d_A3, bc, H.d_gnear, S, part, \
+                                        H.d_flag)
     if (forces) {
-        if (bc.series)
-            k_near<true, true><<<nb, kNearWarps * 32, 0, s>>>(H.g, H.d_start, H.d_A0, H.d_A1, H.d_A2, H.d_A3, bc,
-                                                              H.d_gnear, S, part);
-        else
-            k_near<true, false><<<nb, kNearWarps * 32, 0, s>>>(H.g, H.d_start, H.d_A0, H.d_A1, H.d_A2, H.d_A3, bc,
-                                                               H.d_gnear, S, part);
+        if (mode == kSeriesShort) ANKH_NEAR_LAUNCH(true, kSeriesShort);
+        else if (mode == kSeriesLong) ANKH_NEAR_LAUNCH(true, kSeriesLong);
+        else ANKH_NEAR_LAUNCH(true, kErfcLib);
     } else {
-        if (bc.series)
-            k_near<false, true><<<nb, kNearWarps * 32, 0, s>>>(H.g, H.d_start, H.d_A0, H.d_A1, H.d_A2, H.d_A3, bc,
-                                                               H.d_gnear, S, part);
-        else
-            k_near<false, false><<<nb, kNearWarps * 32, 0, s>>>(H.g, H.d_start, H.d_A0, H.d_A1, H.d_A2, H.d_A3,
-                                                                bc, H.d_gnear, S, part);
+        if (mode == kSeriesShort) ANKH_NEAR_LAUNCH(false, kSeriesShort);
+        else if (mode == kSeriesLong) ANKH_NEAR_LAUNCH(false, kSeriesLong);
+        else ANKH_NEAR_LAUNCH(false, kErfcLib);
     }
+#undef ANKH_NEAR_LAUNCH
     return cudaGetLastError();
 }
 

@@ -220,6 +220,23 @@ def test_nonfinite_input_reports_enumeric(api):
     del torch
 
 
+def test_coincident_atoms_report_enumeric(api):
+    """Two distinct atoms at one position (infinite energy) are reported as
+    ANKH_ENUMERIC by both entry points; a clean call afterwards is unchanged."""
+    b = synth.small_box(100, 3, box=14.0)
+    m = api.Ankh(b.box, b.n, n_cells=3)
+    x, q, mu, th = to_dev(b)
+    E0 = m.energy(x, q, mu, th)
+    for other in (7, 60):
+        xd = x.clone()
+        xd[other] = xd[5]
+        for call in (m.energy, m.energy_forces):
+            with pytest.raises(api.AnkhError) as e:
+                call(xd, q, mu, th)
+            assert e.value.code == api.ANKH_ENUMERIC
+    assert m.energy(x, q, mu, th) == E0
+
+
 def test_host_entry_point_matches_device(api):
     b = synth.small_box(600, 8, box=26.0)
     m, E, g = run_gpu(api, b, n=6, Lu=5)
