@@ -38,6 +38,11 @@ UNIT = "evals/s"
 NEAR_FLOPS_PER_PAIR = 560
 FP32_LANES_PER_SM = 128
 N_SM = 152
+# DRAM bytes (read + write) per launch from one ncu capture of the same kernel
+# code on the same workload (profiles/); keyed by (kernel, workload, n, L_u)
+DRAM_TRAFFIC = {
+    ("near", "water_1008000_qmuTheta", 54, 5): 73.565440e6 + 28.277248e6,   # profiles/k_near_water1008000_n54.md
+}
 
 
 def env_int(k, d):
@@ -363,19 +368,24 @@ def main():
     ncell = n ** 3
     models = {
         "near": ("alu", pairs * NEAR_FLOPS_PER_PAIR / 1e12, fp32_peak, "TFLOP/s"),
+        # algorithmic flop of the correction (unpadded P nodes, n^3 leaves); the
+        # fp16 split executes three products of each, at the fp16 = bf16 rate
         "corr": ("tensor" if not args.plain else "alu", 2 * 27 * P * P * ncell / 1e12,
-                 (peaks["bf16_tflops"] / 2.0) if not args.plain else fp32_peak, "TFLOP/s"),
+                 peaks["bf16_tflops"] if not args.plain else fp32_peak, "TFLOP/s"),
         "p2m": ("hbm", (52 * N + 4 * ncell * P) / 1e9, peaks["hbm_gbs"], "GB/s"),
         "l2p": ("hbm", (52 * N + 8 * ncell * P + 52 * N) / 1e9, peaks["hbm_gbs"], "GB/s"),
     }
-    roof = None
-    if dom in models:
-        bound, work, peak, unit = models[dom]
-        achieved = work / (stage_ms[dom] / 1e3)
-        roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": None,
+
+    def roofline(k):
+        bound, work, peak, unit = models[k]
+        achieved = work / (stage_ms[k] / 1e3)
+        return {"kernel": k, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak, "traffic": DRAM_TRAFFIC.get((k, box.name, n, info["Lu"])),
                 "peak_source": (f"FP32: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz "
                                 f"(sampled clock)" if bound == "alu" else f"{peak_kind} MEASURED_PEAKS")}
+
+    roof = roofline(dom) if dom in models else None
+    roof_all = [roofline(k) for k in models if k in stage_ms and stage_ms[k] > 0]
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -390,7 +400,7 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": box.name + "_energy_forces", "n_atoms": N, "box_A": round(box.box, 4),
                        "n_cells": n, "Lu": info["Lu"], "Lc": info["Lc"], "nf": info["nf"], "xi": 0.01,
-                       "precision": "plain_fp32" if args.plain else "mixed_3xtf32_correction",
+                       "precision": "plain_fp32" if args.plain else "mixed_2xfp16_correction",
                        "l2": "flushed: 256 MiB write between timed steps", "parallelism": f"replicas{world}",
                        "leaf_count": "autotuned" if args.n_cells == 0 else "fixed", "autotune_ms": tune},
             "matoms_per_s": value * N / 1e6,
@@ -400,6 +410,7 @@ def main():
             "accuracy": acc,
             "clocks": clk,
             "roofline": roof,
+            "rooflines": roof_all,
             "cpu_baseline": cpu,
             "e2e": {"value": world * args.e2e_steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},

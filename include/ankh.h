@@ -48,8 +48,10 @@ enum {
                                 Ewald energy; without it E_rec(xi) is neglected
                                 as in Sec. 3.1) -- default on */
 #define ANKH_MIXED 2u        /* adjacent-leaf correction on the tensor cores
-                                (3xTF32 split, FP32 accumulate); otherwise plain
-                                FP32 on the CUDA cores */
+                                (operands scaled by powers of two and split
+                                into fp16 hi + lo, three products, FP32
+                                accumulate: ~22 significant bits); otherwise
+                                plain FP32 on the CUDA cores */
 
 typedef struct {
     double xi;        /* Ewald screening [1/A]; Sec. 5 uses 0.01 */

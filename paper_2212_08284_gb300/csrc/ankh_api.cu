@@ -129,21 +129,6 @@ static std::vector<double> make_C(int Lu, int ldm, double delta, double xi)
     return C;
 }
 
-// Round an FP32 value to TF32 (10 explicit mantissa bits), nearest, ties away
-// from zero -- the rounding of cvt.rna.tf32.f32.
-static float tf32_round(float x)
-{
-    uint32_t u;
-    std::memcpy(&u, &x, 4);
-    if ((u & 0x7f800000u) != 0x7f800000u) {
-        u += 0x1000u;
-        u &= 0xffffe000u;
-    }
-    float r;
-    std::memcpy(&r, &u, 4);
-    return r;
-}
-
 static bool good_fft_size(int m)
 {
     for (int p : {2, 3, 5, 7})
@@ -175,7 +160,7 @@ static void free_device(Handle *H)
     void *ptrs[] = {H->d_cellid, H->d_rank, H->d_count, H->d_start, H->d_perm, H->d_scell, H->d_flag, H->d_bsum,
                     H->d_A0, H->d_A1, H->d_A2, H->d_A3, H->d_W, H->d_M, H->d_rho, H->d_rhohat, H->d_D,
                     H->d_phi, H->d_C, H->d_Chi, H->d_Clo, H->d_psi, H->d_gnear, H->d_part,
-                    H->d_partoff, H->d_terms, H->d_hostbuf, H->d_Mhi, H->d_Mlo};
+                    H->d_partoff, H->d_terms, H->d_hostbuf, H->d_Mhi, H->d_Mlo, H->d_mmax};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (H->h_terms) cudaFreeHost(H->h_terms);
@@ -368,12 +353,7 @@ int ankh_create(double box_edge, int64_t N, const ankh_params *params, ankh_hand
     int nb[kPartCount];
     nb[kPartNear] = near_blocks(H);
     nb[kPartGlob] = spectral_blocks(H);
-    {
-        // tensor-core tiles: ceil(n^2 / R) z-row groups (S = roundup16(n) leaves each)
-        // times the 128-row slices of the ldm target nodes
-        const int S = ((n + 15) / 16) * 16, R = std::max(1, 128 / S);
-        nb[kPartCorr] = std::max(corr_blocks(H), ((n * n + R - 1) / R) * ((g.ldm + 127) / 128));
-    }
+    nb[kPartCorr] = std::max(corr_blocks(H), tc_max_blocks(n, g.ldm));   // SIMT or tensor-core CTAs
     nb[kPartSelf] = self_blocks(H);
     nb[kPartQ] = self_blocks(H);
     H.part_off[0] = 0;
@@ -401,29 +381,38 @@ int ankh_create(double box_edge, int64_t N, const ankh_params *params, ankh_hand
             return bail(ANKH_ECUDA, "upload C");
     }
     if ((p.flags & ANKH_MIXED) && g.ldm % 32 == 0 && g.ldm <= 512 && n <= 128) {
-        const int S = ((n + 15) / 16) * 16;
+        int S, R;
+        tc_tile_shape(n, S, R);
+        H.tc.ldk = tc_ldk(g.ldm);
+        const int ldk = H.tc.ldk;
         const int64_t rows = (int64_t)n * n * (S + 2);
         const int halves = (g.ldm + 127) / 128;
-        const int64_t acols = (int64_t)27 * g.ldm, arows = (int64_t)halves * 128;
-        ANKH_AL(H.d_Mhi, rows * g.ldm);
-        ANKH_AL(H.d_Mlo, rows * g.ldm);
+        const int64_t acols = (int64_t)27 * ldk, arows = (int64_t)halves * 128;
+        ANKH_AL(H.d_Mhi, rows * ldk);
+        ANKH_AL(H.d_Mlo, rows * ldk);
         ANKH_AL(H.d_Chi, arows * acols);
         ANKH_AL(H.d_Clo, arows * acols);
-        cudaMemset(H.d_Mhi, 0, sizeof(float) * rows * g.ldm);
-        cudaMemset(H.d_Mlo, 0, sizeof(float) * rows * g.ldm);
-        // A = [C_0 | ... | C_26] as [halves*128 rows][27*ldm], split hi/lo (round to nearest TF32)
+        ANKH_AL(H.d_mmax, 1);
+        cudaMemset(H.d_Mhi, 0, sizeof(__half) * rows * ldk);
+        cudaMemset(H.d_Mlo, 0, sizeof(__half) * rows * ldk);
+        // A = 2^eC [C_0 | ... | C_26] as [halves*128 rows][27*ldk], split into fp16 hi + lo
+        // (round to nearest), eC from max |C| so that the largest entry is <= 2^14
         std::vector<double> C = make_C(g.Lu, g.ldm, g.h / (g.Lu - 1), p.xi);
-        std::vector<float> Ah((size_t)(arows * acols), 0.f), Al((size_t)(arows * acols), 0.f);
+        double cmax = 0.0;
+        for (double v : C) cmax = std::max(cmax, std::fabs(v));
+        H.tc.eC = split_exponent((float)cmax);
+        const float cs = std::ldexp(1.f, H.tc.eC);
+        std::vector<__half> Ah((size_t)(arows * acols), __float2half_rn(0.f)), Al(Ah);
         for (int d = 0; d < 27; ++d)
             for (int m = 0; m < g.ldm; ++m)
                 for (int l = 0; l < g.ldm; ++l) {
-                    const float v = (float)C[((size_t)d * g.ldm + m) * g.ldm + l];
-                    const float hi = tf32_round(v);
-                    Ah[(size_t)m * acols + (size_t)d * g.ldm + l] = hi;
-                    Al[(size_t)m * acols + (size_t)d * g.ldm + l] = tf32_round(v - hi);
+                    const float v = (float)C[((size_t)d * g.ldm + m) * g.ldm + l] * cs;
+                    const __half hi = __float2half_rn(v);
+                    Ah[(size_t)m * acols + (size_t)d * ldk + l] = hi;
+                    Al[(size_t)m * acols + (size_t)d * ldk + l] = __float2half_rn(v - __half2float(hi));
                 }
-        if (cudaMemcpy(H.d_Chi, Ah.data(), Ah.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(H.d_Clo, Al.data(), Al.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+        if (cudaMemcpy(H.d_Chi, Ah.data(), Ah.size() * sizeof(__half), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(H.d_Clo, Al.data(), Al.size() * sizeof(__half), cudaMemcpyHostToDevice) != cudaSuccess)
             return bail(ANKH_ECUDA, "upload tensor-core blocks");
         std::string terr;
         if (!tc_prepare(H, terr)) return bail(ANKH_ECUDA, terr);

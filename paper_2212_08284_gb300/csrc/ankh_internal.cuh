@@ -4,6 +4,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cufft.h>
+#include <cuda_fp16.h>
 #include <cstdint>
 #include <string>
 
@@ -41,6 +42,9 @@ enum PartSlot { kPartNear = 0, kPartGlob = 1, kPartCorr = 2, kPartSelf = 3, kPar
 struct TcPlan {
     int enabled;
     int S, R, rowstride, N, tiles, halves;
+    int grid;               // persistent CTAs (one per SM)
+    int ldk;                // node stride of the fp16 operands (ldm rounded up to 64)
+    int eC;                 // C_d scaled by 2^eC before the fp16 split
     uint32_t tmem_cols;
     CUtensorMap mAhi, mAlo, mBhi, mBlo;
 };
@@ -48,7 +52,9 @@ struct TcPlan {
 struct Handle {
     Geo g;
     TcPlan tc;
-    float *d_Mhi, *d_Mlo;   // [n*n*rowstride][128] TF32 split of M, z-halo padded (tensor-core path)
+    __half *d_Mhi, *d_Mlo;  // [n*n*rowstride][ldk] fp16 split of 2^eM M, z-halo rows (tensor-core path)
+    __half *d_Chi, *d_Clo;  // [halves*128][27*ldk] fp16 split of 2^eC [C_0 | ... | C_26]
+    unsigned *d_mmax;       // max |M| of the call (FP32 bits), sets eM
     int64_t N;
     int max_order;
     unsigned flags;
@@ -68,7 +74,6 @@ struct Handle {
     float *d_D;             // [nf][nf][nfh] real spectrum of the far-field kernel (k = 0 removed)
     float *d_phi;           // [nf^3] merged grid potential (unnormalised c2r output)
     float *d_C;             // [27][ldm][ldm] adjacent-leaf correction blocks (FP32)
-    float *d_Chi, *d_Clo;   // same, split into TF32 high / low parts for the tensor-core path
     float *d_psi;           // [ncell][ldm] correction potential
     float *d_gnear;         // [13][Nslot] near-field gradient per sorted slot
     double *d_part;         // energy partials
@@ -116,6 +121,10 @@ cudaError_t launch_reduce(Handle &H, cudaStream_t s);
 cudaError_t precompute_kernel_spectrum(Handle &H, double *D0_out, std::string &err);
 
 bool tc_prepare(Handle &H, std::string &err);
+void tc_tile_shape(int n, int &S, int &R);
+int tc_max_blocks(int n, int ldm);   // CTAs of the tensor-core correction (energy partial slots)
+int tc_ldk(int ldm);                 // node stride of the fp16 split operands
+int split_exponent(float maxabs);    // e with max |x| 2^e <= 2^14 (0 for 0 or non-finite)
 int corr_tc_blocks(const Handle &H);
 cudaError_t launch_corr_tc(Handle &H, bool forces, cudaStream_t s);
 

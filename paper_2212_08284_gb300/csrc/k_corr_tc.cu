@@ -3,30 +3,35 @@
 // Same contraction as k_corr.cu (see there for the definition):
 //   Psi[ldm x N] = sum_{d=0..26} C_d[ldm x ldm] . B_d[ldm x N],
 //   B_d[:, j] = M_{t_j + d},
-// one CTA per 128-row slice of the target nodes (blockIdx.y; ldm = 128 for
-// L_u = 5, 224 for L_u = 6, rows beyond ldm are zero),
-// for a tile of N target leaves (R z-rows of the leaf grid, each padded to S
-// columns).  Split precision "3xTF32": every FP32 operand x is written as
-// x_hi + x_lo with x_hi = tf32(x) (round to nearest) and x_lo = tf32(x - x_hi);
-// C.M is accumulated in FP32 as C_hi.M_hi + C_hi.M_lo + C_lo.M_hi, which
-// keeps ~21 bits of every product.
+// for tiles of N target leaves (R z-rows of the leaf grid, each padded to S
+// columns, N = R S <= 128) and 128-row slices of the target nodes (ldm = 128
+// for L_u = 5; 224 for L_u = 6, two slices; rows beyond ldm are zero).
+//
+// Split precision "2xFP16": every FP32 operand x is scaled by a power of two
+// (2^eC for C, fixed per box; 2^eM for M, from max |M| of the call, so that
+// the largest scaled value is <= 2^14) and written as x_hi + x_lo with
+// x_hi = fp16(x), x_lo = fp16(x - x_hi), both rounded to nearest: 11 + 11
+// significant bits, ~2^-22 relative (an absolute floor of 2^-24 below the
+// normal range of x_lo, i.e. ~1e-12 of the largest value).  C.M is
+// accumulated in FP32 as C_hi.M_hi + C_hi.M_lo + C_lo.M_hi (kind::f16, twice
+// the TF32 rate, half the bytes) and scaled back by 2^-(eC + eM) (exact).
 //
 // Data movement: A (= [C_0 | ... | C_26], hi and lo) and B (the leaf rows of
-// the modified charges, hi and lo, stored with a one-leaf halo along z so
-// that the rows t + d of a z-row form one contiguous block) are fetched by
-// TMA with the 128-byte swizzle into a 3-stage shared-memory ring; one thread
-// issues tcgen05.mma (kind::tf32, M = 128, K = 8) into an FP32 accumulator in
-// tensor memory; four epilogue warps read it back with tcgen05.ld, write the
-// correction potential psi and form -1/2 sum M.psi in FP64.
+// the split modified charges, stored with a one-leaf halo along z so that
+// the rows t + d of a z-row form one contiguous block) are fetched by TMA
+// with the 128-byte swizzle (64 halves of K per row) into a 3-stage
+// shared-memory ring; one thread issues tcgen05.mma (M = 128, K = 16) into
+// FP32 accumulators in tensor memory; four epilogue warps read them back
+// with tcgen05.ld, write the correction potential psi and form
+// -1/2 sum M.psi in FP64.
 //
-// The tensor core rounds toward zero as it accumulates; over the 27 x 48 MMA
-// steps of a tile that bias reaches ~4e-5.  So the large C_hi.M_hi products
-// of one stage (K = 32, four MMAs) go to one of three TMEM buffers and are
-// drained after the stage into FP32 registers with round-to-nearest
+// The tensor core rounds toward zero as it accumulates, so the large
+// C_hi.M_hi products of one stage (four MMAs) go to one of two TMEM buffers
+// and are drained after the stage into FP32 registers with round-to-nearest
 // additions, while the next stage accumulates into the other buffer.  The
 // small C_hi.M_lo + C_lo.M_hi corrections (2^-11 of the large ones) stay in a
-// third TMEM accumulator for the whole tile; their truncation bias is
-// relative to their own small size and negligible.
+// per-tile TMEM accumulator; their truncation bias is relative to their own
+// small size and negligible.
 //
 // Every wait is bounded (clock64 budget); on timeout the kernel raises bit 2
 // of the error flag, waits (bounded) for its own copies in flight, frees its
@@ -34,17 +39,23 @@
 #include "ankh_internal.cuh"
 
 #include <cudaTypedefs.h>
+#include <cuda_fp16.h>
+
+#include <cmath>
 
 namespace ankh {
 
 namespace tcg {
 
 constexpr int kStages = 3;
-constexpr int kAccBufs = 3;            // large-product accumulator buffers in TMEM
+constexpr int kAccBufs = 2;            // large-product buffers in TMEM (plus two small accumulators)
+constexpr int kMaxN = 128;             // leaves per tile (MMA N)            // large-product accumulator buffers in TMEM
 constexpr int kRows = 128;            // target-node rows per CTA (MMA M)
-constexpr int kKc = 32;               // K floats per stage (128 bytes)
+constexpr int kKc = 64;               // K halves per stage (one 128-byte swizzle row)
+constexpr int kRowBytes = kKc * 2;
 constexpr int kThreads = 192;         // warps 0-3 epilogue, 4 TMA producer, 5 MMA issuer
-constexpr uint32_t kABytes = kRows * kKc * 4;
+constexpr uint32_t kABytes = kRows * kRowBytes;
+constexpr int kMaxScaled = 14;         // largest scaled operand <= 2^14 (fp16 max 65504)
 constexpr long long kBudget = 4000000000LL;   // ~2 s at 2 GHz
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -104,18 +115,18 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr)
     return d;
 }
 
-// Instruction descriptor, kind::tf32: D = F32, A = B = TF32, both K-major.
-__host__ __device__ constexpr uint32_t idesc_tf32(int m, int n)
+// Instruction descriptor, kind::f16: D = F32, A = B = F16, both K-major.
+__host__ __device__ constexpr uint32_t idesc_f16(int m, int n)
 {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+    return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t dtm, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+__device__ __forceinline__ void mma_f16(uint32_t dtm, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
 {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtm),
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtm),
         "l"(a), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
 }
@@ -160,36 +171,138 @@ __device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t *r)
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+__device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t *r)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float *v)
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+        "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+        "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+        "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+        "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+        "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+        "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])),
+        "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])), "r"(__float_as_uint(v[20])),
+        "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])), "r"(__float_as_uint(v[23])),
+        "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])),
+        "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])),
+        "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31]))
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
+}
+
 }  // namespace tcg
 
+// Exponent e with max |x| * 2^e <= 2^14 (0 for max = 0 or a non-finite max).
+__device__ __forceinline__ int split_exponent_dev(float maxabs)
+{
+    if (!(maxabs > 0.f) || !(maxabs <= 3.0e38f)) return 0;
+    int ex;
+    frexpf(maxabs, &ex);   // maxabs = f 2^ex, f in [0.5, 1)
+    return tcg::kMaxScaled - ex;
+}
+
+int split_exponent(float maxabs)
+{
+    if (!(maxabs > 0.f) || !(maxabs <= 3.0e38f)) return 0;
+    int ex;
+    std::frexp(maxabs, &ex);
+    return tcg::kMaxScaled - ex;
+}
+
+// Split of M for the tensor cores: rows of each z-row with a one-leaf halo
+// (row j of z-row zr holds leaf z = n-1, 0, ..., n-1, 0 for j = 0 .. n+1),
+// nodes padded to ldk with zeros, scaled by 2^eM and split into fp16 hi + lo.
+// One thread per 8 nodes of a row.
+__global__ void __launch_bounds__(256)
+k_split_f16(Geo g, int ldk, int rowstride, const float *__restrict__ M, const unsigned *__restrict__ mmax,
+            __half *__restrict__ Mhi, __half *__restrict__ Mlo)
+{
+    const int n = g.n, per_row = ldk / 8;
+    const int64_t nrows = (int64_t)n * n * (n + 2);
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nrows * per_row) return;
+    const int64_t r = t / per_row;
+    const int node0 = (int)(t % per_row) * 8;
+    const int j = (int)(r % (n + 2));
+    const int64_t zr = r / (n + 2);
+    const int cz = j == 0 ? n - 1 : (j == n + 1 ? 0 : j - 1);
+    const float scale = ldexpf(1.f, split_exponent_dev(__uint_as_float(*mmax)));
+    float v[8];
+    if (node0 < g.ldm) {
+        const float4 *src = reinterpret_cast<const float4 *>(M + (zr * n + cz) * g.ldm + node0);
+        const float4 a = src[0], b = src[1];
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = 0.f;
+    }
+    __align__(16) __half hi[8], lo[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const float x = v[q] * scale;
+        hi[q] = __float2half_rn(x);
+        lo[q] = __float2half_rn(x - __half2float(hi[q]));
+    }
+    const int64_t o = (zr * rowstride + j) * ldk + node0;
+    *reinterpret_cast<uint4 *>(Mhi + o) = *reinterpret_cast<const uint4 *>(hi);
+    *reinterpret_cast<uint4 *>(Mlo + o) = *reinterpret_cast<const uint4 *>(lo);
+}
+
+// Persistent kernel: one CTA per SM walks the work items w = blockIdx.x,
+// blockIdx.x + gridDim.x, ... (tile = w mod tiles, row slice = w / tiles);
+// the TMA ring, the MMA stream and the drains run across item boundaries.
+// TMEM (512 columns): two large-product buffers (drained after every stage)
+// and two small-product accumulators, one per item parity.  When an item's
+// last stage is drained, the epilogue warps fold their FP32 registers into
+// that item's small accumulator (which then holds psi) and finish it -- the
+// energy dot with M and the psi write, 8 columns per stage -- while the next
+// item's MMAs run; the small accumulator is then released for the item after.
 template <bool FORCES>
 __global__ void __launch_bounds__(tcg::kThreads, 1)
 k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
           const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo, Geo g, int S,
-          int R, int rowstride, uint32_t tmem_cols, const float *__restrict__ M, float *__restrict__ psi,
-          double *__restrict__ part, int *__restrict__ errflag)
+          int R, int rowstride, int ldk, int eC, const unsigned *__restrict__ mmax, int ntiles, int nwork,
+          uint32_t tmem_cols, const float *__restrict__ M, float *__restrict__ psi, double *__restrict__ part,
+          int *__restrict__ errflag)
 {
     using namespace tcg;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem =
         reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    const int N = R * S;
-    const uint32_t bbytes = (uint32_t)N * kKc * 4;
+    const int N = R * S;                   // <= kMaxN
+    const uint32_t bbytes = (uint32_t)N * kRowBytes;
     const uint32_t stage = 2 * kABytes + 2 * bbytes;
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStages * stage);
     uint64_t *empty = full + kStages;
-    uint64_t *acc_full = empty + kStages;     // [kAccBufs] accumulator buffer ready for draining
-    uint64_t *acc_empty = acc_full + kAccBufs; // [kAccBufs] buffer drained (4 warp arrivals)
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + kAccBufs);
+    uint64_t *acc_full = empty + kStages;       // [kAccBufs] large buffer ready for draining
+    uint64_t *acc_empty = acc_full + kAccBufs;  // [kAccBufs] large buffer drained (4 warp arrivals)
+    uint64_t *small_free = acc_empty + kAccBufs;  // [2] small accumulator finished (4 warp arrivals)
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(small_free + 2);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     volatile int *issued = abort_flag + 1;
     __shared__ double red[4];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ldm = g.ldm;
-    const int kch = ldm / kKc;            // K chunks per offset d
-    const int kIters = 27 * kch;
-    const int row0 = blockIdx.y * kRows;  // first target-node row of this CTA
+    const int kch = ldk / kKc;            // K chunks per offset d
+    const int kIters = 27 * kch;          // stages per work item
+    const int nmine = blockIdx.x < nwork ? (nwork - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int total = nmine * kIters;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&full[s], 1);
@@ -199,6 +312,7 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
             mbar_init(&acc_full[b], 1);
             mbar_init(&acc_empty[b], 4);
         }
+        for (int p = 0; p < 2; ++p) mbar_init(&small_free[p], 4);
         *abort_flag = 0;
         *issued = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -217,40 +331,47 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
 
     if (warp == 4 && lane == 0) {
         // TMA producer
-        for (int it = 0; it < kIters; ++it) {
-            const int s = it % kStages, k = it / kStages;
-            if (it >= kStages && !mbar_wait(&empty[s], (uint32_t)((k - 1) & 1), kBudget)) {
+        for (int gi = 0; gi < total; ++gi) {
+            const int s = gi % kStages, k = gi / kStages;
+            if (gi >= kStages && !mbar_wait(&empty[s], (uint32_t)((k - 1) & 1), kBudget)) {
                 *abort_flag = 1;
                 break;
             }
             if (*abort_flag) break;
+            const int w = (int)blockIdx.x + (gi / kIters) * (int)gridDim.x, it = gi % kIters;
+            const int tile = w % ntiles, row0 = (w / ntiles) * kRows;
             const int d = it / kch, kc = it % kch;
             const int dx = d / 9 - 1, dy = (d / 3) % 3 - 1, dz = d % 3 - 1;
             unsigned char *st = smem + (size_t)s * stage;
             mbar_expect_tx(&full[s], stage);
-            tma_2d(st, &tmAhi, &full[s], d * ldm + kc * kKc, row0);
-            tma_2d(st + kABytes, &tmAlo, &full[s], d * ldm + kc * kKc, row0);
+            tma_2d(st, &tmAhi, &full[s], d * ldk + kc * kKc, row0);
+            tma_2d(st + kABytes, &tmAlo, &full[s], d * ldk + kc * kKc, row0);
             for (int r = 0; r < R; ++r) {
-                int zrow = blockIdx.x * R + r;
+                int zrow = tile * R + r;
                 if (zrow >= nrow) zrow = nrow - 1;
                 const int cx = zrow / n, cy = zrow % n;
                 const int ncx = (cx + dx + n) % n, ncy = (cy + dy + n) % n;
                 const int brow = (ncx * n + ncy) * rowstride + 1 + dz;
-                tma_2d(st + 2 * kABytes + (size_t)r * S * kKc * 4, &tmBhi, &full[s], kc * kKc, brow);
-                tma_2d(st + 2 * kABytes + bbytes + (size_t)r * S * kKc * 4, &tmBlo, &full[s], kc * kKc, brow);
+                tma_2d(st + 2 * kABytes + (size_t)r * S * kRowBytes, &tmBhi, &full[s], kc * kKc, brow);
+                tma_2d(st + 2 * kABytes + bbytes + (size_t)r * S * kRowBytes, &tmBlo, &full[s], kc * kKc, brow);
             }
-            *issued = it + 1;
+            *issued = gi + 1;
         }
     } else if (warp == 5 && lane == 0) {
         // MMA issuer: large products of each stage into one of two TMEM buffers
-        // (drained by the epilogue warps), small corrections into a third one
-        const uint32_t idesc = idesc_tf32(kRows, N);
-        const uint32_t small = tmem + (uint32_t)(kAccBufs * N);
+        // (drained by the epilogue warps), small corrections into the item's
+        // small accumulator
+        const uint32_t idesc = idesc_f16(kRows, N);
         int consumed = 0;
-        for (int it = 0; it < kIters; ++it) {
-            const int s = it % kStages, k = it / kStages, buf = it % kAccBufs;
-            if (it >= kAccBufs &&
-                !mbar_wait(&acc_empty[buf], (uint32_t)(((it / kAccBufs) - 1) & 1), kBudget)) {
+        for (int gi = 0; gi < total; ++gi) {
+            const int s = gi % kStages, k = gi / kStages, b = gi % kAccBufs, u = gi / kAccBufs;
+            const int j = gi / kIters, it = gi % kIters, par = j & 1;
+            if (it == 0 && j >= 2 &&
+                !mbar_wait(&small_free[par], (uint32_t)(((j >> 1) - 1) & 1), kBudget)) {
+                *abort_flag = 1;
+                break;
+            }
+            if (gi >= kAccBufs && !mbar_wait(&acc_empty[b], (uint32_t)((u - 1) & 1), kBudget)) {
                 *abort_flag = 1;
                 break;
             }
@@ -258,108 +379,141 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
                 *abort_flag = 1;
                 break;
             }
-            consumed = it + 1;
+            consumed = gi + 1;
             fence_after();
-            const uint32_t big = tmem + (uint32_t)(buf * N);
+            const uint32_t big = tmem + (uint32_t)(b * N);
+            const uint32_t small = tmem + (uint32_t)((kAccBufs + par) * N);
             const uint32_t base = su32(smem + (size_t)s * stage);
             const uint32_t ahi = base, alo = base + kABytes, bhi = base + 2 * kABytes, blo = bhi + bbytes;
 #pragma unroll
-            for (int k8 = 0; k8 < kKc / 8; ++k8) {
-                const uint32_t off = k8 * 32;
-                mma_tf32(big, desc_sw128(ahi + off), desc_sw128(bhi + off), idesc, k8 > 0 ? 1u : 0u);
-                mma_tf32(small, desc_sw128(ahi + off), desc_sw128(blo + off), idesc, (it > 0 || k8 > 0) ? 1u : 0u);
-                mma_tf32(small, desc_sw128(alo + off), desc_sw128(bhi + off), idesc, 1u);
+            for (int k16 = 0; k16 < kKc / 16; ++k16) {
+                const uint32_t off = k16 * 32;   // 16 halves = 32 bytes along the swizzled row
+                mma_f16(big, desc_sw128(ahi + off), desc_sw128(bhi + off), idesc, k16 > 0 ? 1u : 0u);
+                mma_f16(small, desc_sw128(ahi + off), desc_sw128(blo + off), idesc, (it > 0 || k16 > 0) ? 1u : 0u);
+                mma_f16(small, desc_sw128(alo + off), desc_sw128(bhi + off), idesc, 1u);
             }
             mma_commit(&empty[s]);
-            mma_commit(&acc_full[buf]);
+            mma_commit(&acc_full[b]);
         }
         if (*abort_flag) {
             // release the epilogue and let every copy this CTA issued land
             for (int b = 0; b < kAccBufs; ++b) mma_commit(&acc_full[b]);
             const int nis = *issued;
-            for (int it = consumed; it < nis; ++it)
-                mbar_wait(&full[it % kStages], (uint32_t)((it / kStages) & 1), kBudget);
+            for (int gi = consumed; gi < nis; ++gi)
+                mbar_wait(&full[gi % kStages], (uint32_t)((gi / kStages) & 1), kBudget);
         }
     }
     double e = 0.0;
     if (warp < 4) {
-        // drain every stage's large accumulator into FP32 registers (round to nearest)
-        float acc[128];
+        float acc[kMaxN];
 #pragma unroll
-        for (int j = 0; j < 128; ++j) acc[j] = 0.f;
+        for (int q = 0; q < kMaxN; ++q) acc[q] = 0.f;
         bool ok = true;
         const uint32_t lanebase = tmem + ((uint32_t)(warp * 32) << 16);
-        for (int it = 0; it < kIters; ++it) {
-            const int buf = it % kAccBufs;
-            bool w = mbar_wait(&acc_full[buf], (uint32_t)((it / kAccBufs) & 1), 2 * kBudget);
-            ok = __all_sync(0xffffffffu, w && !*abort_flag);
+        const float unscale = ldexpf(1.f, -(eC + split_exponent_dev(__uint_as_float(*mmax))));
+        // the item whose small accumulator (= psi) is being finished, and the
+        // next column to finish
+        int pend = -1, pcol = 0;
+        float pe0 = 0.f, pe1 = 0.f;   // FP32 partial dot of the pending item (two chains)
+        auto finish_chunk = [&](int c0) {
+            // columns c0 .. c0+7 of item pend: psi from TMEM, M from global
+            const int w = (int)blockIdx.x + pend * (int)gridDim.x;
+            const int tile = w % ntiles, m = (w / ntiles) * kRows + warp * 32 + lane;
+            float mv[8];
+            int64_t ofs[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int c = c0 + q, slab = c / S, z = c % S, zrow = tile * R + slab;
+                const bool valid = (m < ldm) && (c < N) && (z < n) && (zrow < nrow);
+                ofs[q] = valid ? ((int64_t)zrow * n + z) * ldm + m : -1;
+                mv[q] = valid ? __ldg(&M[ofs[q]]) : 0.f;
+            }
+            uint32_t v[8];
+            tmem_ld8_nowait(lanebase + (uint32_t)((kAccBufs + (pend & 1)) * N + c0), v);
+            tmem_wait_ld();
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float pv = __uint_as_float(v[q]);
+                if (q & 1) pe1 = fmaf(mv[q], pv, pe1);
+                else pe0 = fmaf(mv[q], pv, pe0);
+                if (FORCES && ofs[q] >= 0) psi[ofs[q]] = pv;
+            }
+        };
+        auto release_pending = [&]() {
+            e += (double)pe0 + (double)pe1;
+            pe0 = pe1 = 0.f;
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&small_free[pend & 1]);
+            pend = -1;
+        };
+        for (int gi = 0; gi < total; ++gi) {
+            const int b = gi % kAccBufs, u = gi / kAccBufs;
+            const int j = gi / kIters, it = gi % kIters;
+            bool wok = mbar_wait(&acc_full[b], (uint32_t)(u & 1), 2 * kBudget);
+            ok = __all_sync(0xffffffffu, wok && !*abort_flag);
             if (!ok) break;
             fence_after();
-            const uint32_t ta = lanebase + (uint32_t)(buf * N);
+            const uint32_t ta = lanebase + (uint32_t)(b * N);
 #pragma unroll
-            for (int c = 0; c < 4; c += 2) {
+            for (int c = 0; c < kMaxN / 32; c += 2) {
                 if (c * 32 < N) {
                     uint32_t v[64];
                     tmem_ld32_nowait(ta + (uint32_t)(c * 32), v);
                     if ((c + 1) * 32 < N) tmem_ld32_nowait(ta + (uint32_t)((c + 1) * 32), v + 32);
                     tmem_wait_ld();
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) acc[c * 32 + j] += __uint_as_float(v[j]);
+                    for (int q = 0; q < 32; ++q) acc[c * 32 + q] += __uint_as_float(v[q]);
                     if ((c + 1) * 32 < N) {
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) acc[(c + 1) * 32 + j] += __uint_as_float(v[32 + j]);
+                        for (int q = 0; q < 32; ++q) acc[(c + 1) * 32 + q] += __uint_as_float(v[32 + q]);
                     }
                 }
             }
             fence_before();
             __syncwarp();
-            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&acc_empty[buf]))
-                                        : "memory");
-        }
-        if (ok) {
-            // the small corrections, accumulated in TMEM over the whole tile (the
-            // last acc_full arrival follows every MMA of the tile)
-            const uint32_t ts = lanebase + (uint32_t)(kAccBufs * N);
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                if (c * 32 < N) {
-                    uint32_t v[32];
-                    tmem_ld32_nowait(ts + (uint32_t)(c * 32), v);
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) acc[c * 32 + j] += __uint_as_float(v[j]);
+            if (lane == 0) mbar_arrive(&acc_empty[b]);
+            // finish 8 columns of the previous item while this one streams
+            if (pend >= 0) {
+                finish_chunk(pcol);
+                pcol += 8;
+                if (pcol >= N) release_pending();
+            }
+            if (it == kIters - 1) {
+                // item j complete (this arrival follows all of its MMAs): fold
+                // the drained large products into its small accumulator
+                while (pend >= 0) {              // (only if N / 8 > kIters)
+                    finish_chunk(pcol);
+                    pcol += 8;
+                    if (pcol >= N) release_pending();
                 }
+                const uint32_t ts = lanebase + (uint32_t)((kAccBufs + (j & 1)) * N);
+#pragma unroll
+                for (int c = 0; c < kMaxN / 32; ++c) {
+                    if (c * 32 < N) {
+                        uint32_t v[32];
+                        tmem_ld32_nowait(ts + (uint32_t)(c * 32), v);
+                        tmem_wait_ld();
+                        float o[32];
+#pragma unroll
+                        for (int q = 0; q < 32; ++q) {
+                            o[q] = (acc[c * 32 + q] + __uint_as_float(v[q])) * unscale;
+                            acc[c * 32 + q] = 0.f;
+                        }
+                        tmem_st32(ts + (uint32_t)(c * 32), o);
+                    }
+                }
+                tmem_wait_st();
+                pend = j;
+                pcol = 0;
             }
         }
         if (ok) {
-            // energy dot and psi: M loads issued 16 at a time (independent), FP32
-            // partial sums per thread (128 products), FP64 across threads
-            const int m = row0 + warp * 32 + lane;
-            const bool mrow = m < ldm;
-            float e0 = 0.f, e1 = 0.f;
-#pragma unroll
-            for (int c0 = 0; c0 < 128; c0 += 16) {
-                if (c0 < N) {
-                    float mv[16];
-                    int64_t ofs[16];
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int c = c0 + j;
-                        const int slab = c / S, z = c % S;
-                        const int zrow = blockIdx.x * R + slab;
-                        const bool valid = mrow && (c < N) && (z < n) && (zrow < nrow);
-                        ofs[j] = valid ? ((int64_t)zrow * n + z) * ldm + m : -1;
-                        mv[j] = valid ? __ldg(&M[ofs[j]]) : 0.f;
-                    }
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        if (j & 1) e1 = fmaf(mv[j], acc[c0 + j], e1);
-                        else e0 = fmaf(mv[j], acc[c0 + j], e0);
-                        if (FORCES && ofs[j] >= 0) psi[ofs[j]] = acc[c0 + j];
-                    }
-                }
+            while (pend >= 0) {
+                finish_chunk(pcol);
+                pcol += 8;
+                if (pcol >= N) release_pending();
             }
-            e = (double)e0 + (double)e1;
         } else {
             *abort_flag = 1;
         }
@@ -370,7 +524,7 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
     fence_before();
     __syncthreads();
     if (threadIdx.x == 0) {
-        part[blockIdx.y * gridDim.x + blockIdx.x] = -0.5 * (red[0] + red[1] + red[2] + red[3]);
+        part[blockIdx.x] = -0.5 * (red[0] + red[1] + red[2] + red[3]);
         if (*abort_flag) atomicOr(errflag, 2);
     }
     if (warp == 5) {
@@ -383,6 +537,7 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
 // ---------------------------------------------------------------------------
 // host side
 
+// 2-D fp16 tensor map, rows of `inner` halves, boxes of 64 x box_outer (128-byte swizzle)
 static bool encode_2d(CUtensorMap *map, void *ptr, uint64_t inner, uint64_t outer, uint32_t box_inner,
                       uint32_t box_outer, std::string &err)
 {
@@ -399,10 +554,10 @@ static bool encode_2d(CUtensorMap *map, void *ptr, uint64_t inner, uint64_t oute
         fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
     }
     cuuint64_t dims[2] = {inner, outer};
-    cuuint64_t strides[1] = {inner * sizeof(float)};
+    cuuint64_t strides[1] = {inner * sizeof(__half)};
     cuuint32_t box[2] = {box_inner, box_outer};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, ptr, dims, strides, box, estr,
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, ptr, dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
@@ -414,36 +569,59 @@ static bool encode_2d(CUtensorMap *map, void *ptr, uint64_t inner, uint64_t oute
 
 static size_t tc_smem_bytes(int N)
 {
-    const size_t stage = 2 * (size_t)tcg::kABytes + 2 * (size_t)N * tcg::kKc * 4;
-    return tcg::kStages * stage + 1024 + 256;
+    const size_t stage = 2 * (size_t)tcg::kABytes + 2 * (size_t)N * tcg::kRowBytes;
+    return (size_t)tcg::kStages * stage + 1024 + 256;
+}
+
+// Tile of R z-rows of S (>= n, multiple of 16) leaves, N = R S <= 128.
+void tc_tile_shape(int n, int &S, int &R)
+{
+    S = ((n + 15) / 16) * 16;
+    R = std::max(1, tcg::kMaxN / S);
+}
+
+int tc_max_blocks(int n, int ldm)
+{
+    int S, R;
+    tc_tile_shape(n, S, R);
+    return ((n * n + R - 1) / R) * ((ldm + tcg::kRows - 1) / tcg::kRows);
 }
 
 bool tc_prepare(Handle &H, std::string &err)
 {
     H.tc.enabled = 0;
     const Geo &g = H.g;
-    if (g.ldm % tcg::kKc != 0 || g.ldm > 512 || g.n > 128) return true;   // plain FP32 kernel is used
-    const int S = ((g.n + 15) / 16) * 16;
-    const int R = std::max(1, 128 / S);
+    if (g.ldm % 32 != 0 || g.ldm > 512 || g.n > 128) return true;   // plain FP32 kernel is used
+    int S, R;
+    tc_tile_shape(g.n, S, R);
     H.tc.S = S;
     H.tc.R = R;
     H.tc.rowstride = S + 2;
     H.tc.N = R * S;
     H.tc.tmem_cols = 32;
-    while ((int)H.tc.tmem_cols < (tcg::kAccBufs + 1) * H.tc.N) H.tc.tmem_cols <<= 1;   // large buffers + small
+    while ((int)H.tc.tmem_cols < (tcg::kAccBufs + 2) * H.tc.N) H.tc.tmem_cols <<= 1;   // large buffers + 2 small
     H.tc.tiles = (g.n * g.n + R - 1) / R;
     H.tc.halves = (g.ldm + tcg::kRows - 1) / tcg::kRows;
+    if (H.tc.tiles * H.tc.halves > H.part_off[kPartCorr + 1] - H.part_off[kPartCorr]) {
+        err = "tensor-core correction: more CTAs than energy partial slots";
+        return false;
+    }
     const uint64_t rows = (uint64_t)g.n * g.n * H.tc.rowstride;
     const uint64_t arows = (uint64_t)H.tc.halves * tcg::kRows;
-    if (!encode_2d(&H.tc.mAhi, H.d_Chi, 27 * (uint64_t)g.ldm, arows, tcg::kKc, 128, err)) return false;
-    if (!encode_2d(&H.tc.mAlo, H.d_Clo, 27 * (uint64_t)g.ldm, arows, tcg::kKc, 128, err)) return false;
-    if (!encode_2d(&H.tc.mBhi, H.d_Mhi, g.ldm, rows, tcg::kKc, (uint32_t)S, err)) return false;
-    if (!encode_2d(&H.tc.mBlo, H.d_Mlo, g.ldm, rows, tcg::kKc, (uint32_t)S, err)) return false;
-    const size_t smem = tc_smem_bytes(H.tc.N);
-    if (cudaFuncSetAttribute(k_corr_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(k_corr_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess) {
+    const int ldk = H.tc.ldk;
+    if (!encode_2d(&H.tc.mAhi, H.d_Chi, 27 * (uint64_t)ldk, arows, tcg::kKc, 128, err)) return false;
+    if (!encode_2d(&H.tc.mAlo, H.d_Clo, 27 * (uint64_t)ldk, arows, tcg::kKc, 128, err)) return false;
+    if (!encode_2d(&H.tc.mBhi, H.d_Mhi, ldk, rows, tcg::kKc, (uint32_t)S, err)) return false;
+    if (!encode_2d(&H.tc.mBlo, H.d_Mlo, ldk, rows, tcg::kKc, (uint32_t)S, err)) return false;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, H.device) != cudaSuccess || sms <= 0) {
+        err = "cudaDeviceGetAttribute (SM count) failed";
+        return false;
+    }
+    H.tc.grid = std::min(H.tc.tiles * H.tc.halves, sms);   // persistent: one CTA per SM
+    const int smem = (int)tc_smem_bytes(H.tc.N);
+    if (cudaFuncSetAttribute(k_corr_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+        cudaFuncSetAttribute(k_corr_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
         err = "cudaFuncSetAttribute (shared memory) failed";
         return false;
     }
@@ -451,21 +629,33 @@ bool tc_prepare(Handle &H, std::string &err)
     return true;
 }
 
-int corr_tc_blocks(const Handle &H) { return H.tc.tiles * H.tc.halves; }
+int corr_tc_blocks(const Handle &H) { return H.tc.grid; }
+
+int tc_ldk(int ldm) { return ((ldm + tcg::kKc - 1) / tcg::kKc) * tcg::kKc; }
+
+cudaError_t launch_split_f16(Handle &H, cudaStream_t s)
+{
+    const int64_t nthr = (int64_t)H.g.n * H.g.n * (H.g.n + 2) * (H.tc.ldk / 8);
+    k_split_f16<<<(unsigned)((nthr + 255) / 256), 256, 0, s>>>(H.g, H.tc.ldk, H.tc.rowstride, H.d_M, H.d_mmax,
+                                                               H.d_Mhi, H.d_Mlo);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_corr_tc(Handle &H, bool forces, cudaStream_t s)
 {
+    cudaError_t e = launch_split_f16(H, s);
+    if (e != cudaSuccess) return e;
     const size_t smem = tc_smem_bytes(H.tc.N);
     double *part = H.d_part + H.part_off[kPartCorr];
-    const dim3 grid(H.tc.tiles, H.tc.halves);
-    if (forces)
-        k_corr_tc<true><<<grid, tcg::kThreads, smem, s>>>(H.tc.mAhi, H.tc.mAlo, H.tc.mBhi, H.tc.mBlo, H.g,
-                                                                H.tc.S, H.tc.R, H.tc.rowstride, H.tc.tmem_cols,
-                                                                H.d_M, H.d_psi, part, H.d_flag);
-    else
-        k_corr_tc<false><<<grid, tcg::kThreads, smem, s>>>(H.tc.mAhi, H.tc.mAlo, H.tc.mBhi, H.tc.mBlo, H.g,
-                                                                 H.tc.S, H.tc.R, H.tc.rowstride, H.tc.tmem_cols,
-                                                                 H.d_M, H.d_psi, part, H.d_flag);
+    const int nwork = H.tc.tiles * H.tc.halves;
+#define ANKH_CORR_LAUNCH(F)                                                                                     \
+    k_corr_tc<F><<<H.tc.grid, tcg::kThreads, smem, s>>>(H.tc.mAhi, H.tc.mAlo, H.tc.mBhi, H.tc.mBlo, H.g, H.tc.S,  \
+                                                        H.tc.R, H.tc.rowstride, H.tc.ldk, H.tc.eC, H.d_mmax,      \
+                                                        H.tc.tiles, nwork, H.tc.tmem_cols, H.d_M, H.d_psi, part,  \
+                                                        H.d_flag)
+    if (forces) ANKH_CORR_LAUNCH(true);
+    else ANKH_CORR_LAUNCH(false);
+#undef ANKH_CORR_LAUNCH
     return cudaGetLastError();
 }
 

@@ -42,13 +42,6 @@ __device__ __forceinline__ void basis_1d(float xh, const float *__restrict__ W, 
     }
 }
 
-__device__ __forceinline__ float tf32_rna(float x)
-{
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
-}
-
 // One warp per leaf.  The ten terms of Alg. 2 factor by the x-derivative
 // order: M[a,b,c] += sum_p ux^(p)[a] G_p[b,c] with G_0 = q uy0 uz0 + mu_y uy1 uz0
 // + mu_z uy0 uz1 + Th_yy uy2 uz0 + 2 Th_yz uy1 uz1 + Th_zz uy0 uz2, G_1 = mu_x uy0 uz0
@@ -71,8 +64,7 @@ template <int LU>
 __global__ void __launch_bounds__(kP2MWarps * 32)
 k_p2m(Geo g, const int *__restrict__ start, const float4 *__restrict__ A0,
       const float4 *__restrict__ A1, const float4 *__restrict__ A2, const float4 *__restrict__ A3,
-      const float *__restrict__ W, float *__restrict__ M, float *__restrict__ Mhi, float *__restrict__ Mlo,
-      int rowstride)
+      const float *__restrict__ W, float *__restrict__ M, unsigned *__restrict__ mmax)
 {
     constexpr int P = LU * LU * LU;
     constexpr int NBC = LU * LU;
@@ -145,43 +137,27 @@ k_p2m(Geo g, const int *__restrict__ start, const float4 *__restrict__ A0,
             }
         }
     }
-    const int n = g.n;
-    const int cz = cell % n, zr = cell / n;
-    const int64_t base = (int64_t)zr * rowstride;
     float *Mrow = M + (int64_t)cell * g.ldm;
     // nodes a*LU^2 + bc: this lane's column; zero padding beyond P
+    float amax = 0.f;
 #pragma unroll
     for (int ps = 0; ps < NPASS; ++ps) {
         const int bc = lane + 32 * ps;
         if (bc < NBC) {
 #pragma unroll
             for (int a = 0; a < LU; ++a) {
-                const int node = a * NBC + bc;
-                const float v = acc[ps][a];
-                Mrow[node] = v;
-                if (Mhi) {
-                    // split for the tensor-core correction: rows of each z-row with a one-leaf halo
-                    const float hi = tf32_rna(v), lo = tf32_rna(v - hi);
-                    Mhi[(base + 1 + cz) * g.ldm + node] = hi;
-                    Mlo[(base + 1 + cz) * g.ldm + node] = lo;
-                    if (cz == n - 1) {
-                        Mhi[base * g.ldm + node] = hi;
-                        Mlo[base * g.ldm + node] = lo;
-                    }
-                    if (cz == 0) {
-                        Mhi[(base + n + 1) * g.ldm + node] = hi;
-                        Mlo[(base + n + 1) * g.ldm + node] = lo;
-                    }
-                }
+                Mrow[a * NBC + bc] = acc[ps][a];
+                amax = fmaxf(amax, fabsf(acc[ps][a]));
             }
         }
     }
-    for (int node = P + lane; node < g.ldm; node += 32) {
-        Mrow[node] = 0.f;
-        if (Mhi) {
-            Mhi[(base + 1 + cz) * g.ldm + node] = 0.f;
-            Mlo[(base + 1 + cz) * g.ldm + node] = 0.f;
-        }
+    for (int node = P + lane; node < g.ldm; node += 32) Mrow[node] = 0.f;
+    if (mmax) {
+        // max |M| for the scaling of the tensor-core operands (non-negative
+        // floats order like their bit patterns)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        if (lane == 0) atomicMax(mmax, __float_as_uint(amax));
     }
 }
 
@@ -370,10 +346,14 @@ k_l2p(Geo g, const int *__restrict__ scell, const int *__restrict__ perm, const 
 
 cudaError_t launch_p2m(Handle &H, cudaStream_t s)
 {
+    unsigned *mmax = H.tc.enabled ? H.d_mmax : nullptr;
+    if (mmax) {
+        const cudaError_t e = cudaMemsetAsync(mmax, 0, sizeof(unsigned), s);
+        if (e != cudaSuccess) return e;
+    }
     ANKH_LU_SWITCH(H.g.Lu,
         k_p2m<LU><<<(H.g.ncell + kP2MWarps - 1) / kP2MWarps, kP2MWarps * 32, 0, s>>>(
-            H.g, H.d_start, H.d_A0, H.d_A1, H.d_A2, H.d_A3, H.d_W, H.d_M,
-            H.tc.enabled ? H.d_Mhi : nullptr, H.tc.enabled ? H.d_Mlo : nullptr, H.tc.rowstride));
+            H.g, H.d_start, H.d_A0, H.d_A1, H.d_A2, H.d_A3, H.d_W, H.d_M, mmax));
     return cudaGetLastError();
 }
 
