@@ -157,9 +157,9 @@ static int choose_n(double box, int Lu)
 static void free_device(Handle *H)
 {
     if (!H) return;
-    void *ptrs[] = {H->d_cellid, H->d_rank, H->d_count, H->d_start, H->d_perm, H->d_scell, H->d_flag, H->d_bsum,
+    void *ptrs[] = {H->d_cellid, H->d_rank, H->d_count, H->d_start, H->d_perm, H->d_inv, H->d_scell, H->d_flag, H->d_bsum,
                     H->d_A0, H->d_A1, H->d_A2, H->d_A3, H->d_W, H->d_M, H->d_rho, H->d_rhohat, H->d_D,
-                    H->d_phi, H->d_C, H->d_Chi, H->d_Clo, H->d_psi, H->d_gnear, H->d_part,
+                    H->d_phi, H->d_C, H->d_Chi, H->d_Clo, H->d_psi, H->d_gnear, H->d_pi, H->d_part,
                     H->d_partoff, H->d_terms, H->d_hostbuf, H->d_Mhi, H->d_Mlo, H->d_mmax};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -334,6 +334,7 @@ int ankh_create(double box_edge, int64_t N, const ankh_params *params, ankh_hand
     ANKH_AL(H.d_start, g.ncell + 1);
     ANKH_AL(H.d_bsum, (g.ncell + 1023) / 1024 + 1);
     ANKH_AL(H.d_perm, N);
+    ANKH_AL(H.d_inv, N);
     ANKH_AL(H.d_scell, N);
     ANKH_AL(H.d_flag, 4);
     ANKH_AL(H.d_A0, N);
@@ -349,6 +350,7 @@ int ankh_create(double box_edge, int64_t N, const ankh_params *params, ankh_hand
     ANKH_AL(H.d_C, (int64_t)27 * g.ldm * g.ldm);
     ANKH_AL(H.d_psi, (int64_t)g.ncell * g.ldm);
     ANKH_AL(H.d_gnear, 13 * N);
+    ANKH_AL(H.d_pi, (int64_t)g.ncell * g.ldm);
     // energy partial layout
     int nb[kPartCount];
     nb[kPartNear] = near_blocks(H);
@@ -375,6 +377,8 @@ int ankh_create(double box_edge, int64_t N, const ankh_params *params, ankh_hand
         std::vector<float> Wf(W.begin(), W.end());
         if (cudaMemcpy(H.d_W, Wf.data(), Wf.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
             return bail(ANKH_ECUDA, "upload W");
+        if (g.Lc == g.Lu && g.Lu <= 8)
+            for (size_t k = 0; k < Wf.size(); ++k) H.h_Wf[k] = Wf[k];
         std::vector<double> C = make_C(g.Lu, g.ldm, g.h / (g.Lu - 1), p.xi);
         std::vector<float> Cf(C.begin(), C.end());
         if (cudaMemcpy(H.d_C, Cf.data(), Cf.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)

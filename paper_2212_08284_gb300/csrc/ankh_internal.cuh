@@ -65,9 +65,11 @@ struct Handle {
 
     // atoms (sorted by leaf)
     int *d_cellid, *d_rank, *d_count, *d_start, *d_perm, *d_scell, *d_flag, *d_bsum;
+    int *d_inv;             // [N] sorted slot of each atom (inverse of perm)
     float4 *d_A0, *d_A1, *d_A2, *d_A3;   // (lx, ly, lz, q) (mu, 0) (txx, txy, txz, tyy) (tyz, tzz, 0, 0)
     // interpolation
-    float *d_W;             // [4][Lu][Lc] fused Chebyshev->equispaced derivative matrices, scaled by (2/h)^p
+    float *d_W;
+    float h_Wf[4 * 8 * 8];  // host copy of W for L_c = L_u <= 8 (kernel-parameter basis tables)             // [4][Lu][Lc] fused Chebyshev->equispaced derivative matrices, scaled by (2/h)^p
     float *d_M;             // [ncell][ldm] equispaced modified charges
     float *d_rho;           // [nf^3] merged grid charges
     cufftComplex *d_rhohat; // [nf][nf][nfh]
@@ -76,6 +78,7 @@ struct Handle {
     float *d_C;             // [27][ldm][ldm] adjacent-leaf correction blocks (FP32)
     float *d_psi;           // [ncell][ldm] correction potential
     float *d_gnear;         // [13][Nslot] near-field gradient per sorted slot
+    float *d_pi;            // [ncell][ldm] far-field node potentials (forces)
     double *d_part;         // energy partials
     int part_off[kPartCount + 1];
     int *d_partoff;         // device copy of part_off

@@ -42,6 +42,40 @@ __device__ __forceinline__ void basis_1d(float xh, const float *__restrict__ W, 
     }
 }
 
+// Same for L_c = L_u with W passed as a kernel parameter (read from the
+// constant bank by the FMAs: no load instructions).
+template <int LU>
+struct WTab {
+    float w[4 * LU * LU];   // [p][a][k]
+};
+
+template <int LU, int NP>
+__device__ __forceinline__ void basis_1d_fixed(float xh, const WTab<LU> &W, float (&u)[NP][LU])
+{
+    float t[LU];
+    t[0] = 1.f;
+    if (LU > 1) t[1] = xh;
+#pragma unroll
+    for (int k = 2; k < LU; ++k) t[k] = 2.f * xh * t[k - 1] - t[k - 2];
+#pragma unroll
+    for (int p = 0; p < NP; ++p)
+#pragma unroll
+        for (int a = 0; a < LU; ++a) {
+            float v = 0.f;
+#pragma unroll
+            for (int k = 0; k < LU; ++k) v = fmaf(W.w[(p * LU + a) * LU + k], t[k], v);
+            u[p][a] = v;
+        }
+}
+
+template <int LU, bool FASTW, int NP>
+__device__ __forceinline__ void basis_any(float xh, const float *__restrict__ W, int Lc, const WTab<LU> &Wc,
+                                          float (&u)[NP][LU])
+{
+    if (FASTW) basis_1d_fixed<LU, NP>(xh, Wc, u);
+    else basis_1d<LU, NP>(xh, W, Lc, u);
+}
+
 // One warp per leaf.  The ten terms of Alg. 2 factor by the x-derivative
 // order: M[a,b,c] += sum_p ux^(p)[a] G_p[b,c] with G_0 = q uy0 uz0 + mu_y uy1 uz0
 // + mu_z uy0 uz1 + Th_yy uy2 uz0 + 2 Th_yz uy1 uz1 + Th_zz uy0 uz2, G_1 = mu_x uy0 uz0
@@ -60,11 +94,12 @@ struct P2MAtom {
     float uz[3][LU];
 };
 
-template <int LU>
+template <int LU, bool FASTW>
 __global__ void __launch_bounds__(kP2MWarps * 32)
 k_p2m(Geo g, const int *__restrict__ start, const float4 *__restrict__ A0,
       const float4 *__restrict__ A1, const float4 *__restrict__ A2, const float4 *__restrict__ A3,
-      const float *__restrict__ W, float *__restrict__ M, unsigned *__restrict__ mmax)
+      const float *__restrict__ W, const __grid_constant__ WTab<LU> Wc, float *__restrict__ M,
+      unsigned *__restrict__ mmax)
 {
     constexpr int P = LU * LU * LU;
     constexpr int NBC = LU * LU;
@@ -87,7 +122,7 @@ k_p2m(Geo g, const int *__restrict__ start, const float4 *__restrict__ A0,
             const float4 a0 = A0[c0 + at];
             const float l = ax == 0 ? a0.x : (ax == 1 ? a0.y : a0.z);
             float u[3][LU];
-            basis_1d<LU, 3>(l * g.two_over_h, W, g.Lc, u);
+            basis_any<LU, FASTW, 3>(l * g.two_over_h, W, g.Lc, Wc, u);
             P2MAtom<LU> &rec = sA[warp][at];
             if (ax == 0) {
                 float *ux = reinterpret_cast<float *>(rec.ux);
@@ -162,63 +197,82 @@ k_p2m(Geo g, const int *__restrict__ start, const float4 *__restrict__ A0,
 }
 
 // Merged periodic grid: rho[g] = sum of M over the (up to 8) leaf nodes at g.
-__global__ void k_fine(Geo g, const float *__restrict__ M, float *__restrict__ rho)
+// Grid (ceil(nf / 128), nf, nf): x -> gz, y -> gy, z -> gx.
+template <int LU>
+__global__ void __launch_bounds__(128) k_fine(Geo g, const float *__restrict__ M, float *__restrict__ rho)
 {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= g.M) return;
-    const int nf = g.nf, Lm = g.Lu - 1, n = g.n, Lu = g.Lu;
-    const int gz = (int)(idx % nf), gy = (int)((idx / nf) % nf), gx = (int)(idx / ((int64_t)nf * nf));
+    constexpr int Lm = LU - 1;
+    const int gz = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nf = g.nf, n = g.n;
+    if (gz >= nf) return;
+    const int gg[3] = {(int)blockIdx.z, (int)blockIdx.y, gz};
     int oc[3][2], on[3][2], cnt[3];
-    const int gg[3] = {gx, gy, gz};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const int q = gg[a] / Lm, r = gg[a] % Lm;
+        const int q = gg[a] / Lm, r = gg[a] - q * Lm;
         oc[a][0] = q; on[a][0] = r; cnt[a] = 1;
-        if (r == 0) {
-            oc[a][1] = (q - 1 + n) % n;
-            on[a][1] = Lm;
-            cnt[a] = 2;
-        }
+        oc[a][1] = q == 0 ? n - 1 : q - 1;   // the node is also the last one of the previous leaf
+        on[a][1] = Lm;
+        if (r == 0) cnt[a] = 2;
     }
     float s = 0.f;
     for (int i = 0; i < cnt[0]; ++i)
         for (int j = 0; j < cnt[1]; ++j)
             for (int k = 0; k < cnt[2]; ++k) {
                 const int cell = (oc[0][i] * n + oc[1][j]) * n + oc[2][k];
-                const int node = (on[0][i] * Lu + on[1][j]) * Lu + on[2][k];
-                s += M[(int64_t)cell * g.ldm + node];
+                const int node = (on[0][i] * LU + on[1][j]) * LU + on[2][k];
+                s += __ldg(&M[(int64_t)cell * g.ldm + node]);
             }
-    rho[idx] = s;
+    rho[((int64_t)gg[0] * nf + gg[1]) * nf + gz] = s;
 }
 
-// L2P fused with the gradient assembly, one thread per sorted atom: node
-// potentials of its leaf Pi_t[k] = phi[g(t,k)] / M - psi_t[k] (read through
-// the cache, shared by the leaf's atoms), far-field gradient by the adjoint
-// of P2M, plus the near-field gradient, the self-term gradient and the k = 0
-// potential; torques; write to the caller's atom order.
+// Node potentials of the far field, per leaf t and node k:
+//   Pi_t[k] = phi[g(t,k)] / M - psi_t[k]
+// (the merged-grid potential at the node minus the adjacent-leaf
+// correction), one thread per (leaf, node); nodes beyond P are left alone.
 template <int LU>
+__global__ void __launch_bounds__(128) k_node_pot(Geo g, const float *__restrict__ phi, float invM,
+                                                  const float *__restrict__ psi, float *__restrict__ pi)
+{
+    constexpr int P = LU * LU * LU, Lm = LU - 1;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int cell = (int)(idx / P), node = (int)(idx - (int64_t)cell * P);
+    if (cell >= g.ncell) return;
+    const int n = g.n, nf = g.nf;
+    const int a = node / (LU * LU), bb = (node / LU) % LU, c = node % LU;
+    int gx = (cell / (n * n)) * Lm + a, gy = ((cell / n) % n) * Lm + bb, gz = (cell % n) * Lm + c;
+    gx = gx >= nf ? gx - nf : gx;
+    gy = gy >= nf ? gy - nf : gy;
+    gz = gz >= nf ? gz - nf : gz;
+    const int64_t o = (int64_t)cell * g.ldm + node;
+    pi[o] = __ldg(&phi[((int64_t)gx * nf + gy) * nf + gz]) * invM - psi[o];
+}
+
+// L2P fused with the gradient assembly, one thread per sorted atom: the node
+// potentials of its leaf (Pi, read through the cache, shared by the leaf's
+// atoms) contracted with its basis -- the adjoint of P2M -- for the far-field
+// gradient, plus the near-field gradient, the self-term gradient and the
+// k = 0 potential; torques; write to the caller's atom order.
+template <int LU, bool FASTW>
 __global__ void __launch_bounds__(128)
 k_l2p(Geo g, const int *__restrict__ scell, const int *__restrict__ perm, const float4 *__restrict__ A0,
       const float4 *__restrict__ A1, const float4 *__restrict__ A2, const float4 *__restrict__ A3,
-      const float *__restrict__ W, const float *__restrict__ phi, float invM, const float *__restrict__ psi,
+      const float *__restrict__ W, const __grid_constant__ WTab<LU> Wc, const float *__restrict__ pi,
       const float *__restrict__ gnear, int64_t Nslot, const double *__restrict__ terms,
-      float *__restrict__ dEdx, float *__restrict__ dEdq, float *__restrict__ dEdmu,
-      float *__restrict__ dEdth, float *__restrict__ torque)
+      float *__restrict__ dEdx, float *__restrict__ dEdq, float *__restrict__ dEdmu, float *__restrict__ dEdth,
+      float *__restrict__ torque)
 {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= Nslot) return;
-    const int cell = scell[s];
-    const int n = g.n, nf = g.nf, Lm = LU - 1;
-    const int cx = cell / (n * n), cy = (cell / n) % n, cz = cell % n;
-    const float *ps = psi + (int64_t)cell * g.ldm;
+    const float *__restrict__ pil = pi + (int64_t)scell[s] * g.ldm;
     const float dcpot = (float)terms[6];
     const float xi = g.xi;
     {
         const float4 a0 = A0[s], a1 = A1[s], a2 = A2[s], a3 = A3[s];
         float ux[4][LU], uy[4][LU], uz[4][LU];
-        basis_1d<LU, 4>(a0.x * g.two_over_h, W, g.Lc, ux);
-        basis_1d<LU, 4>(a0.y * g.two_over_h, W, g.Lc, uy);
-        basis_1d<LU, 4>(a0.z * g.two_over_h, W, g.Lc, uz);
+        basis_any<LU, FASTW, 4>(a0.x * g.two_over_h, W, g.Lc, Wc, ux);
+        basis_any<LU, FASTW, 4>(a0.y * g.two_over_h, W, g.Lc, Wc, uy);
+        basis_any<LU, FASTW, 4>(a0.z * g.two_over_h, W, g.Lc, Wc, uz);
         // V[px][py][pz] = sum_k Pi[k] ux^(px) uy^(py) uz^(pz), px + py + pz <= 3
         float V[4][4][4];
 #pragma unroll
@@ -237,12 +291,9 @@ k_l2p(Geo g, const int *__restrict__ scell, const int *__restrict__ perm, const 
 #pragma unroll
             for (int bb = 0; bb < LU; ++bb) {
                 float X[4] = {0.f, 0.f, 0.f, 0.f};
-                const int gyy = (cy * Lm + bb) % nf, gzz = (cz * Lm + c) % nf;
 #pragma unroll
                 for (int a = 0; a < LU; ++a) {
-                    const int gxx = (cx * Lm + a) % nf;
-                    const float pi = __ldg(&phi[((int64_t)gxx * nf + gyy) * nf + gzz]) * invM
-                                   - __ldg(&ps[(a * LU + bb) * LU + c]);
+                    const float pi = __ldg(&pil[(a * LU + bb) * LU + c]);
 #pragma unroll
                     for (int p = 0; p < 4; ++p) X[p] = fmaf(pi, ux[p][a], X[p]);
                 }
@@ -344,6 +395,14 @@ k_l2p(Geo g, const int *__restrict__ scell, const int *__restrict__ perm, const 
     default: return cudaErrorInvalidValue;                         \
     }
 
+template <int LU>
+static WTab<LU> wtab(const Handle &H)
+{
+    WTab<LU> t;
+    for (int k = 0; k < 4 * LU * LU; ++k) t.w[k] = H.h_Wf[k];
+    return t;
+}
+
 cudaError_t launch_p2m(Handle &H, cudaStream_t s)
 {
     unsigned *mmax = H.tc.enabled ? H.d_mmax : nullptr;
@@ -351,29 +410,49 @@ cudaError_t launch_p2m(Handle &H, cudaStream_t s)
         const cudaError_t e = cudaMemsetAsync(mmax, 0, sizeof(unsigned), s);
         if (e != cudaSuccess) return e;
     }
+    const unsigned nb = (unsigned)((H.g.ncell + kP2MWarps - 1) / kP2MWarps);
     ANKH_LU_SWITCH(H.g.Lu,
-        k_p2m<LU><<<(H.g.ncell + kP2MWarps - 1) / kP2MWarps, kP2MWarps * 32, 0, s>>>(
-            H.g, H.d_start, H.d_A0, H.d_A1, H.d_A2, H.d_A3, H.d_W, H.d_M, mmax));
+        if (H.g.Lc == LU)
+            k_p2m<LU, true><<<nb, kP2MWarps * 32, 0, s>>>(H.g, H.d_start, H.d_A0, H.d_A1, H.d_A2, H.d_A3, H.d_W,
+                                                          wtab<LU>(H), H.d_M, mmax);
+        else
+            k_p2m<LU, false><<<nb, kP2MWarps * 32, 0, s>>>(H.g, H.d_start, H.d_A0, H.d_A1, H.d_A2, H.d_A3, H.d_W,
+                                                           WTab<LU>{}, H.d_M, mmax));
     return cudaGetLastError();
 }
 
 cudaError_t launch_fine_gather(Handle &H, cudaStream_t s)
 {
-    const int64_t nb = (H.g.M + 255) / 256;
-    k_fine<<<(unsigned)nb, 256, 0, s>>>(H.g, H.d_M, H.d_rho);
+    const dim3 grid((unsigned)((H.g.nf + 127) / 128), (unsigned)H.g.nf, (unsigned)H.g.nf);
+    ANKH_LU_SWITCH(H.g.Lu, k_fine<LU><<<grid, 128, 0, s>>>(H.g, H.d_M, H.d_rho));
+    return cudaGetLastError();
+}
+
+template <int LU>
+static cudaError_t l2p_one(Handle &H, float *dEdx, float *dEdq, float *dEdmu, float *dEdtheta, float *torque,
+                           cudaStream_t s)
+{
+    constexpr int P = LU * LU * LU;
+    const float invM = (float)(1.0 / (double)H.g.M);
+    const int64_t npot = (int64_t)H.g.ncell * P;
+    k_node_pot<LU><<<(unsigned)((npot + 127) / 128), 128, 0, s>>>(H.g, H.d_phi, invM, H.d_psi, H.d_pi);
+    const unsigned nb = (unsigned)((H.N + 127) / 128);
+    if (H.g.Lc == LU)
+        k_l2p<LU, true><<<nb, 128, 0, s>>>(H.g, H.d_scell, H.d_perm, H.d_A0, H.d_A1, H.d_A2, H.d_A3, H.d_W,
+                                           wtab<LU>(H), H.d_pi, H.d_gnear, H.N, H.d_terms, dEdx, dEdq, dEdmu,
+                                           dEdtheta, torque);
+    else
+        k_l2p<LU, false><<<nb, 128, 0, s>>>(H.g, H.d_scell, H.d_perm, H.d_A0, H.d_A1, H.d_A2, H.d_A3, H.d_W,
+                                            WTab<LU>{}, H.d_pi, H.d_gnear, H.N, H.d_terms, dEdx, dEdq, dEdmu,
+                                            dEdtheta, torque);
     return cudaGetLastError();
 }
 
 cudaError_t launch_l2p(Handle &H, float *dEdx, float *dEdq, float *dEdmu, float *dEdtheta, float *torque,
                        cudaStream_t s)
 {
-    const float invM = (float)(1.0 / (double)H.g.M);
-    const int nb = (int)((H.N + 127) / 128);
-    ANKH_LU_SWITCH(H.g.Lu,
-        k_l2p<LU><<<nb, 128, 0, s>>>(H.g, H.d_scell, H.d_perm, H.d_A0, H.d_A1, H.d_A2, H.d_A3, H.d_W,
-                                                H.d_phi, invM, H.d_psi, H.d_gnear, H.N, H.d_terms, dEdx, dEdq,
-                                                dEdmu, dEdtheta, torque));
-    return cudaGetLastError();
+    ANKH_LU_SWITCH(H.g.Lu, return l2p_one<LU>(H, dEdx, dEdq, dEdmu, dEdtheta, torque, s));
+    return cudaSuccess;
 }
 
 }  // namespace ankh

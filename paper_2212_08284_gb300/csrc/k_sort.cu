@@ -162,8 +162,28 @@ __global__ void k_leafsort(int ncell, const int *__restrict__ start, int *__rest
     }
 }
 
-// Gather the atoms into leaf order; coordinates relative to the leaf centre
-// (computed in FP64, rounded once to FP32).
+// Same, and the inverse permutation inv[perm[k]] = k (slot of each atom).
+__global__ void k_leafsort_inv(int ncell, const int *__restrict__ start, int *__restrict__ perm,
+                               int *__restrict__ inv)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    int b = start[c], e = start[c + 1];
+    for (int k = b + 1; k < e; ++k) {
+        int v = perm[k];
+        int j = k - 1;
+        while (j >= b && perm[j] > v) {
+            perm[j + 1] = perm[j];
+            --j;
+        }
+        perm[j + 1] = v;
+    }
+    for (int k = b; k < e; ++k) inv[perm[k]] = k;
+}
+
+// Move the atoms into leaf order, one thread per atom in the caller's order
+// (coalesced reads, one scattered write per sorted array); coordinates
+// relative to the leaf centre (computed in FP64, rounded once to FP32).
 // Self term of Eq. ewald per atom (general symmetric Theta), FP32:
 //   -(xi/sqrt(pi)) [q^2 + (2xi^2/3)|mu|^2 - (4xi^2/3) q tr + (8xi^4/5) Theta:Theta + (4xi^4/5) tr^2]
 __device__ __forceinline__ float self_energy_atom(float q, float mx, float my, float mz, const float *t, float xi)
@@ -176,17 +196,17 @@ __device__ __forceinline__ float self_energy_atom(float q, float mx, float my, f
 }
 
 __global__ void __launch_bounds__(256)
-k_gather(int N, const int *__restrict__ perm, const float *__restrict__ x,
+k_gather(int N, const int *__restrict__ inv, const float *__restrict__ x,
          const float *__restrict__ q, const float *__restrict__ mu,
          const float *__restrict__ th, Geo g, int *__restrict__ scell,
          float4 *__restrict__ A0, float4 *__restrict__ A1, float4 *__restrict__ A2,
          float4 *__restrict__ A3, double *__restrict__ part_self, double *__restrict__ part_q)
 {
     __shared__ double sh1[8], sh2[8];
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double es = 0.0, qs = 0.0;
-    if (s < N) {
-    const int i = perm[s];
+    if (i < N) {
+    const int s = inv[i];
     float l[3];
     int c[3];
 #pragma unroll
@@ -259,8 +279,8 @@ cudaError_t launch_scatter_sort_gather(Handle &H, const float *x, const float *q
 {
     int N = (int)H.N;
     k_scatter<<<(N + 255) / 256, 256, 0, s>>>(N, H.d_cellid, H.d_rank, H.d_start, H.d_perm);
-    k_leafsort<<<(H.g.ncell + 127) / 128, 128, 0, s>>>(H.g.ncell, H.d_start, H.d_perm);
-    k_gather<<<(N + 255) / 256, 256, 0, s>>>(N, H.d_perm, x, q, H.max_order >= 1 ? mu : nullptr,
+    k_leafsort_inv<<<(H.g.ncell + 127) / 128, 128, 0, s>>>(H.g.ncell, H.d_start, H.d_perm, H.d_inv);
+    k_gather<<<(N + 255) / 256, 256, 0, s>>>(N, H.d_inv, x, q, H.max_order >= 1 ? mu : nullptr,
                                               H.max_order >= 2 ? theta : nullptr, H.g, H.d_scell,
                                               H.d_A0, H.d_A1, H.d_A2, H.d_A3, H.d_part + H.part_off[kPartSelf],
                                               H.d_part + H.part_off[kPartQ]);
