@@ -48,6 +48,15 @@ design notes of the repository):
     non-neutral systems match the Ewald convention (zero for neutral ones).
   * Energies are 1/2 sum over ordered pairs (Eq. 1); the "2 D D G" of the
     mutual loops in Alg. 3/5 counts each unordered pair once.
+
+Non-periodic variant (ankh_energy_nonperiodic; Sec. 5.2, Eq. relerrnonperio):
+the kernel is the bare H = 1/|x - y| (no images, no Ewald split: xi = 0),
+the leaves tile the box [-r_B, r_B)^3 without wrapping (every atom must lie
+inside), the far field couples every pair of NON-adjacent leaves of the box
+(the 6-D operator is multilevel Toeplitz in the cell and node displacements
+and is embedded in a circulant of size 2n - 1 per cell axis and 2 L_u - 1
+per node axis), the near field couples the atoms of the same and adjacent
+leaves inside the box, and there is no self or neutralising term.
 """
 from __future__ import annotations
 
@@ -436,3 +445,156 @@ def torques(mp: np.ndarray, grad: np.ndarray) -> np.ndarray:
     eps[0, 2, 1] = eps[2, 1, 0] = eps[1, 0, 2] = -1.0
     dW = np.cross(mu, g) + 2.0 * np.einsum("adc,nac->nd", eps, X)
     return -dW
+
+
+# ----------------------------------------------------------------------------
+# Non-periodic ANKH-FFT (Sec. 5.2): bare kernel 1/r, no images
+
+def bin_atoms_nonperiodic(x32: np.ndarray, box: float, n: int):
+    """Leaf of each atom of the box [-r_B, r_B)^3 without wrapping (FP64,
+    correctly rounded: s = (x + r_B) * (1/L), c = min(floor(s * n), n - 1)).
+    Raises if an atom lies outside the box."""
+    x = np.asarray(x32, dtype=np.float64)
+    rB = box / 2.0
+    s = (x + rB) * (1.0 / box)
+    if np.any(s < 0.0) or np.any(s >= 1.0):
+        raise ValueError("non-periodic: every atom must lie inside the box")
+    c = np.minimum(np.floor(s * n), n - 1).astype(np.int64)
+    cell = (c[:, 0] * n + c[:, 1]) * n + c[:, 2]
+    perm = np.argsort(cell, kind="stable")
+    return cell, c, x, perm
+
+
+def far_field_column_nonperiodic(p: Params) -> np.ndarray:
+    """First column of the circulant embedding of the non-periodic far-field
+    operator: entry (dc, da) per axis (cell displacement dc in
+    [-(n-1), n-1], node displacement da in [-(L_u-1), L_u-1], both embedded
+    circularly) holds H(z) = 1/|z| at z = dc h + da delta when the cells are
+    NOT adjacent (max |dc| > 1), else 0.  Shape (2n-1, 2Lu-1) x 3."""
+    n, Lu = p.n, p.Lu
+    h = p.box / n
+    delta = h / (Lu - 1)
+    Pc, Pn = 2 * n - 1, 2 * Lu - 1
+    dc = np.where(np.arange(Pc) < n, np.arange(Pc), np.arange(Pc) - Pc)
+    da = np.where(np.arange(Pn) < Lu, np.arange(Pn), np.arange(Pn) - Pn)
+    z = dc[:, None] * h + da[None, :] * delta                          # (Pc, Pn)
+    zx = z[:, :, None, None, None, None]
+    zy = z[None, None, :, :, None, None]
+    zz = z[None, None, None, None, :, :]
+    r = np.sqrt(zx * zx + zy * zy + zz * zz)
+    far = (np.abs(dc) > 1)
+    nonadj = (far[:, None, None, None, None, None] | far[None, None, :, None, None, None]
+              | far[None, None, None, None, :, None])
+    nonadj = np.broadcast_to(nonadj, r.shape)
+    with np.errstate(divide="ignore"):
+        return np.where(nonadj, 1.0 / np.where(r > 0, r, 1.0), 0.0)
+
+
+def near_pairs_nonperiodic(cvec, perm, p: Params):
+    """Ordered pairs (i, j) with j in the same or an adjacent leaf of i inside
+    the box (no wrapping; i == j excluded), CSR by target, zero shifts."""
+    n = p.n
+    N = cvec.shape[0]
+    cell = (cvec[:, 0] * n + cvec[:, 1]) * n + cvec[:, 2]
+    counts = np.bincount(cell, minlength=n ** 3)
+    start = np.concatenate([[0], np.cumsum(counts)])
+    rows_i, rows_j = [], []
+    for dx in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dz in (-1, 0, 1):
+                sc = cvec + np.array([dx, dy, dz])
+                inside = np.all((sc >= 0) & (sc < n), axis=1)
+                scell = np.where(inside, (sc[:, 0] * n + sc[:, 1]) * n + sc[:, 2], 0)
+                cnt = np.where(inside, counts[scell], 0)
+                ii = np.repeat(np.arange(N), cnt)
+                base = np.repeat(start[scell], cnt)
+                off = np.arange(cnt.sum()) - np.repeat(np.cumsum(cnt) - cnt, cnt)
+                jj = perm[base + off]
+                if dx == 0 and dy == 0 and dz == 0:
+                    keep = ii != jj
+                    ii, jj = ii[keep], jj[keep]
+                rows_i.append(ii)
+                rows_j.append(jj)
+    ii = np.concatenate(rows_i)
+    jj = np.concatenate(rows_j)
+    order = np.argsort(ii, kind="stable")
+    ii, jj = ii[order], jj[order]
+    rowptr = np.concatenate([[0], np.cumsum(np.bincount(ii, minlength=N))]).astype(np.int64)
+    return rowptr, jj.astype(np.int32), np.zeros((len(jj), 3))
+
+
+def ankh_energy_nonperiodic(x32, q, mu, theta, p: Params, grad: bool = True, tensor_pairs: bool = False,
+                            nthreads: int | None = None) -> dict:
+    """Non-periodic ANKH-FFT energy (and its exact gradient) in FP64.
+
+    Steps as in ankh_energy (Alg. 2 and E_s, far field by the diagonalised
+    circulant embedding, near field), with the bare kernel and the aperiodic
+    (multilevel Toeplitz) far-field operator; xi and include_rec of p are
+    not used."""
+    N = len(q)
+    mp = ew.pack_multipoles(q, mu, theta)
+    cell, cvec, xw, perm = bin_atoms_nonperiodic(x32, p.box, p.n)
+    n, Lu, Lc = p.n, p.Lu, p.Lc
+    S = basis_derivs(xw, cvec, p, pmax=3 if grad else 2)
+    Q = modified_charges(cell, S, mp, p)
+    E = reinterp_E(Lu, Lc)
+    M = np.einsum("ak,bl,cm,sklm->sabc", E, E, E, Q)                   # (n^3, Lu, Lu, Lu)
+
+    Pc, Pn = 2 * n - 1, 2 * Lu - 1
+    col = far_field_column_nonperiodic(p)
+    Dspec = np.fft.fftn(col)
+    v = np.zeros((Pc, Pn, Pc, Pn, Pc, Pn))
+    v[:n, :Lu, :n, :Lu, :n, :Lu] = M.reshape(n, n, n, Lu, Lu, Lu).transpose(0, 3, 1, 4, 2, 5)
+    w = np.fft.fftn(v)
+    E_far = float(np.sum(Dspec.real * (w.real ** 2 + w.imag ** 2)) / (2.0 * v.size))
+
+    rowptr, colj, shift = near_pairs_nonperiodic(cvec, perm, p)
+    e_pairs, g_near = ew.pair_csr(xw, mp, rowptr, colj, shift, 0.0, tensor=tensor_pairs, grad=grad,
+                                  nthreads=nthreads)
+    E_near = 0.5 * e_pairs
+    out = {"E": E_far + E_near, "E_far": E_far, "E_near": E_near, "M": M, "cell": cell, "perm": perm}
+    if not grad:
+        return out
+    Pi6 = np.fft.ifftn(Dspec * w).real
+    Pi = Pi6[:n, :Lu, :n, :Lu, :n, :Lu].transpose(0, 2, 4, 1, 3, 5).reshape(n ** 3, Lu, Lu, Lu)
+    PiQ = np.einsum("ak,bl,cm,sabc->sklm", E, E, E, Pi)
+    Pcq = PiQ[cell]
+    Vv = {}
+    for ox in range(4):
+        X = np.einsum("iklm,ik->ilm", Pcq, S[ox][:, 0, :])
+        for oy in range(4 - ox):
+            Y = np.einsum("ilm,il->im", X, S[oy][:, 1, :])
+            for oz in range(4 - ox - oy):
+                Vv[(ox, oy, oz)] = np.einsum("im,im->i", Y, S[oz][:, 2, :])
+    g_far = np.zeros((N, 13))
+    for col_, (ox, oy, oz), fac in ALG2_TERMS:
+        g_far[:, 3 + col_] = fac * Vv[(ox, oy, oz)]
+        for a, sh in enumerate(((1, 0, 0), (0, 1, 0), (0, 0, 1))):
+            g_far[:, a] += fac * mp[:, col_] * Vv[(ox + sh[0], oy + sh[1], oz + sh[2])]
+    out["grad"] = g_far + g_near
+    out["grad_far"] = g_far
+    out["grad_near"] = g_near
+    return out
+
+
+def far_field_dense_nonperiodic(M: np.ndarray, p: Params) -> float:
+    """The non-periodic far field written out: 1/2 sum over ordered pairs of
+    non-adjacent leaves (t, s) and their equispaced nodes of
+    M_t[k] M_s[l] / |x_tk - x_sl|.  For tests (O((n^3 L_u^3)^2))."""
+    n, Lu = p.n, p.Lu
+    h = p.box / n
+    nodes1 = -h / 2 + np.arange(Lu) * (h / (Lu - 1))
+    off = np.stack(np.meshgrid(nodes1, nodes1, nodes1, indexing="ij"), -1).reshape(-1, 3)
+    cidx = np.stack(np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij"), -1).reshape(-1, 3)
+    ctr = -p.box / 2 + (cidx + 0.5) * h
+    pos = (ctr[:, None, :] + off[None, :, :])                            # (n^3, Lu^3, 3)
+    Mf = M.reshape(n ** 3, -1)
+    tot = 0.0
+    for t in range(n ** 3):
+        far = np.max(np.abs(cidx - cidx[t]), axis=1) > 1
+        if not np.any(far):
+            continue
+        d = pos[t][:, None, None, :] - pos[far][None, :, :, :]           # (P, nf, P, 3)
+        r = np.sqrt(np.sum(d * d, axis=-1))
+        tot += float(np.einsum("k,ksl,sl->", Mf[t], 1.0 / r, Mf[far]))
+    return 0.5 * tot

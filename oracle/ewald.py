@@ -216,3 +216,17 @@ def ewald_real_rows(x, mp, box: float, alpha: float, rc: float, targets, grad: b
                       t.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), t.shape[0], _dp(Er), gp,
                       nthreads or nthreads_default())
     return float(Er[0]), g
+
+
+def direct_nonperiodic(x, mp, grad: bool = True, tensor: bool = False, nthreads: int | None = None):
+    """E = 1/2 sum_{i != j} D_i D_j 1/|x_i - x_j| (Eq. relerrnonperio, no images),
+    by the same pair evaluators with the bare kernel (a = 0), FP64.
+    Returns (E, grad N x 13 or None)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    n = x.shape[0]
+    jj = np.concatenate([np.concatenate([np.arange(i), np.arange(i + 1, n)]) for i in range(n)]) if n > 1 \
+        else np.zeros(0, dtype=np.int64)
+    rowptr = np.arange(n + 1, dtype=np.int64) * (n - 1)
+    e, g = pair_csr(x, mp, rowptr, jj, np.zeros((len(jj), 3)), 0.0, tensor=tensor, grad=grad,
+                    nthreads=nthreads)
+    return 0.5 * e, g
