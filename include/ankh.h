@@ -52,6 +52,13 @@ enum {
                                 into fp16 hi + lo, three products, FP32
                                 accumulate: ~22 significant bits); otherwise
                                 plain FP32 on the CUDA cores */
+#define ANKH_NONPERIODIC 4u  /* no periodic images (Sec. 5.2, Eq. relerrnonperio):
+                                bare kernel 1/r (xi and ANKH_INCLUDE_REC are
+                                ignored), leaves tile the box [-L/2, L/2)^3
+                                without wrapping, the far field is the linear
+                                (zero-padded) convolution of the non-adjacent
+                                leaves; every atom must lie inside the box,
+                                else the energy calls return ANKH_EINVAL */
 
 typedef struct {
     double xi;        /* Ewald screening [1/A]; Sec. 5 uses 0.01 */

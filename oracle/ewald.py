@@ -230,3 +230,21 @@ def direct_nonperiodic(x, mp, grad: bool = True, tensor: bool = False, nthreads:
     e, g = pair_csr(x, mp, rowptr, jj, np.zeros((len(jj), 3)), 0.0, tensor=tensor, grad=grad,
                     nthreads=nthreads)
     return 0.5 * e, g
+
+
+def direct_nonperiodic_rows(x, mp, targets, tensor: bool = False, nthreads: int | None = None):
+    """Gradient rows (len(targets) x 13) of the non-periodic direct sum for the
+    given target atoms only (all sources j != i), FP64."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    n = x.shape[0]
+    targets = np.asarray(targets, dtype=np.int64)
+    xs = np.concatenate([x[targets], x])
+    mps = np.concatenate([mp[targets], mp])
+    nt = len(targets)
+    cols = [np.concatenate([np.arange(nt, nt + t), np.arange(nt + t + 1, nt + n)]) for t in targets]
+    rowptr = np.concatenate([[0], np.cumsum([len(c) for c in cols])]).astype(np.int64)
+    rowptr = np.concatenate([rowptr, np.full(n, rowptr[-1], dtype=np.int64)])
+    col = np.concatenate(cols)
+    _, g = pair_csr(xs, mps, rowptr, col, np.zeros((len(col), 3)), 0.0, tensor=tensor, grad=True,
+                    nthreads=nthreads)
+    return g[:nt]

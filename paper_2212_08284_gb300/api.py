@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(HERE, "libankh.so")
 ANKH_OK, ANKH_EINVAL, ANKH_ENOMEM, ANKH_ECUDA, ANKH_ETIMEOUT, ANKH_ENUMERIC = range(6)
 ANKH_INCLUDE_REC = 1
 ANKH_MIXED = 2
+ANKH_NONPERIODIC = 4
 
 # buffer ids of ankh_debug_copy
 BUF_PERM, BUF_START, BUF_M, BUF_RHO, BUF_PSI, BUF_SCELL = range(6)
@@ -254,14 +255,16 @@ class Ankh:
     """Owning wrapper of one handle (one cubic box, fixed N)."""
 
     def __init__(self, box_edge: float, n_atoms: int, xi: float = 0.01, n_cells: int = 0, Lu: int = 5,
-                 Lc: int = 0, max_order: int = 2, include_rec: bool = True, mixed: bool = True):
+                 Lc: int = 0, max_order: int = 2, include_rec: bool = True, mixed: bool = True,
+                 nonperiodic: bool = False):
         p = ankh_default_params()
         p.xi = xi
         p.n_cells = n_cells
         p.Lu = Lu
         p.Lc = Lc
         p.max_order = max_order
-        p.flags = (ANKH_INCLUDE_REC if include_rec else 0) | (ANKH_MIXED if mixed else 0)
+        p.flags = ((ANKH_INCLUDE_REC if include_rec else 0) | (ANKH_MIXED if mixed else 0)
+                   | (ANKH_NONPERIODIC if nonperiodic else 0))
         self.n_atoms = int(n_atoms)
         self.box = float(box_edge)
         self.h = ankh_create(box_edge, n_atoms, p)
@@ -336,10 +339,11 @@ class AnkhBatch:
     """Owning wrapper of a batch of independent boxes (replicas)."""
 
     def __init__(self, box_edges, n_atoms, xi: float = 0.01, n_cells: int = 0, Lu: int = 5, Lc: int = 0,
-                 max_order: int = 2, include_rec: bool = True, mixed: bool = True):
+                 max_order: int = 2, include_rec: bool = True, mixed: bool = True, nonperiodic: bool = False):
         p = ankh_default_params()
         p.xi, p.n_cells, p.Lu, p.Lc, p.max_order = xi, n_cells, Lu, Lc, max_order
-        p.flags = (ANKH_INCLUDE_REC if include_rec else 0) | (ANKH_MIXED if mixed else 0)
+        p.flags = ((ANKH_INCLUDE_REC if include_rec else 0) | (ANKH_MIXED if mixed else 0)
+                   | (ANKH_NONPERIODIC if nonperiodic else 0))
         self.n_atoms = [int(v) for v in n_atoms]
         self.nbox = len(self.n_atoms)
         self.h = ankh_create_batch(box_edges, self.n_atoms, p)

@@ -24,10 +24,11 @@ def candidates(box: float, spread: int = 4, h0: float = 4.0) -> list[int]:
 
 
 def autotune_n(box: float, x, q, mu=None, theta=None, Lu: int = 5, Lc: int = 0, mixed: bool = True,
-               max_order: int = 2, cands: list[int] | None = None, reps: int = 4, warm: int = 2):
+               max_order: int = 2, cands: list[int] | None = None, reps: int = 4, warm: int = 2,
+               nonperiodic: bool = False):
     """Return (best n, {n: milliseconds per evaluation})."""
     import torch
-    key = (round(box, 6), int(x.shape[0]), Lu, Lc, mixed, max_order)
+    key = (round(box, 6), int(x.shape[0]), Lu, Lc, mixed, max_order, nonperiodic)
     if key in _cache:
         return _cache[key]
     n_atoms = int(x.shape[0])
@@ -38,7 +39,8 @@ def autotune_n(box: float, x, q, mu=None, theta=None, Lu: int = 5, Lc: int = 0, 
     stream = torch.cuda.current_stream()
     for n in (cands or candidates(box)):
         try:
-            m = api.Ankh(box, n_atoms, n_cells=n, Lu=Lu, Lc=Lc, mixed=mixed, max_order=max_order)
+            m = api.Ankh(box, n_atoms, n_cells=n, Lu=Lu, Lc=Lc, mixed=mixed, max_order=max_order,
+                         nonperiodic=nonperiodic)
         except api.AnkhError:
             continue
         for _ in range(warm):

@@ -136,6 +136,13 @@ static bool good_fft_size(int m)
     return m == 1;
 }
 
+// smallest m' >= m with prime factors 2, 3, 5, 7 only
+static int next_fft_size(int m)
+{
+    while (!good_fft_size(m)) ++m;
+    return m;
+}
+
 static int choose_n(double box, int Lu)
 {
     // leaf edge near 4.0 A for L_u = 5 (balances near-field pairs against
@@ -157,7 +164,7 @@ static int choose_n(double box, int Lu)
 static void free_device(Handle *H)
 {
     if (!H) return;
-    void *ptrs[] = {H->d_cellid, H->d_rank, H->d_count, H->d_start, H->d_perm, H->d_inv, H->d_scell, H->d_flag, H->d_bsum,
+    void *ptrs[] = {H->d_cellid, H->d_rank, H->d_count, H->d_start, H->d_perm, H->d_inv, H->d_loc, H->d_scell, H->d_flag, H->d_bsum,
                     H->d_A0, H->d_A1, H->d_A2, H->d_A3, H->d_W, H->d_M, H->d_rho, H->d_rhohat, H->d_D,
                     H->d_phi, H->d_C, H->d_Chi, H->d_Clo, H->d_psi, H->d_gnear, H->d_pi, H->d_part,
                     H->d_partoff, H->d_terms, H->d_hostbuf, H->d_Mhi, H->d_Mlo, H->d_mmax};
@@ -241,6 +248,7 @@ static int fetch_terms(Handle &H, double *E_host, cudaStream_t s)
     if (flag & 2) return fail(ANKH_ETIMEOUT, "a bounded wait of the tensor-core correction ran out");
     if (flag & 1) return fail(ANKH_ENUMERIC, "non-finite input coordinate");
     if (flag & 4) return fail(ANKH_ENUMERIC, "two atoms at the same position (infinite energy)");
+    if (flag & 8) return fail(ANKH_EINVAL, "non-periodic box: an atom lies outside [-L/2, L/2)^3");
     if (E_host) *E_host = H.h_terms[5];
     return ANKH_OK;
 }
@@ -283,11 +291,16 @@ int ankh_create(double box_edge, int64_t N, const ankh_params *params, ankh_hand
     if (p.Lc == 0) p.Lc = p.Lu;
     if (p.Lu < 2 || p.Lu > kMaxLu) return fail(ANKH_EINVAL, "Lu out of range [2, 8]");
     if (p.Lc < 2 || p.Lc > kMaxLc) return fail(ANKH_EINVAL, "Lc out of range [2, 16]");
-    if (!(p.xi > 0.0) || !std::isfinite(p.xi)) return fail(ANKH_EINVAL, "xi must be > 0");
+    const bool nonper = (p.flags & ANKH_NONPERIODIC) != 0;
+    if (nonper) p.xi = 0.0;   // bare kernel
+    else if (!(p.xi > 0.0) || !std::isfinite(p.xi)) return fail(ANKH_EINVAL, "xi must be > 0");
     if (p.max_order < 0 || p.max_order > 2) return fail(ANKH_EINVAL, "max_order out of range [0, 2]");
     int n = p.n_cells ? p.n_cells : choose_n(box_edge, p.Lu);
     if (n < 3) return fail(ANKH_EINVAL, "at least 3 leaves per axis are needed");
-    if ((int64_t)n * (p.Lu - 1) > 1024) return fail(ANKH_EINVAL, "merged grid larger than 1024 points per axis");
+    // non-periodic: the n (L_u - 1) + 1 nodes per axis are zero-padded to at
+    // least twice that minus one, so the circular convolution is the linear one
+    const int ngrid = nonper ? next_fft_size(2 * (n * (p.Lu - 1) + 1) - 1) : n * (p.Lu - 1);
+    if (ngrid > 1024) return fail(ANKH_EINVAL, "FFT grid larger than 1024 points per axis");
 
     auto t0 = std::chrono::steady_clock::now();
     ankh_handle *hh = new (std::nothrow) ankh_handle();
@@ -305,14 +318,17 @@ int ankh_create(double box_edge, int64_t N, const ankh_params *params, ankh_hand
     g.Lc = p.Lc;
     g.P = p.Lu * p.Lu * p.Lu;
     g.ldm = ((g.P + 31) / 32) * 32;
-    g.nf = n * (p.Lu - 1);
+    g.nf = ngrid;
     g.nfh = g.nf / 2 + 1;
+    g.nonperiodic = nonper ? 1 : 0;
+    g.ng = nonper ? n * (p.Lu - 1) + 1 : g.nf;
     g.M = (int64_t)g.nf * g.nf * g.nf;
     g.box = box_edge;
     g.rB = box_edge / 2.0;
     g.inv_box = 1.0 / box_edge;
     g.h = box_edge / n;
     g.hf = (float)g.h;
+    g.hf_lo = (float)(g.h - (double)g.hf);
     g.two_over_h = (float)(2.0 / g.h);
     g.xi = (float)p.xi;
 
@@ -335,6 +351,7 @@ int ankh_create(double box_edge, int64_t N, const ankh_params *params, ankh_hand
     ANKH_AL(H.d_bsum, (g.ncell + 1023) / 1024 + 1);
     ANKH_AL(H.d_perm, N);
     ANKH_AL(H.d_inv, N);
+    ANKH_AL(H.d_loc, N);
     ANKH_AL(H.d_scell, N);
     ANKH_AL(H.d_flag, 4);
     ANKH_AL(H.d_A0, N);
@@ -344,6 +361,7 @@ int ankh_create(double box_edge, int64_t N, const ankh_params *params, ankh_hand
     ANKH_AL(H.d_W, 4 * g.Lu * g.Lc);
     ANKH_AL(H.d_M, (int64_t)g.ncell * g.ldm);
     ANKH_AL(H.d_rho, g.M);
+    cudaMemset(H.d_rho, 0, sizeof(float) * g.M);   // the zero padding of the non-periodic grid
     ANKH_AL(H.d_rhohat, nspec);
     ANKH_AL(H.d_D, nspec);
     ANKH_AL(H.d_phi, g.M);
@@ -389,7 +407,8 @@ int ankh_create(double box_edge, int64_t N, const ankh_params *params, ankh_hand
         tc_tile_shape(n, S, R);
         H.tc.ldk = tc_ldk(g.ldm);
         const int ldk = H.tc.ldk;
-        const int64_t rows = (int64_t)n * n * (S + 2);
+        // z-rows with a one-leaf halo; a non-periodic box has one extra all-zero z-row block
+        const int64_t rows = ((int64_t)n * n + (nonper ? 1 : 0)) * (S + 2);
         const int halves = (g.ldm + 127) / 128;
         const int64_t acols = (int64_t)27 * ldk, arows = (int64_t)halves * 128;
         ANKH_AL(H.d_Mhi, rows * ldk);
@@ -737,6 +756,8 @@ int ankh_energy_forces_batch(ankh_batch *b, const float *x, const float *q, cons
         const int flag = (int)b->h_E[2 * i + 1];
         if (flag & 2) return fail(ANKH_ETIMEOUT, "box " + std::to_string(i) + ": bounded wait ran out");
         if (flag & 1) return fail(ANKH_ENUMERIC, "box " + std::to_string(i) + ": non-finite coordinate");
+        if (flag & 4) return fail(ANKH_ENUMERIC, "box " + std::to_string(i) + ": two atoms at one position");
+        if (flag & 8) return fail(ANKH_EINVAL, "box " + std::to_string(i) + ": atom outside the non-periodic box");
         E_host[i] = b->h_E[2 * i];
     }
     return ANKH_OK;

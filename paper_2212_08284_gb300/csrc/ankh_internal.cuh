@@ -22,11 +22,14 @@ struct Geo {
     int Lu, Lc;       // interpolation orders
     int P;            // Lu^3 nodes per leaf
     int ldm;          // padded leading dimension of per-leaf node arrays (multiple of 32)
-    int nf;           // merged equispaced grid points per axis, n (Lu - 1)
+    int nf;           // FFT grid points per axis: n (Lu - 1) (periodic) or the padded size
     int nfh;          // nf / 2 + 1
     int64_t M;        // nf^3
+    int ng;           // merged equispaced nodes per axis: nf (periodic) or n (Lu - 1) + 1
+    int nonperiodic;  // 1: no images, bare kernel, zero-padded linear convolution
     double box, rB, inv_box, h;
     float hf;         // leaf edge (float)
+    float hf_lo;      // h - hf (float): hf + hf_lo carries the FP64 leaf edge
     float two_over_h; // chain-rule factor of x_hat = 2 (x - ctr) / h
     float xi;
 };
@@ -66,6 +69,7 @@ struct Handle {
     // atoms (sorted by leaf)
     int *d_cellid, *d_rank, *d_count, *d_start, *d_perm, *d_scell, *d_flag, *d_bsum;
     int *d_inv;             // [N] sorted slot of each atom (inverse of perm)
+    float4 *d_loc;          // [N] coordinates relative to the leaf centre (caller's order)
     float4 *d_A0, *d_A1, *d_A2, *d_A3;   // (lx, ly, lz, q) (mu, 0) (txx, txy, txz, tyy) (tyz, tzz, 0, 0)
     // interpolation
     float *d_W;

@@ -18,11 +18,13 @@ constexpr int kCT = 64;    // target leaves per tile
 constexpr int kKT = 128;   // rows (target nodes) per tile
 constexpr int kLC = 32;    // contraction chunk
 
-__device__ __forceinline__ int neighbour_leaf(int t, int d, int n)
+// leaf t + d (periodic), or -1 beyond a face of a non-periodic box
+__device__ __forceinline__ int neighbour_leaf(int t, int d, int n, int nonperiodic)
 {
     const int cx = t / (n * n), cy = (t / n) % n, cz = t % n;
-    const int dx = d / 9 - 1, dy = (d / 3) % 3 - 1, dz = d % 3 - 1;
-    return (((cx + dx + n) % n) * n + (cy + dy + n) % n) * n + (cz + dz + n) % n;
+    const int ax = cx + d / 9 - 1, ay = cy + (d / 3) % 3 - 1, az = cz + d % 3 - 1;
+    if (nonperiodic && (ax < 0 || ax >= n || ay < 0 || ay >= n || az < 0 || az >= n)) return -1;
+    return (((ax + n) % n) * n + (ay + n) % n) * n + (az + n) % n;
 }
 
 template <bool FORCES>
@@ -57,7 +59,10 @@ k_corr_simt(Geo g, const float *__restrict__ M, const float *__restrict__ C, flo
                 const int j = e / kLC, l = e % kLC;
                 const int t = t0 + j;
                 float v = 0.f;
-                if (t < g.ncell) v = M[(int64_t)neighbour_leaf(t, d, g.n) * ldm + l0 + l];
+                if (t < g.ncell) {
+                    const int nb = neighbour_leaf(t, d, g.n, g.nonperiodic);
+                    if (nb >= 0) v = M[(int64_t)nb * ldm + l0 + l];
+                }
                 sB[l][j] = v;
             }
             __syncthreads();

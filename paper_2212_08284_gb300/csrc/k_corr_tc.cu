@@ -225,7 +225,8 @@ int split_exponent(float maxabs)
 }
 
 // Split of M for the tensor cores: rows of each z-row with a one-leaf halo
-// (row j of z-row zr holds leaf z = n-1, 0, ..., n-1, 0 for j = 0 .. n+1),
+// (row j of z-row zr holds leaf z = n-1, 0, ..., n-1, 0 for j = 0 .. n+1;
+// zeros in place of the wrapped rows for a non-periodic box),
 // nodes padded to ldk with zeros, scaled by 2^eM and split into fp16 hi + lo.
 // One thread per 8 nodes of a row.
 __global__ void __launch_bounds__(256)
@@ -242,8 +243,10 @@ k_split_f16(Geo g, int ldk, int rowstride, const float *__restrict__ M, const un
     const int64_t zr = r / (n + 2);
     const int cz = j == 0 ? n - 1 : (j == n + 1 ? 0 : j - 1);
     const float scale = ldexpf(1.f, split_exponent_dev(__uint_as_float(*mmax)));
+    // the halo rows wrap around the z-row (periodic) or are zero (non-periodic)
+    const bool halo_zero = g.nonperiodic && (j == 0 || j == n + 1);
     float v[8];
-    if (node0 < g.ldm) {
+    if (node0 < g.ldm && !halo_zero) {
         const float4 *src = reinterpret_cast<const float4 *>(M + (zr * n + cz) * g.ldm + node0);
         const float4 a = src[0], b = src[1];
         v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
@@ -350,8 +353,11 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
                 int zrow = tile * R + r;
                 if (zrow >= nrow) zrow = nrow - 1;
                 const int cx = zrow / n, cy = zrow % n;
-                const int ncx = (cx + dx + n) % n, ncy = (cy + dy + n) % n;
-                const int brow = (ncx * n + ncy) * rowstride + 1 + dz;
+                const int ax = cx + dx, ay = cy + dy;
+                // a non-periodic box reads the all-zero z-row block n^2 beyond its faces
+                const bool outside = g.nonperiodic && (ax < 0 || ax >= n || ay < 0 || ay >= n);
+                const int ncx = (ax + n) % n, ncy = (ay + n) % n;
+                const int brow = (outside ? nrow : ncx * n + ncy) * rowstride + 1 + dz;
                 tma_2d(st + 2 * kABytes + (size_t)r * S * kRowBytes, &tmBhi, &full[s], kc * kKc, brow);
                 tma_2d(st + 2 * kABytes + bbytes + (size_t)r * S * kRowBytes, &tmBlo, &full[s], kc * kKc, brow);
             }
@@ -606,7 +612,7 @@ bool tc_prepare(Handle &H, std::string &err)
         err = "tensor-core correction: more CTAs than energy partial slots";
         return false;
     }
-    const uint64_t rows = (uint64_t)g.n * g.n * H.tc.rowstride;
+    const uint64_t rows = ((uint64_t)g.n * g.n + (g.nonperiodic ? 1 : 0)) * H.tc.rowstride;
     const uint64_t arows = (uint64_t)H.tc.halves * tcg::kRows;
     const int ldk = H.tc.ldk;
     if (!encode_2d(&H.tc.mAhi, H.d_Chi, 27 * (uint64_t)ldk, arows, tcg::kKc, 128, err)) return false;

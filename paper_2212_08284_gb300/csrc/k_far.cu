@@ -165,6 +165,49 @@ __global__ void k_pre_spec(Geo g, const cufftDoubleComplex *__restrict__ Tk, dou
     }
 }
 
+// Non-periodic kernel on the zero-padded grid (FP64): the linear
+// convolution of the ng merged nodes per axis with
+//   G(d) = H(d delta) = 1/(delta |d|)  if max_a |d_a| >= L_u - 1 (one leaf), else 0,
+// displacements d in [-(ng-1), ng-1] per axis placed circularly (nf >= 2 ng - 1,
+// so the wrap-around entries are never reached and stay 0).
+__global__ void k_pre_np(Geo g, double *__restrict__ T)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= g.M) return;
+    const int nf = g.nf, ng = g.ng, Lm = g.Lu - 1;
+    const int j[3] = {(int)(idx / ((int64_t)nf * nf)), (int)((idx / nf) % nf), (int)(idx % nf)};
+    int d[3];
+    bool used = true;
+    int dmax = 0;
+    for (int a = 0; a < 3; ++a) {
+        d[a] = j[a] < ng ? j[a] : (j[a] > nf - ng ? j[a] - nf : 0);
+        if (j[a] >= ng && j[a] <= nf - ng) used = false;
+        dmax = max(dmax, abs(d[a]));
+    }
+    double v = 0.0;
+    if (used && dmax >= Lm) {
+        const double delta = g.h / Lm;
+        v = 1.0 / (delta * sqrt((double)d[0] * d[0] + (double)d[1] * d[1] + (double)d[2] * d[2]));
+    }
+    T[idx] = v;
+}
+
+// D (FP32) from the D2Z transform of the non-periodic kernel; the k = 0 value
+// is returned in FP64 and removed from D (its term D_0 Q^2 / 2M is added in FP64).
+__global__ void k_pre_spec_np(Geo g, const cufftDoubleComplex *__restrict__ Tk, float *__restrict__ D,
+                              double *__restrict__ D0)
+{
+    const int64_t total = (int64_t)g.nf * g.nf * g.nfh;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    if (idx == 0) {
+        *D0 = Tk[0].x;
+        D[0] = 0.f;
+    } else {
+        D[idx] = (float)Tk[idx].x;
+    }
+}
+
 cudaError_t precompute_kernel_spectrum(Handle &H, double *D0_out, std::string &err)
 {
     const Geo &g = H.g;
@@ -188,14 +231,18 @@ cudaError_t precompute_kernel_spectrum(Handle &H, double *D0_out, std::string &e
     if ((ce = cudaMalloc(&dT, sizeof(double) * g.M)) != cudaSuccess) return fail("cudaMalloc T");
     if ((ce = cudaMalloc(&dTk, sizeof(cufftDoubleComplex) * nspec)) != cudaSuccess) return fail("cudaMalloc Tk");
     if ((ce = cudaMalloc(&dD0, sizeof(double))) != cudaSuccess) return fail("cudaMalloc D0");
-    k_pre_real<<<(unsigned)((g.M + 255) / 256), 256>>>(g, eta, (double)H.g.xi, dT);
-    if ((ce = cudaGetLastError()) != cudaSuccess) return fail("k_pre_real");
+    if (g.nonperiodic) k_pre_np<<<(unsigned)((g.M + 255) / 256), 256>>>(g, dT);
+    else k_pre_real<<<(unsigned)((g.M + 255) / 256), 256>>>(g, eta, (double)H.g.xi, dT);
+    if ((ce = cudaGetLastError()) != cudaSuccess) return fail("kernel table");
     if (cufftPlan3d(&plan, g.nf, g.nf, g.nf, CUFFT_D2Z) != CUFFT_SUCCESS) return fail("cufftPlan3d D2Z");
     have_plan = true;
     if (cufftExecD2Z(plan, dT, dTk) != CUFFT_SUCCESS) return fail("cufftExecD2Z");
-    k_pre_spec<<<(unsigned)((nspec + 255) / 256), 256>>>(g, dTk, eta, (double)H.g.xi,
-                                                          (H.flags & ANKH_INCLUDE_REC) ? 1 : 0, mmax,
-                                                          kcut * kcut, H.d_D, dD0);
+    if (g.nonperiodic)
+        k_pre_spec_np<<<(unsigned)((nspec + 255) / 256), 256>>>(g, dTk, H.d_D, dD0);
+    else
+        k_pre_spec<<<(unsigned)((nspec + 255) / 256), 256>>>(g, dTk, eta, (double)H.g.xi,
+                                                              (H.flags & ANKH_INCLUDE_REC) ? 1 : 0, mmax,
+                                                              kcut * kcut, H.d_D, dD0);
     if ((ce = cudaGetLastError()) != cudaSuccess) return fail("k_pre_spec");
     if ((ce = cudaMemcpy(D0_out, dD0, sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess)
         return fail("copy D0");

@@ -196,29 +196,39 @@ k_p2m(Geo g, const int *__restrict__ start, const float4 *__restrict__ A0,
     }
 }
 
-// Merged periodic grid: rho[g] = sum of M over the (up to 8) leaf nodes at g.
-// Grid (ceil(nf / 128), nf, nf): x -> gz, y -> gy, z -> gx.
-template <int LU>
+// Merged grid: rho[g] = sum of M over the (up to 8) leaf nodes at g.
+// Periodic: nf = n (L_u - 1) points per axis, node 0 of leaf q is also node
+// L_u - 1 of leaf q - 1 (mod n).  Non-periodic (NP): ng = n (L_u - 1) + 1
+// nodes per axis written into the zero-padded FFT grid (stride nf), node 0
+// of leaf q shared with leaf q - 1 only for q >= 1, and the last node
+// (q = n) belongs to leaf n - 1 alone.
+// Grid (ceil(ng / 128), ng, ng): x -> gz, y -> gy, z -> gx.
+template <int LU, bool NP>
 __global__ void __launch_bounds__(128) k_fine(Geo g, const float *__restrict__ M, float *__restrict__ rho)
 {
     constexpr int Lm = LU - 1;
     const int gz = blockIdx.x * blockDim.x + threadIdx.x;
     const int nf = g.nf, n = g.n;
-    if (gz >= nf) return;
+    if (gz >= g.ng) return;
     const int gg[3] = {(int)blockIdx.z, (int)blockIdx.y, gz};
-    int oc[3][2], on[3][2], cnt[3];
+    int oc[3][2], on[3][2], lo[3], cnt[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const int q = gg[a] / Lm, r = gg[a] - q * Lm;
-        oc[a][0] = q; on[a][0] = r; cnt[a] = 1;
+        oc[a][0] = q; on[a][0] = r;
         oc[a][1] = q == 0 ? n - 1 : q - 1;   // the node is also the last one of the previous leaf
         on[a][1] = Lm;
-        if (r == 0) cnt[a] = 2;
+        lo[a] = 0;
+        cnt[a] = r == 0 ? 2 : 1;
+        if (NP) {
+            if (r == 0 && q == 0) cnt[a] = 1;             // first face: no previous leaf
+            if (q == n) { lo[a] = 1; cnt[a] = 2; }        // last face: previous leaf only
+        }
     }
     float s = 0.f;
-    for (int i = 0; i < cnt[0]; ++i)
-        for (int j = 0; j < cnt[1]; ++j)
-            for (int k = 0; k < cnt[2]; ++k) {
+    for (int i = lo[0]; i < cnt[0]; ++i)
+        for (int j = lo[1]; j < cnt[1]; ++j)
+            for (int k = lo[2]; k < cnt[2]; ++k) {
                 const int cell = (oc[0][i] * n + oc[1][j]) * n + oc[2][k];
                 const int node = (on[0][i] * LU + on[1][j]) * LU + on[2][k];
                 s += __ldg(&M[(int64_t)cell * g.ldm + node]);
@@ -423,8 +433,12 @@ cudaError_t launch_p2m(Handle &H, cudaStream_t s)
 
 cudaError_t launch_fine_gather(Handle &H, cudaStream_t s)
 {
-    const dim3 grid((unsigned)((H.g.nf + 127) / 128), (unsigned)H.g.nf, (unsigned)H.g.nf);
-    ANKH_LU_SWITCH(H.g.Lu, k_fine<LU><<<grid, 128, 0, s>>>(H.g, H.d_M, H.d_rho));
+    const dim3 grid((unsigned)((H.g.ng + 127) / 128), (unsigned)H.g.ng, (unsigned)H.g.ng);
+    if (H.g.nonperiodic) {
+        ANKH_LU_SWITCH(H.g.Lu, k_fine<LU, true><<<grid, 128, 0, s>>>(H.g, H.d_M, H.d_rho));
+    } else {
+        ANKH_LU_SWITCH(H.g.Lu, k_fine<LU, false><<<grid, 128, 0, s>>>(H.g, H.d_M, H.d_rho));
+    }
     return cudaGetLastError();
 }
 

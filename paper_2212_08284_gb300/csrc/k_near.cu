@@ -161,7 +161,7 @@ k_near(Geo g, const int *__restrict__ start, const float4 *__restrict__ A0, cons
     __shared__ double sE[kNearWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n = g.n;
-    const float h = g.hf;
+    const float h = g.hf, hlo = g.hf_lo;
     double ew = 0.0;
     for (int t = blockIdx.x * kNearWarps + warp; t < g.ncell; t += gridDim.x * kNearWarps) {
         const int tb = start[t], nt_all = start[t + 1] - tb;
@@ -171,9 +171,14 @@ k_near(Geo g, const int *__restrict__ start, const float4 *__restrict__ A0, cons
         int cnt = 0, beg = 0;
         if (lane < 27) {
             const int dx = lane / 9 - 1, dy = (lane / 3) % 3 - 1, dz = lane % 3 - 1;
-            const int nc = (((cx + dx + n) % n) * n + (cy + dy + n) % n) * n + (cz + dz + n) % n;
-            beg = start[nc];
-            cnt = start[nc + 1] - beg;
+            const int ax = cx + dx, ay = cy + dy, az = cz + dz;
+            // non-periodic box: leaves beyond its faces do not exist
+            const bool inside = !g.nonperiodic || (ax >= 0 && ax < n && ay >= 0 && ay < n && az >= 0 && az < n);
+            if (inside) {
+                const int nc = (((ax + n) % n) * n + (ay + n) % n) * n + (az + n) % n;
+                beg = start[nc];
+                cnt = start[nc + 1] - beg;
+            }
         }
         int incl = cnt;
 #pragma unroll
@@ -223,9 +228,13 @@ k_near(Geo g, const int *__restrict__ start, const float4 *__restrict__ A0, cons
                     const int slot = sBeg[warp][d] + (f - sPre[warp][d]);
                     float4 a0 = A0[slot];
                     const float4 a1 = A1[slot], a2 = A2[slot], a3 = A3[slot];
-                    a0.x += (d / 9 - 1) * h;
-                    a0.y += ((d / 3) % 3 - 1) * h;
-                    a0.z += (d % 3 - 1) * h;
+                    // shift into the target leaf's frame by d h with the FP64 leaf
+                    // edge carried as hf + hf_lo (an FP32 h alone would bias every
+                    // cross-leaf distance the same way)
+                    const float sx = (float)(d / 9 - 1), sy = (float)((d / 3) % 3 - 1), sz = (float)(d % 3 - 1);
+                    a0.x = fmaf(sx, h, a0.x) + sx * hlo;
+                    a0.y = fmaf(sy, h, a0.y) + sy * hlo;
+                    a0.z = fmaf(sz, h, a0.z) + sz * hlo;
                     sSrc[warp][k][0] = a0;
                     sSrc[warp][k][1] = make_float4(a1.x, a1.y, a1.z, a2.x + a2.w + a3.y);
                     sSrc[warp][k][2] = a2;
@@ -233,7 +242,7 @@ k_near(Geo g, const int *__restrict__ start, const float4 *__restrict__ A0, cons
                 }
                 __syncwarp();
                 if (active) {
-#pragma unroll 2
+#pragma unroll 1
                     for (int k = grp; k < cs; k += G) {
                         const float4 s0 = sSrc[warp][k][0];
                         src_fields<FORCES, MODE>(ti.x - s0.x, ti.y - s0.y, ti.z - s0.z, s0, sSrc[warp][k][1],
@@ -315,8 +324,10 @@ cudaError_t launch_near(Handle &H, bool forces, cudaStream_t s)
     const double log2e = 1.4426950408889634;
     bc.xi = (float)xi;
     bc.kap = (float)(xi * xi * log2e);
-    double c = 1.0 / (xi * sqrt(M_PI));
-    double cl[6];
+    // screening coefficients; all zero for the bare kernel (xi = 0, non-periodic):
+    // B0 = 1/r and B_l = (2l - 1) B_{l-1} / r^2
+    double cl[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    double c = xi > 0.0 ? 1.0 / (xi * sqrt(M_PI)) : 0.0;
     for (int l = 1; l <= 5; ++l) {
         c *= 2.0 * xi * xi;
         cl[l] = c;

@@ -42,6 +42,73 @@ __global__ void k_bin(int N, const float *__restrict__ x, Geo g, int *__restrict
     rank[i] = atomicAdd(&count[cell], 1);
 }
 
+// Same, and the coordinates relative to the leaf centre, loc = (s n - c - 1/2) h
+// (FP64, rounded once to FP32), for the move into leaf order.
+__global__ void k_bin_loc(int N, const float *__restrict__ x, Geo g, int *__restrict__ cellid,
+                          int *__restrict__ rank, int *__restrict__ count, int *__restrict__ flag,
+                          float4 *__restrict__ loc)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int c[3];
+    float l[3];
+    bool bad = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double xv = (double)x[3 * (int64_t)i + a];
+        if (!isfinite(xv)) { bad = true; xv = 0.0; }
+        double sn;
+        c[a] = leaf_coord(xv, g, &sn);
+        l[a] = (float)__dmul_rn(__dadd_rn(sn, -((double)c[a] + 0.5)), g.h);
+    }
+    if (bad) atomicOr(flag, 1);
+    int cell = (c[0] * g.n + c[1]) * g.n + c[2];
+    cellid[i] = cell;
+    loc[i] = make_float4(l[0], l[1], l[2], 0.f);
+    rank[i] = atomicAdd(&count[cell], 1);
+}
+
+// Non-periodic box (no wrapping): s = (x + r_B) * (1/L) must lie in [0, 1);
+// c = min(floor(s * n), n - 1); an atom outside the box sets bit 8 of the
+// error flag (its leaf is clamped so that the call completes).
+__device__ __forceinline__ int leaf_coord_np(double xv, const Geo &g, double *frac_times_n, bool *outside)
+{
+    const double s = __dmul_rn(__dadd_rn(xv, g.rB), g.inv_box);
+    *outside = !(s >= 0.0 && s < 1.0);
+    const double sn = __dmul_rn(s, (double)g.n);
+    int c = (int)floor(sn);
+    c = c < 0 ? 0 : (c > g.n - 1 ? g.n - 1 : c);
+    *frac_times_n = sn;
+    return c;
+}
+
+__global__ void k_bin_np(int N, const float *__restrict__ x, Geo g, int *__restrict__ cellid,
+                         int *__restrict__ rank, int *__restrict__ count, int *__restrict__ flag,
+                         float4 *__restrict__ loc)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int c[3];
+    float l[3];
+    bool bad = false, out = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double xv = (double)x[3 * (int64_t)i + a];
+        if (!isfinite(xv)) { bad = true; xv = 0.0; }
+        double sn;
+        bool o;
+        c[a] = leaf_coord_np(xv, g, &sn, &o);
+        out |= o;
+        l[a] = (float)__dmul_rn(__dadd_rn(sn, -((double)c[a] + 0.5)), g.h);
+    }
+    if (bad) atomicOr(flag, 1);
+    if (out) atomicOr(flag, 8);
+    int cell = (c[0] * g.n + c[1]) * g.n + c[2];
+    cellid[i] = cell;
+    loc[i] = make_float4(l[0], l[1], l[2], 0.f);
+    rank[i] = atomicAdd(&count[cell], 1);
+}
+
 // Exclusive scan of the per-leaf counts (single block, 1024 threads).
 __global__ void k_scan(int ncell, const int *__restrict__ count, int *__restrict__ start)
 {
@@ -196,7 +263,7 @@ __device__ __forceinline__ float self_energy_atom(float q, float mx, float my, f
 }
 
 __global__ void __launch_bounds__(256)
-k_gather(int N, const int *__restrict__ inv, const float *__restrict__ x,
+k_gather(int N, const int *__restrict__ inv, const int *__restrict__ cellid, const float4 *__restrict__ loc,
          const float *__restrict__ q, const float *__restrict__ mu,
          const float *__restrict__ th, Geo g, int *__restrict__ scell,
          float4 *__restrict__ A0, float4 *__restrict__ A1, float4 *__restrict__ A2,
@@ -207,18 +274,9 @@ k_gather(int N, const int *__restrict__ inv, const float *__restrict__ x,
     double es = 0.0, qs = 0.0;
     if (i < N) {
     const int s = inv[i];
-    float l[3];
-    int c[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        double xv = (double)x[3 * (int64_t)i + a];
-        if (!isfinite(xv)) xv = 0.0;
-        double sn;
-        c[a] = leaf_coord(xv, g, &sn);
-        double loc = __dmul_rn(__dadd_rn(sn, -((double)c[a] + 0.5)), g.h);
-        l[a] = (float)loc;
-    }
-    scell[s] = (c[0] * g.n + c[1]) * g.n + c[2];
+    const float4 lv = loc[i];
+    const float l[3] = {lv.x, lv.y, lv.z};
+    scell[s] = cellid[i];
     const float qi = q[i];
     A0[s] = make_float4(l[0], l[1], l[2], qi);
     float m3[3] = {0.f, 0.f, 0.f}, t6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -262,7 +320,12 @@ cudaError_t launch_bin(Handle &H, const float *x, cudaStream_t s)
     cudaMemsetAsync(H.d_count, 0, sizeof(int) * H.g.ncell, s);
     cudaMemsetAsync(H.d_flag, 0, sizeof(int), s);
     int N = (int)H.N;
-    k_bin<<<(N + 255) / 256, 256, 0, s>>>(N, x, H.g, H.d_cellid, H.d_rank, H.d_count, H.d_flag);
+    if (H.g.nonperiodic)
+        k_bin_np<<<(N + 255) / 256, 256, 0, s>>>(N, x, H.g, H.d_cellid, H.d_rank, H.d_count, H.d_flag,
+                                                  H.d_loc);
+    else
+        k_bin_loc<<<(N + 255) / 256, 256, 0, s>>>(N, x, H.g, H.d_cellid, H.d_rank, H.d_count, H.d_flag,
+                                                   H.d_loc);
     return cudaGetLastError();
 }
 
@@ -280,7 +343,8 @@ cudaError_t launch_scatter_sort_gather(Handle &H, const float *x, const float *q
     int N = (int)H.N;
     k_scatter<<<(N + 255) / 256, 256, 0, s>>>(N, H.d_cellid, H.d_rank, H.d_start, H.d_perm);
     k_leafsort_inv<<<(H.g.ncell + 127) / 128, 128, 0, s>>>(H.g.ncell, H.d_start, H.d_perm, H.d_inv);
-    k_gather<<<(N + 255) / 256, 256, 0, s>>>(N, H.d_inv, x, q, H.max_order >= 1 ? mu : nullptr,
+    (void)x;
+    k_gather<<<(N + 255) / 256, 256, 0, s>>>(N, H.d_inv, H.d_cellid, H.d_loc, q, H.max_order >= 1 ? mu : nullptr,
                                               H.max_order >= 2 ? theta : nullptr, H.g, H.d_scell,
                                               H.d_A0, H.d_A1, H.d_A2, H.d_A3, H.d_part + H.part_off[kPartSelf],
                                               H.d_part + H.part_off[kPartQ]);

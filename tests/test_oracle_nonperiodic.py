@@ -47,6 +47,13 @@ def test_direct_sum_dipole_pair_closed_form():
     assert E == pytest.approx(ref, rel=1e-13)
 
 
+def test_direct_rows_are_rows_of_the_direct_sum(box648):
+    b, mp, _, gd = box648
+    rows = [0, 17, 301, 647]
+    gr = ew.direct_nonperiodic_rows(b.x.astype(np.float64), mp, rows)
+    assert np.allclose(gr, gd[rows], rtol=1e-13, atol=1e-13)
+
+
 def test_far_field_fft_equals_dense_double_loop(box648):
     b, mp, _, _ = box648
     for n, Lu in ((4, 4), (3, 5)):
