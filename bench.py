@@ -301,6 +301,60 @@ def run_replicas(args, rank, world, dev, api, synth, dist=None):
     bt.close()
 
 
+def run_induce(args, rank, world, dev, api, synth, dist, cfg):
+    """Induced dipoles of the workload (point polarizability 0.005 A^3 per
+    atom: positive definite down to 0.22 A separations): one step = one full
+    conjugate-gradient solve to |r| <= 1e-6 |F|, each iteration one ANKH
+    field evaluation.  Reported: solves/s, iterations, ms per iteration."""
+    import torch
+    box = synth.config_box(cfg)
+    f32 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
+    x, q, mu, th = f32(box.x), f32(box.q), f32(box.mu), f32(box.theta)
+    alpha = torch.full((box.n,), 0.005, device=dev)
+    n_cells = args.n_cells
+    if n_cells == 0:
+        from paper_2212_08284_gb300 import autotune
+        n_cells, _ = autotune.autotune_n(box.box, x, q, mu, th, Lu=args.Lu, Lc=args.Lu, mixed=not args.plain,
+                                         nonperiodic=args.nonperiodic)
+    model = api.Ankh(box.box, box.n, n_cells=n_cells, Lu=args.Lu, Lc=args.Lu, mixed=not args.plain,
+                     nonperiodic=args.nonperiodic)
+    out = torch.empty((box.n, 3), device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        E_pol, it = api.ankh_induce(model.h, x, q, mu, th, alpha, out, tol=1e-6, stream=stream)
+    clocks = ClockSampler(dev.index)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    its = []
+    for _ in range(args.steps):
+        E_pol, it = api.ankh_induce(model.h, x, q, mu, th, alpha, out, tol=1e-6, stream=stream)
+        its.append(it)
+    e1.record(stream)
+    e1.synchronize()
+    clk = clocks.stop()
+    t = max_over_ranks(e0.elapsed_time(e1) / 1e3, dist, dev)
+    value = world * args.steps / t
+    evals = args.steps * (statistics.mean(its) + 2)
+    if rank == 0:
+        print(json.dumps({
+            "metric": "induced-dipole solves/s (CG to 1e-6 on the ANKH field)", "value": value,
+            "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": box.name + ("_nonperiodic" if args.nonperiodic else "") + "_induce",
+                       "n_atoms": box.n, "n_cells": n_cells, "Lu": args.Lu, "alpha_A3": 0.005, "tol": 1e-6,
+                       "parallelism": f"replicas{world}"},
+            "iterations": statistics.mean(its), "ms_per_field_evaluation": t * 1e3 / evals,
+            "E_pol": E_pol, "clocks": clk, "roofline": None, "cpu_baseline": None, "e2e": None,
+            "gpu_launches": None}), flush=True)
+    model.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -309,6 +363,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="water_1008000", choices=sorted(WORKLOADS))
     ap.add_argument("--plain", action="store_true", help="plain FP32 adjacent-leaf correction")
+    ap.add_argument("--induce", action="store_true",
+                    help="time induced-dipole solves (conjugate gradients on the ANKH field) instead")
     ap.add_argument("--nonperiodic", action="store_true",
                     help="no periodic images (bare kernel, zero-padded far field, Sec. 5.2)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -342,6 +398,9 @@ def main():
     cfg = WORKLOADS[args.workload]
     if cfg == 5:
         run_replicas(args, rank, world, dev, api, synth, dist)
+        return
+    if args.induce:
+        run_induce(args, rank, world, dev, api, synth, dist, cfg)
         return
     box = synth.config_box(cfg) if rank == 0 else synth.water_box(
         synth.CONFIGS[cfg]["n_waters"], synth.SEED_BASE + cfg + 1000 * rank, multipoles=True,

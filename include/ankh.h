@@ -38,8 +38,9 @@ enum {
     ANKH_ENOMEM = 2,   /* device or host allocation failed; nothing leaked */
     ANKH_ECUDA = 3,    /* a CUDA or cuFFT call failed */
     ANKH_ETIMEOUT = 4, /* a bounded device-side wait ran out */
-    ANKH_ENUMERIC = 5  /* a non-finite input coordinate was seen, or two atoms
+    ANKH_ENUMERIC = 5, /* a non-finite input coordinate was seen, or two atoms
                           share one position (infinite energy) */
+    ANKH_ENOTCONV = 6  /* an iterative solve (ankh_induce) did not converge */
 };
 
 /* flags */
@@ -117,6 +118,32 @@ int ankh_energy_forces(ankh_handle *h, const float *x, const float *q, const flo
 int ankh_energy_forces_host(ankh_handle *h, const float *x, const float *q, const float *mu,
                             const float *theta, double *E, float *dEdx, float *dEdq,
                             float *dEdmu, float *dEdtheta, float *torque, void *cuda_stream);
+
+/* Induced dipoles of point-polarizable atoms (the polarizable force fields
+ * named in Sec. 1 and 6 of the paper as a use of the repeated field
+ * evaluations): every atom i carries an isotropic polarizability alpha_i
+ * (A^3, > 0) and the induced dipole
+ *     mu_ind_i = alpha_i (F_i^perm + F_i(mu_ind)),
+ * where F_i = -dE/dmu_i is the field of all other atoms and all periodic
+ * images (the periodic boundary of the handle; ANKH_NONPERIODIC: no images),
+ * F^perm that of the permanent multipoles (q, mu, theta as for
+ * ankh_energy).  Solved by conjugate gradients with the preconditioner
+ * diag(alpha) on (diag(1/alpha) - T) mu_ind = F^perm, T mu = F(mu) being one
+ * ANKH evaluation of the dipoles mu alone (the adjoint path); no damping of
+ * the short-range dipole-dipole field (point polarizabilities: the system
+ * must be positive definite).  Initial guess alpha F^perm; stops when
+ * |residual| <= tol |F^perm| (2-norms) or after max_iter iterations.
+ * x, q: N x 3 and N device; mu: N x 3 device or NULL; theta: N x 6 device or
+ * NULL; alpha: N device; mu_ind: N x 3 device output (caller-allocated).
+ * *E_pol (host, may be NULL) receives -1/2 sum mu_ind . F^perm; *iterations
+ * (host, may be NULL) the number of CG iterations.  Synchronises the stream
+ * once per iteration.  Errors: ANKH_EINVAL (NULL, tol <= 0, alpha <= 0),
+ * ANKH_ENUMERIC (non-finite input, or the system is not positive definite),
+ * ANKH_ENOTCONV (max_iter reached; mu_ind holds the last iterate),
+ * ANKH_ENOMEM, ANKH_ECUDA. */
+int ankh_induce(ankh_handle *h, const float *x, const float *q, const float *mu, const float *theta,
+                const float *alpha, double tol, int max_iter, float *mu_ind, double *E_pol, int *iterations,
+                void *cuda_stream);
 
 /* Energy terms of the last completed call on h, in e^2/A:
  * [0] near field, [1] far field on the merged grid (k != 0), [2] its k = 0

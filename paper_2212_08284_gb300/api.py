@@ -18,7 +18,7 @@ import threading
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libankh.so")
 
-ANKH_OK, ANKH_EINVAL, ANKH_ENOMEM, ANKH_ECUDA, ANKH_ETIMEOUT, ANKH_ENUMERIC = range(6)
+ANKH_OK, ANKH_EINVAL, ANKH_ENOMEM, ANKH_ECUDA, ANKH_ETIMEOUT, ANKH_ENUMERIC, ANKH_ENOTCONV = range(7)
 ANKH_INCLUDE_REC = 1
 ANKH_MIXED = 2
 ANKH_NONPERIODIC = 4
@@ -30,7 +30,7 @@ EXPORTED = ["ankh_default_params", "ankh_create", "ankh_energy", "ankh_energy_fo
             "ankh_energy_forces_host", "ankh_last_terms", "ankh_get_info", "ankh_debug_copy",
             "ankh_ldm", "ankh_set_timing", "ankh_stage_times", "ankh_bin_sort_noalloc", "ankh_destroy",
             "ankh_last_error", "ankh_version", "ankh_create_batch", "ankh_energy_forces_batch",
-            "ankh_batch_box", "ankh_destroy_batch"]
+            "ankh_batch_box", "ankh_destroy_batch", "ankh_induce"]
 STAGES = ["sort", "self", "p2m", "merge", "fft_fwd", "spectral", "corr", "near", "fft_inv", "l2p",
           "unused", "reduce"]
 
@@ -79,6 +79,9 @@ def load_library(path: str = LIB_PATH):
         lib.ankh_energy_forces.restype = ctypes.c_int
         lib.ankh_energy_forces_host.argtypes = [vp, vp, vp, vp, vp, dp, vp, vp, vp, vp, vp, vp]
         lib.ankh_energy_forces_host.restype = ctypes.c_int
+        lib.ankh_induce.argtypes = [vp, vp, vp, vp, vp, vp, ctypes.c_double, ctypes.c_int, vp, dp,
+                                    ctypes.POINTER(ctypes.c_int), vp]
+        lib.ankh_induce.restype = ctypes.c_int
         lib.ankh_last_terms.argtypes = [vp, dp]
         lib.ankh_last_terms.restype = ctypes.c_int
         lib.ankh_get_info.argtypes = [vp, ctypes.POINTER(ankh_info)]
@@ -166,6 +169,18 @@ def ankh_energy(h, x, q, mu=None, theta=None, stream=None) -> float:
     _check(load_library().ankh_energy(h, _ptr(x), _ptr(q), _ptr(mu), _ptr(theta), ctypes.byref(E),
                                       _stream_ptr(stream)))
     return E.value
+
+
+def ankh_induce(h, x, q, mu, theta, alpha, mu_ind, tol: float = 1e-6, max_iter: int = 50, stream=None):
+    """Induced dipoles (conjugate gradients on the ANKH field) into mu_ind
+    (N x 3 float32 CUDA tensor).  Returns (E_pol, iterations)."""
+    _check_tensor(x, (3,), "x"); _check_tensor(mu_ind, (3,), "mu_ind")
+    E = ctypes.c_double()
+    it = ctypes.c_int()
+    _check(load_library().ankh_induce(h, _ptr(x), _ptr(q), _ptr(mu), _ptr(theta), _ptr(alpha), float(tol),
+                                      int(max_iter), _ptr(mu_ind), ctypes.byref(E), ctypes.byref(it),
+                                      _stream_ptr(stream)))
+    return E.value, it.value
 
 
 def ankh_energy_forces(h, x, q, mu=None, theta=None, dEdx=None, dEdq=None, dEdmu=None, dEdtheta=None,
@@ -300,6 +315,14 @@ class Ankh:
 
     def terms(self):
         return ankh_last_terms(self.h)
+
+    def induce(self, x, q, mu, theta, alpha, tol: float = 1e-6, max_iter: int = 50):
+        """Induced dipoles of point polarizabilities alpha (N); returns
+        (mu_ind N x 3 tensor, E_pol, iterations)."""
+        import torch
+        out = torch.empty((self.n_atoms, 3), device=x.device, dtype=torch.float32)
+        E, it = ankh_induce(self.h, x, q, mu, theta, alpha, out, tol=tol, max_iter=max_iter)
+        return out, E, it
 
 
 def ankh_create_batch(box_edges, n_atoms, params: ankh_params | None = None) -> ctypes.c_void_p:

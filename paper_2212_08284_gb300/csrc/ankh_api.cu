@@ -167,7 +167,7 @@ static void free_device(Handle *H)
     void *ptrs[] = {H->d_cellid, H->d_rank, H->d_count, H->d_start, H->d_perm, H->d_inv, H->d_loc, H->d_scell, H->d_flag, H->d_bsum,
                     H->d_A0, H->d_A1, H->d_A2, H->d_A3, H->d_W, H->d_M, H->d_rho, H->d_rhohat, H->d_D,
                     H->d_phi, H->d_C, H->d_Chi, H->d_Clo, H->d_psi, H->d_gnear, H->d_pi, H->d_part,
-                    H->d_partoff, H->d_terms, H->d_hostbuf, H->d_Mhi, H->d_Mlo, H->d_mmax};
+                    H->d_partoff, H->d_terms, H->d_hostbuf, H->d_Mhi, H->d_Mlo, H->d_mmax, H->d_ind, H->d_ind_part};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (H->h_terms) cudaFreeHost(H->h_terms);
@@ -239,7 +239,7 @@ int run_sequence(Handle &H, const float *x, const float *q, const float *mu, con
     return ANKH_OK;
 }
 
-static int fetch_terms(Handle &H, double *E_host, cudaStream_t s)
+int fetch_terms(Handle &H, double *E_host, cudaStream_t s)
 {
     ANKH_CU(cudaMemcpyAsync(H.h_terms, H.d_terms, 9 * sizeof(double), cudaMemcpyDeviceToHost, s), "copy E");
     ANKH_CU(cudaStreamSynchronize(s), "synchronize");
@@ -534,6 +534,19 @@ int ankh_energy_forces_host(ankh_handle *h, const float *x, const float *q, cons
     if (rc) return rc;
     if (E) *E = Ed;
     return ANKH_OK;
+}
+
+int ankh_induce(ankh_handle *h, const float *x, const float *q, const float *mu, const float *theta,
+                const float *alpha, double tol, int max_iter, float *mu_ind, double *E_pol, int *iterations,
+                void *cuda_stream)
+{
+    if (!h || !x || !q || !alpha || !mu_ind) return fail(ANKH_EINVAL, "NULL argument");
+    if (!(tol > 0.0) || !std::isfinite(tol) || max_iter < 0) return fail(ANKH_EINVAL, "tol must be > 0, max_iter >= 0");
+    std::string err;
+    const int rc = induce_dipoles(h->h, x, q, mu, theta, alpha, tol, max_iter, mu_ind, E_pol, iterations,
+                                  (cudaStream_t)cuda_stream, err);
+    if (rc != ANKH_OK && !err.empty()) return fail(rc, err);
+    return rc;
 }
 
 int ankh_last_terms(const ankh_handle *h, double terms[6])

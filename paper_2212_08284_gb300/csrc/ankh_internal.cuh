@@ -58,6 +58,8 @@ struct Handle {
     __half *d_Mhi, *d_Mlo;  // [n*n*rowstride][ldk] fp16 split of 2^eM M, z-halo rows (tensor-core path)
     __half *d_Chi, *d_Clo;  // [halves*128][27*ldk] fp16 split of 2^eC [C_0 | ... | C_26]
     unsigned *d_mmax;       // max |M| of the call (FP32 bits), sets eM
+    float *d_ind;           // induced-dipole workspace (allocated on first use)
+    double *d_ind_part;
     int64_t N;
     int max_order;
     unsigned flags;
@@ -122,6 +124,12 @@ cudaError_t launch_near(Handle &H, bool forces, cudaStream_t s);
 cudaError_t launch_l2p(Handle &H, float *dEdx, float *dEdq, float *dEdmu, float *dEdtheta, float *torque,
                        cudaStream_t s);
 cudaError_t launch_self_dc(Handle &H, cudaStream_t s);
+int fetch_terms(Handle &H, double *E_host, cudaStream_t s);
+int run_sequence(Handle &H, const float *x, const float *q, const float *mu, const float *theta, bool forces,
+                 float *dEdx, float *dEdq, float *dEdmu, float *dEdtheta, float *torque, cudaStream_t s);
+int induce_dipoles(Handle &H, const float *x, const float *q, const float *mu, const float *theta,
+                   const float *alpha, double tol, int max_iter, float *mu_ind, double *E_pol, int *iterations,
+                   cudaStream_t s, std::string &err);
 cudaError_t launch_reduce(Handle &H, cudaStream_t s);
 
 // precomputation on the device (FP64)
