@@ -60,6 +60,20 @@ enum {
                                 (zero-padded) convolution of the non-adjacent
                                 leaves; every atom must lie inside the box,
                                 else the energy calls return ANKH_EINVAL */
+#define ANKH_FMM 8u          /* ANKH-FMM (Sec. 3, Alg. 3) in place of ANKH-FFT:
+                                perfect octree with n_cells = 2^E leaves per
+                                axis (2 <= E <= 7; 0 picks the leaf edge
+                                nearest 4 A), L = Lu = Lc first-kind
+                                Chebyshev nodes per axis in every cell (L <= 8),
+                                M2M up the tree, mutual M2L on the tensor cores
+                                (fp16 hi + lo split, FP32 accumulation),
+                                images beyond the direct ones through the root
+                                expansion.  Energy only: ankh_energy_forces,
+                                the batch and ankh_induce return ANKH_EINVAL.
+                                Periodic boxes only.  Stage timings: "merge"
+                                holds M2M, "spectral" the root term, "corr"
+                                the M2L; ankh_last_terms: [1] root term,
+                                [2] 0, [3] M2L far field */
 
 typedef struct {
     double xi;        /* Ewald screening [1/A]; Sec. 5 uses 0.01 */

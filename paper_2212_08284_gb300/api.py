@@ -22,6 +22,7 @@ ANKH_OK, ANKH_EINVAL, ANKH_ENOMEM, ANKH_ECUDA, ANKH_ETIMEOUT, ANKH_ENUMERIC, ANK
 ANKH_INCLUDE_REC = 1
 ANKH_MIXED = 2
 ANKH_NONPERIODIC = 4
+ANKH_FMM = 8
 
 # buffer ids of ankh_debug_copy
 BUF_PERM, BUF_START, BUF_M, BUF_RHO, BUF_PSI, BUF_SCELL = range(6)
@@ -271,7 +272,7 @@ class Ankh:
 
     def __init__(self, box_edge: float, n_atoms: int, xi: float = 0.01, n_cells: int = 0, Lu: int = 5,
                  Lc: int = 0, max_order: int = 2, include_rec: bool = True, mixed: bool = True,
-                 nonperiodic: bool = False):
+                 nonperiodic: bool = False, fmm: bool = False):
         p = ankh_default_params()
         p.xi = xi
         p.n_cells = n_cells
@@ -279,7 +280,7 @@ class Ankh:
         p.Lc = Lc
         p.max_order = max_order
         p.flags = ((ANKH_INCLUDE_REC if include_rec else 0) | (ANKH_MIXED if mixed else 0)
-                   | (ANKH_NONPERIODIC if nonperiodic else 0))
+                   | (ANKH_NONPERIODIC if nonperiodic else 0) | (ANKH_FMM if fmm else 0))
         self.n_atoms = int(n_atoms)
         self.box = float(box_edge)
         self.h = ankh_create(box_edge, n_atoms, p)

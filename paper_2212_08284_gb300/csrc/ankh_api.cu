@@ -35,13 +35,14 @@ static int fail(int code, const std::string &msg)
 // Host FP64 tables
 
 // Fused Chebyshev -> equispaced derivative matrices W_p = (2/h)^p E H D^p,
-// p = 0..3, each L_u x L_c (Sec. 3.4 and 4.1):
+// p = 0..3, each L_u x L_c (Sec. 3.4 and 4.1); at_cheb: E = I (L_u = L_c), the
+// values at the Chebyshev nodes themselves (S^(p) of Alg. 2, for ANKH-FMM):
 //   Chebyshev nodes r_k = cos((2k+1) pi / (2 L_c));
 //   H[k][m] = (m == 0 ? 1 : 2 T_m(r_k)) / L_c        (S = H T);
 //   D with T' = D T: D[m][j] = 2m / c_j for j < m, m - j odd (c_0 = 2);
 //   E[a][k] = U_a(r_k), U_a the Lagrange basis of the L_u equispaced nodes
 //   -1 + 2a/(L_u - 1).
-static std::vector<double> make_W(int Lu, int Lc, double h)
+static std::vector<double> make_W(int Lu, int Lc, double h, bool at_cheb)
 {
     std::vector<double> r(Lc), Hm(Lc * Lc), Dm(Lc * Lc, 0.0), Em(Lu * Lc);
     for (int k = 0; k < Lc; ++k) r[k] = std::cos((2.0 * k + 1.0) * M_PI / (2.0 * Lc));
@@ -70,7 +71,7 @@ static std::vector<double> make_W(int Lu, int Lc, double h)
                 double ec = -1.0 + 2.0 * c / (Lu - 1);
                 u *= (r[k] - ec) / (ea - ec);
             }
-            Em[a * Lc + k] = u;
+            Em[a * Lc + k] = at_cheb ? (a == k ? 1.0 : 0.0) : u;
         }
     std::vector<double> W(4 * Lu * Lc);
     std::vector<double> Dp(Lc * Lc, 0.0), tmp(Lc * Lc);
@@ -161,6 +162,13 @@ static int choose_n(double box, int Lu)
     return best;
 }
 
+// ANKH-FMM: n = 2^E with the leaf edge nearest to 4 A (log scale), 2 <= E <= 7
+static int choose_n_fmm(double box)
+{
+    const int E = (int)std::lround(std::log2(box / 4.0));
+    return 1 << std::min(7, std::max(2, E));
+}
+
 static void free_device(Handle *H)
 {
     if (!H) return;
@@ -170,6 +178,7 @@ static void free_device(Handle *H)
                     H->d_partoff, H->d_terms, H->d_hostbuf, H->d_Mhi, H->d_Mlo, H->d_mmax, H->d_ind, H->d_ind_part};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    fmm_free(*H);
     if (H->h_terms) cudaFreeHost(H->h_terms);
     if (H->have_events)
         for (int k = 0; k <= kNumStages; ++k) cudaEventDestroy(H->ev[k]);
@@ -190,7 +199,7 @@ static cudaError_t dalloc(Handle *H, T **p, size_t count)
     return e;
 }
 
-static void mark(Handle &H, int stage_done, cudaStream_t s)
+void mark_stage(Handle &H, int stage_done, cudaStream_t s)
 {
     if (!H.timing || !H.have_events || H.nrec > kNumStages) return;
     cudaEventRecord(H.ev[H.nrec], s);
@@ -202,40 +211,44 @@ int run_sequence(Handle &H, const float *x, const float *q, const float *mu, con
                         bool forces, float *dEdx, float *dEdq, float *dEdmu, float *dEdtheta, float *torque,
                         cudaStream_t s)
 {
+    if (H.fmm.enabled) {
+        if (forces) return fail(ANKH_EINVAL, "ANKH_FMM computes the energy only (Alg. 3)");
+        return run_fmm(H, x, q, mu, theta, s);
+    }
     H.nrec = 0;
-    mark(H, -1, s);
+    mark_stage(H, -1, s);
     ANKH_CU(launch_bin(H, x, s), "bin");
     ANKH_CU(launch_scan(H, s), "scan");
     ANKH_CU(launch_scatter_sort_gather(H, x, q, mu, theta, s), "sort");
-    mark(H, kStSort, s);
+    mark_stage(H, kStSort, s);
     ANKH_CU(launch_self_dc(H, s), "self");
-    mark(H, kStSelf, s);
+    mark_stage(H, kStSelf, s);
     ANKH_CU(launch_p2m(H, s), "p2m");
-    mark(H, kStP2M, s);
+    mark_stage(H, kStP2M, s);
     ANKH_CU(launch_fine_gather(H, s), "merge");
-    mark(H, kStMerge, s);
+    mark_stage(H, kStMerge, s);
     if (cufftSetStream(H.plan_r2c, s) != CUFFT_SUCCESS) return fail(ANKH_ECUDA, "cufftSetStream");
     if (cufftExecR2C(H.plan_r2c, H.d_rho, H.d_rhohat) != CUFFT_SUCCESS) return fail(ANKH_ECUDA, "cufftExecR2C");
-    mark(H, kStFFTf, s);
+    mark_stage(H, kStFFTf, s);
     ANKH_CU(launch_spectral(H, forces, s), "spectral");
-    mark(H, kStSpectral, s);
+    mark_stage(H, kStSpectral, s);
     if (H.tc.enabled && (H.flags & ANKH_MIXED))
         ANKH_CU(launch_corr_tc(H, forces, s), "corr (tensor cores)");
     else
         ANKH_CU(launch_corr(H, forces, s), "corr");
-    mark(H, kStCorr, s);
+    mark_stage(H, kStCorr, s);
     ANKH_CU(launch_near(H, forces, s), "near");
-    mark(H, kStNear, s);
+    mark_stage(H, kStNear, s);
     if (forces) {
         if (cufftSetStream(H.plan_c2r, s) != CUFFT_SUCCESS) return fail(ANKH_ECUDA, "cufftSetStream");
         if (cufftExecC2R(H.plan_c2r, H.d_rhohat, H.d_phi) != CUFFT_SUCCESS)
             return fail(ANKH_ECUDA, "cufftExecC2R");
-        mark(H, kStFFTi, s);
+        mark_stage(H, kStFFTi, s);
         ANKH_CU(launch_l2p(H, dEdx, dEdq, dEdmu, dEdtheta, torque, s), "l2p");
-        mark(H, kStL2P, s);
+        mark_stage(H, kStL2P, s);
     }
     ANKH_CU(launch_reduce(H, s), "reduce");
-    mark(H, kStReduce, s);
+    mark_stage(H, kStReduce, s);
     return ANKH_OK;
 }
 
@@ -292,14 +305,17 @@ int ankh_create(double box_edge, int64_t N, const ankh_params *params, ankh_hand
     if (p.Lu < 2 || p.Lu > kMaxLu) return fail(ANKH_EINVAL, "Lu out of range [2, 8]");
     if (p.Lc < 2 || p.Lc > kMaxLc) return fail(ANKH_EINVAL, "Lc out of range [2, 16]");
     const bool nonper = (p.flags & ANKH_NONPERIODIC) != 0;
+    const bool fmm = (p.flags & ANKH_FMM) != 0;
+    if (fmm && nonper) return fail(ANKH_EINVAL, "ANKH_FMM: periodic boxes only");
+    if (fmm && p.Lc != p.Lu) return fail(ANKH_EINVAL, "ANKH_FMM: one Chebyshev order (Lc = Lu)");
     if (nonper) p.xi = 0.0;   // bare kernel
     else if (!(p.xi > 0.0) || !std::isfinite(p.xi)) return fail(ANKH_EINVAL, "xi must be > 0");
     if (p.max_order < 0 || p.max_order > 2) return fail(ANKH_EINVAL, "max_order out of range [0, 2]");
-    int n = p.n_cells ? p.n_cells : choose_n(box_edge, p.Lu);
+    int n = p.n_cells ? p.n_cells : (fmm ? choose_n_fmm(box_edge) : choose_n(box_edge, p.Lu));
     if (n < 3) return fail(ANKH_EINVAL, "at least 3 leaves per axis are needed");
     // non-periodic: the n (L_u - 1) + 1 nodes per axis are zero-padded to at
     // least twice that minus one, so the circular convolution is the linear one
-    const int ngrid = nonper ? next_fft_size(2 * (n * (p.Lu - 1) + 1) - 1) : n * (p.Lu - 1);
+    const int ngrid = fmm ? 0 : (nonper ? next_fft_size(2 * (n * (p.Lu - 1) + 1) - 1) : n * (p.Lu - 1));
     if (ngrid > 1024) return fail(ANKH_EINVAL, "FFT grid larger than 1024 points per axis");
 
     auto t0 = std::chrono::steady_clock::now();
@@ -322,7 +338,7 @@ int ankh_create(double box_edge, int64_t N, const ankh_params *params, ankh_hand
     g.nfh = g.nf / 2 + 1;
     g.nonperiodic = nonper ? 1 : 0;
     g.ng = nonper ? n * (p.Lu - 1) + 1 : g.nf;
-    g.M = (int64_t)g.nf * g.nf * g.nf;
+    g.M = fmm ? 1 : (int64_t)g.nf * g.nf * g.nf;   // (no grid for ANKH-FMM)
     g.box = box_edge;
     g.rB = box_edge / 2.0;
     g.inv_box = 1.0 / box_edge;
@@ -360,20 +376,23 @@ int ankh_create(double box_edge, int64_t N, const ankh_params *params, ankh_hand
     ANKH_AL(H.d_A3, N);
     ANKH_AL(H.d_W, 4 * g.Lu * g.Lc);
     ANKH_AL(H.d_M, (int64_t)g.ncell * g.ldm);
-    ANKH_AL(H.d_rho, g.M);
-    cudaMemset(H.d_rho, 0, sizeof(float) * g.M);   // the zero padding of the non-periodic grid
-    ANKH_AL(H.d_rhohat, nspec);
-    ANKH_AL(H.d_D, nspec);
-    ANKH_AL(H.d_phi, g.M);
-    ANKH_AL(H.d_C, (int64_t)27 * g.ldm * g.ldm);
-    ANKH_AL(H.d_psi, (int64_t)g.ncell * g.ldm);
-    ANKH_AL(H.d_gnear, 13 * N);
-    ANKH_AL(H.d_pi, (int64_t)g.ncell * g.ldm);
-    // energy partial layout
+    if (!fmm) {
+        ANKH_AL(H.d_rho, g.M);
+        cudaMemset(H.d_rho, 0, sizeof(float) * g.M);   // the zero padding of the non-periodic grid
+        ANKH_AL(H.d_rhohat, nspec);
+        ANKH_AL(H.d_D, nspec);
+        ANKH_AL(H.d_phi, g.M);
+        ANKH_AL(H.d_C, (int64_t)27 * g.ldm * g.ldm);
+        ANKH_AL(H.d_psi, (int64_t)g.ncell * g.ldm);
+        ANKH_AL(H.d_gnear, 13 * N);
+        ANKH_AL(H.d_pi, (int64_t)g.ncell * g.ldm);
+    }
+    // energy partial layout (ANKH-FMM: the root term in the far slot, the M2L CTAs in the correction slot)
     int nb[kPartCount];
     nb[kPartNear] = near_blocks(H);
-    nb[kPartGlob] = spectral_blocks(H);
-    nb[kPartCorr] = std::max(corr_blocks(H), tc_max_blocks(n, g.ldm));   // SIMT or tensor-core CTAs
+    nb[kPartGlob] = fmm ? 1 : spectral_blocks(H);
+    nb[kPartCorr] = fmm ? fmm_part_slots(H)
+                        : std::max(corr_blocks(H), tc_max_blocks(n, g.ldm));   // SIMT or tensor-core CTAs
     nb[kPartSelf] = self_blocks(H);
     nb[kPartQ] = self_blocks(H);
     H.part_off[0] = 0;
@@ -387,16 +406,29 @@ int ankh_create(double box_edge, int64_t N, const ankh_params *params, ankh_hand
         return bail(ANKH_ECUDA, "upload part offsets");
     cudaMemset(H.d_part, 0, sizeof(double) * H.part_off[kPartCount]);
     cudaMemset(H.d_terms, 0, 9 * sizeof(double));
-    cudaMemset(H.d_psi, 0, sizeof(float) * (size_t)g.ncell * g.ldm);
+    if (H.d_psi) cudaMemset(H.d_psi, 0, sizeof(float) * (size_t)g.ncell * g.ldm);
+    cudaMemset(H.d_M, 0, sizeof(float) * (size_t)g.ncell * g.ldm);
 
     // tables
     {
-        std::vector<double> W = make_W(g.Lu, g.Lc, g.h);
+        std::vector<double> W = make_W(g.Lu, g.Lc, g.h, fmm);
         std::vector<float> Wf(W.begin(), W.end());
         if (cudaMemcpy(H.d_W, Wf.data(), Wf.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
             return bail(ANKH_ECUDA, "upload W");
         if (g.Lc == g.Lu && g.Lu <= 8)
             for (size_t k = 0; k < Wf.size(); ++k) H.h_Wf[k] = Wf[k];
+    }
+    if (fmm) {
+        std::string ferr;
+        const int frc = fmm_prepare(H, p.xi, (p.flags & ANKH_INCLUDE_REC) != 0, ferr);
+        if (frc != ANKH_OK) return bail(frc, ferr);
+        if (cudaDeviceSynchronize() != cudaSuccess) return bail(ANKH_ECUDA, "precompute synchronize");
+        H.precompute_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        *out = hh;
+        set_error("");
+        return ANKH_OK;
+    }
+    {
         std::vector<double> C = make_C(g.Lu, g.ldm, g.h / (g.Lu - 1), p.xi);
         std::vector<float> Cf(C.begin(), C.end());
         if (cudaMemcpy(H.d_C, Cf.data(), Cf.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
@@ -541,6 +573,7 @@ int ankh_induce(ankh_handle *h, const float *x, const float *q, const float *mu,
                 void *cuda_stream)
 {
     if (!h || !x || !q || !alpha || !mu_ind) return fail(ANKH_EINVAL, "NULL argument");
+    if (h->h.fmm.enabled) return fail(ANKH_EINVAL, "ANKH_FMM computes the energy only (no fields)");
     if (!(tol > 0.0) || !std::isfinite(tol) || max_iter < 0) return fail(ANKH_EINVAL, "tol must be > 0, max_iter >= 0");
     std::string err;
     const int rc = induce_dipoles(h->h, x, q, mu, theta, alpha, tol, max_iter, mu_ind, E_pol, iterations,
@@ -619,6 +652,7 @@ int ankh_debug_copy(const ankh_handle *h, int which, void *dst, int64_t *bytes, 
     case 5: src = H.d_scell; nb = H.N * 4; break;
     default: return fail(ANKH_EINVAL, "unknown buffer id");
     }
+    if (!src) return fail(ANKH_EINVAL, "buffer not allocated for this handle");
     *bytes = nb;
     if (!dst) return ANKH_OK;
     cudaStream_t s = (cudaStream_t)cuda_stream;

@@ -52,12 +52,48 @@ struct TcPlan {
     CUtensorMap mAhi, mAlo, mBhi, mBlo;
 };
 
+// ANKH-FMM (fmm.cu): perfect octree of depth E, L Chebyshev nodes per axis per cell.
+constexpr int kFmmMaxLevels = 8;   // E <= 7
+
+struct FmmLevel {
+    const float *M;   // [(2m)^3][ldm] expansions of the level, natural cell order
+    int m;            // parent cells per axis (2^(e-1)); the level has 2m cells per axis
+    int S, R, tiles;  // z-row of m targets padded to S = max(16, m); R = 128 / S z-rows per tile; tiles per class
+    int rowstride;    // S + 2 rows per z-row of the split operand (one-cell z halo)
+    int rowbase;      // first row of the level in the split operand
+    int acol;         // first column of the level in the operator table
+    int eC;           // C_e(d) scaled by 2^eC before the fp16 split
+};
+
+struct FmmLevels {
+    FmmLevel lv[kFmmMaxLevels];   // lv[e], e = 1 .. E (lv[0] unused)
+};
+
+struct FmmPlan {
+    int enabled;
+    int E, L, ldk, kch, slices;
+    int nitems, grid, ntab;
+    int64_t brows;          // rows of the split operand (all levels)
+    uint32_t tmem_cols;
+    float *d_Mlev[kFmmMaxLevels];   // levels 0 .. E-1 (level E is Handle::d_M)
+    __half *d_Bhi, *d_Blo;  // [brows][ldk] parity-major split expansions with a one-cell z halo
+    __half *d_Ahi, *d_Alo;  // [slices*128][E * 343 * ldk] split M2L operators C_e(d), d in [-3,3]^3
+    int4 *d_items;          // work items (level | class << 4 | slice << 8, tile, first offset, offsets)
+    int *d_tab;             // interaction offsets per class (block | class' << 9 | (D + 1) << 12..16)
+    double *d_K;            // [L^3][L^3] root operator of the images beyond the direct ones
+    float V[2][8][8];       // M2M: V[b][k][l] = S_k((2b - 1 + r_l) / 2)
+    FmmLevels lev;
+    FmmLevel *d_lev;        // device copy of lev.lv
+    CUtensorMap mAhi, mAlo, mBhi, mBlo;
+};
+
 struct Handle {
     Geo g;
     TcPlan tc;
+    FmmPlan fmm;
     __half *d_Mhi, *d_Mlo;  // [n*n*rowstride][ldk] fp16 split of 2^eM M, z-halo rows (tensor-core path)
     __half *d_Chi, *d_Clo;  // [halves*128][27*ldk] fp16 split of 2^eC [C_0 | ... | C_26]
-    unsigned *d_mmax;       // max |M| of the call (FP32 bits), sets eM
+    unsigned *d_mmax;       // max |M| of the call (FP32 bits), sets eM (ANKH-FMM: one per level)
     float *d_ind;           // induced-dipole workspace (allocated on first use)
     double *d_ind_part;
     int64_t N;
@@ -74,9 +110,9 @@ struct Handle {
     float4 *d_loc;          // [N] coordinates relative to the leaf centre (caller's order)
     float4 *d_A0, *d_A1, *d_A2, *d_A3;   // (lx, ly, lz, q) (mu, 0) (txx, txy, txz, tyy) (tyz, tzz, 0, 0)
     // interpolation
-    float *d_W;
-    float h_Wf[4 * 8 * 8];  // host copy of W for L_c = L_u <= 8 (kernel-parameter basis tables)             // [4][Lu][Lc] fused Chebyshev->equispaced derivative matrices, scaled by (2/h)^p
-    float *d_M;             // [ncell][ldm] equispaced modified charges
+    float *d_W;             // [4][Lu][Lc] derivative matrices (2/h)^p E H D^p (E = I for ANKH-FMM)
+    float h_Wf[4 * 8 * 8];  // host copy of W for L_c = L_u <= 8 (kernel-parameter basis tables)
+    float *d_M;             // [ncell][ldm] modified charges at the leaf nodes (equispaced; Chebyshev for ANKH-FMM)
     float *d_rho;           // [nf^3] merged grid charges
     cufftComplex *d_rhohat; // [nf][nf][nfh]
     float *d_D;             // [nf][nf][nfh] real spectrum of the far-field kernel (k = 0 removed)
@@ -136,6 +172,14 @@ cudaError_t launch_reduce(Handle &H, cudaStream_t s);
 cudaError_t precompute_kernel_spectrum(Handle &H, double *D0_out, std::string &err);
 
 bool tc_prepare(Handle &H, std::string &err);
+bool encode_2d(CUtensorMap *map, void *ptr, uint64_t inner, uint64_t outer, uint32_t box_inner, uint32_t box_outer,
+               std::string &err);   // 2-D fp16 tensor map, 128-byte swizzle
+// ANKH-FMM (fmm.cu)
+int fmm_prepare(Handle &H, double xi, bool include_rec, std::string &err);
+void fmm_free(Handle &H);
+int fmm_part_slots(const Handle &H);   // energy partial slots of the M2L launch
+void mark_stage(Handle &H, int stage_done, cudaStream_t s);   // optional per-stage timing
+int run_fmm(Handle &H, const float *x, const float *q, const float *mu, const float *theta, cudaStream_t s);
 void tc_tile_shape(int n, int &S, int &R);
 int tc_max_blocks(int n, int ldm);   // CTAs of the tensor-core correction (energy partial slots)
 int tc_ldk(int ldm);                 // node stride of the fp16 split operands

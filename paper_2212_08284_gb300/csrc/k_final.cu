@@ -84,7 +84,10 @@ cudaError_t launch_self_dc(Handle &H, cudaStream_t s)
 
 cudaError_t launch_reduce(Handle &H, cudaStream_t s)
 {
-    k_reduce<<<1, 256, 0, s>>>(H.d_part, H.d_partoff, 0.5 / (double)H.g.M, H.D0, H.d_flag, H.d_terms, 1, 1);
+    // ANKH-FMM: the far slot holds the root term itself and there is no k = 0 grid term
+    const double invM2 = H.fmm.enabled ? 1.0 : 0.5 / (double)H.g.M;
+    const double D0 = H.fmm.enabled ? 0.0 : H.D0;
+    k_reduce<<<1, 256, 0, s>>>(H.d_part, H.d_partoff, invM2, D0, H.d_flag, H.d_terms, 1, 1);
     return cudaGetLastError();
 }
 

@@ -415,7 +415,8 @@ static WTab<LU> wtab(const Handle &H)
 
 cudaError_t launch_p2m(Handle &H, cudaStream_t s)
 {
-    unsigned *mmax = H.tc.enabled ? H.d_mmax : nullptr;
+    // max |M| of the leaves: the fp16 split exponent of the tensor-core correction, or of the leaf level (ANKH-FMM)
+    unsigned *mmax = H.fmm.enabled ? H.d_mmax + H.fmm.E : (H.tc.enabled ? H.d_mmax : nullptr);
     if (mmax) {
         const cudaError_t e = cudaMemsetAsync(mmax, 0, sizeof(unsigned), s);
         if (e != cudaSuccess) return e;
