@@ -3,6 +3,7 @@
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload water_1008000|water_96000|water_24000] [--plain]
+                  [--nonperiodic | --induce | --fmm]
 
 One "step" is one full evaluation (bin/sort, P2M, merged-grid FFT far field,
 adjacent-leaf correction, near field, L2P, gradient assembly, FP64 energy)
@@ -301,6 +302,124 @@ def run_replicas(args, rank, world, dev, api, synth, dist=None):
     bt.close()
 
 
+def run_fmm(args, rank, world, dev, api, synth, dist, cfg):
+    """ANKH-FMM energy (Alg. 3, flag ANKH_FMM): one step = one energy
+    evaluation (sort, P2M, M2M, mutual M2L on the tensor cores, root term,
+    near field, self term) on inputs resident in HBM, L2 flushed between
+    steps.  The tree is 2^E leaves per axis (default: the leaf edge nearest
+    4 A, n = 64 for the 1M-atom box) with L = --Lu Chebyshev nodes per axis."""
+    import torch
+    box = synth.config_box(cfg) if rank == 0 else synth.water_box(
+        synth.CONFIGS[cfg]["n_waters"], synth.SEED_BASE + cfg + 1000 * rank, multipoles=True,
+        name=synth.CONFIGS[cfg]["name"])
+    N = box.n
+    f32 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
+    x, q, mu, th = f32(box.x), f32(box.q), f32(box.mu), f32(box.theta)
+    L = args.Lu
+    t_pre0 = time.perf_counter()
+    model = api.Ankh(box.box, N, n_cells=args.n_cells, Lu=L, Lc=L, fmm=True)
+    t_pre = time.perf_counter() - t_pre0
+    info = model.info
+    n = info["n_cells"]
+    depth = int(round(math.log2(n)))
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    api.ankh_set_timing(model.h, True)
+    for _ in range(max(args.warmup, 3)):
+        flush.fill_(1.0)
+        api.ankh_energy(model.h, x, q, mu, th, stream=stream)
+    clocks = ClockSampler(dev.index)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    names = {"sort": "sort", "self": "self", "p2m": "p2m", "merge": "m2m", "spectral": "root", "corr": "m2l",
+             "near": "near", "reduce": "reduce"}
+    stage_sum = {v: 0.0 for v in names.values()}
+    t_dev = 0.0
+    E = None
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        E = api.ankh_energy(model.h, x, q, mu, th, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        t_dev += e0.elapsed_time(e1) / 1e3
+        for s_, v in api.ankh_stage_times(model.h).items():
+            if s_ in names:
+                stage_sum[names[s_]] += v
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    t_max = max_over_ranks(t_dev, dist, dev)
+    value = world * args.steps / t_max
+    stage_ms = {k: v / args.steps for k, v in stage_sum.items()}
+
+    # end to end: pinned host inputs copied in, energy read back, every step
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).pin_memory()
+    hx, hq, hmu, hth = pin(box.x), pin(box.q), pin(box.mu), pin(box.theta)
+    api.ankh_set_timing(model.h, False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        x.copy_(hx, non_blocking=True)
+        q.copy_(hq, non_blocking=True)
+        mu.copy_(hmu, non_blocking=True)
+        th.copy_(hth, non_blocking=True)
+        api.ankh_energy(model.h, x, q, mu, th, stream=stream)
+    t_e2e = max_over_ranks(time.perf_counter() - t0, dist, dev)
+
+    acc = None
+    gpath = os.path.join(ROOT, "tests", "golden", f"ewald_{box.name}.json")
+    if rank == 0 and os.path.exists(gpath):
+        gd = json.load(open(gpath))
+        acc = {"rel_energy_error": abs(E - gd["E"]) / abs(gd["E"]), "reference": "FP64 Ewald oracle (tests/golden)"}
+
+    # M2L roofline: per level e, 8^e targets x 189 list members, each unordered
+    # pair once (mutual), one P x P matrix-vector product + dot = 2 P^2 flop
+    peaks, peak_kind = measured_peaks()
+    P = L ** 3
+    m2l_flop = sum(8 ** e for e in range(1, depth + 1)) * 189 / 2 * 2 * P * P
+    achieved = m2l_flop / 1e12 / (stage_ms["m2l"] / 1e3)
+    roof = {"kernel": "m2l", "bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops"],
+            "unit": "TFLOP/s", "frac": achieved / peaks["bf16_tflops"],
+            "traffic": DRAM_TRAFFIC.get(("m2l", box.name, n, L)),
+            "peak_source": f"{peak_kind} MEASURED_PEAKS bf16 (= fp16 rate; the split executes 3 products)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the oracle's ANKH-FMM on the 24,000-atom box (62.1 A) at the same
+        # order and a leaf edge of 3.9 A, scaled per atom to this workload
+        from oracle import ankh_fmm as fm
+        sb = synth.config_box(2)
+        a = time.perf_counter()
+        fm.ankh_fmm_energy(sb.x, sb.q, sb.mu, sb.theta, sb.box, 4, L)
+        ts = time.perf_counter() - a
+        cpu = {"value": 1.0 / (ts * N / sb.n), "unit": "evals/s", "cores": os.cpu_count() or 1, "kind": "oracle",
+               "sample": f"FP64 ANKH-FMM oracle, energy of the {sb.n}-atom water box at depth 4, L={L} "
+                         f"({ts:.1f} s), scaled by atoms ({N}/{sb.n})"}
+
+    if rank == 0:
+        print(json.dumps({
+            "metric": "ANKH-FMM energy evals/s", "value": value, "unit": "evals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": box.name + "_fmm_energy", "n_atoms": N, "box_A": round(box.box, 4),
+                       "n_cells": n, "depth": depth, "L": L, "xi": 0.01,
+                       "precision": "mixed_2xfp16_m2l", "l2": "flushed: 256 MiB write between timed steps",
+                       "parallelism": f"replicas{world}"},
+            "matoms_per_s": value * N / 1e6, "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+            "precompute_s": t_pre, "accuracy": acc, "clocks": clk, "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": world * args.e2e_steps / t_e2e, "unit": "evals/s",
+                    "h2d_bytes_per_step": 4 * N * (3 + 1 + 3 + 6), "d2h_bytes_per_step": 9 * 8},
+            "gpu_launches": (13 + depth) * args.steps}), flush=True)
+    model.close()
+
+
 def run_induce(args, rank, world, dev, api, synth, dist, cfg):
     """Induced dipoles of the workload (point polarizability 0.005 A^3 per
     atom: positive definite down to 0.22 A separations): one step = one full
@@ -365,6 +484,8 @@ def main():
     ap.add_argument("--plain", action="store_true", help="plain FP32 adjacent-leaf correction")
     ap.add_argument("--induce", action="store_true",
                     help="time induced-dipole solves (conjugate gradients on the ANKH field) instead")
+    ap.add_argument("--fmm", action="store_true",
+                    help="time ANKH-FMM energy evaluations (Alg. 3) instead")
     ap.add_argument("--nonperiodic", action="store_true",
                     help="no periodic images (bare kernel, zero-padded far field, Sec. 5.2)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -401,6 +522,9 @@ def main():
         return
     if args.induce:
         run_induce(args, rank, world, dev, api, synth, dist, cfg)
+        return
+    if args.fmm:
+        run_fmm(args, rank, world, dev, api, synth, dist, cfg)
         return
     box = synth.config_box(cfg) if rank == 0 else synth.water_box(
         synth.CONFIGS[cfg]["n_waters"], synth.SEED_BASE + cfg + 1000 * rank, multipoles=True,

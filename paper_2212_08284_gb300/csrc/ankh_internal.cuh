@@ -59,7 +59,7 @@ struct FmmLevel {
     const float *M;   // [(2m)^3][ldm] expansions of the level, natural cell order
     int m;            // parent cells per axis (2^(e-1)); the level has 2m cells per axis
     int S, R, tiles;  // z-row of m targets padded to S = max(16, m); R = 128 / S z-rows per tile; tiles per class
-    int rowstride;    // S + 2 rows per z-row of the split operand (one-cell z halo)
+    int rowstride;    // S + 2 rows per z-row block of the split operand (one-cell z halo)
     int rowbase;      // first row of the level in the split operand
     int acol;         // first column of the level in the operator table
     int eC;           // C_e(d) scaled by 2^eC before the fp16 split
@@ -76,7 +76,7 @@ struct FmmPlan {
     int64_t brows;          // rows of the split operand (all levels)
     uint32_t tmem_cols;
     float *d_Mlev[kFmmMaxLevels];   // levels 0 .. E-1 (level E is Handle::d_M)
-    __half *d_Bhi, *d_Blo;  // [brows][ldk] parity-major split expansions with a one-cell z halo
+    __half *d_Bhi, *d_Blo;  // [brows][ldk] parity-major split expansions, one-cell y and z halos
     __half *d_Ahi, *d_Alo;  // [slices*128][E * 343 * ldk] split M2L operators C_e(d), d in [-3,3]^3
     int4 *d_items;          // work items (level | class << 4 | slice << 8, tile, first offset, offsets)
     int *d_tab;             // interaction offsets per class (block | class' << 9 | (D + 1) << 12..16)
@@ -85,6 +85,7 @@ struct FmmPlan {
     FmmLevels lev;
     FmmLevel *d_lev;        // device copy of lev.lv
     CUtensorMap mAhi, mAlo, mBhi, mBlo;
+    CUtensorMap mB3hi[4], mB3lo[4];   // 3-D maps of the levels with m >= 8 (slot e - 4)
 };
 
 struct Handle {
@@ -174,6 +175,8 @@ cudaError_t precompute_kernel_spectrum(Handle &H, double *D0_out, std::string &e
 bool tc_prepare(Handle &H, std::string &err);
 bool encode_2d(CUtensorMap *map, void *ptr, uint64_t inner, uint64_t outer, uint32_t box_inner, uint32_t box_outer,
                std::string &err);   // 2-D fp16 tensor map, 128-byte swizzle
+bool encode_3d(CUtensorMap *map, void *ptr, uint64_t inner, uint64_t mid, uint64_t outer, uint32_t box_mid,
+               uint32_t box_outer, std::string &err);   // 3-D fp16 tensor map, boxes {64, box_mid, box_outer}
 // ANKH-FMM (fmm.cu)
 int fmm_prepare(Handle &H, double xi, bool include_rec, std::string &err);
 void fmm_free(Handle &H);

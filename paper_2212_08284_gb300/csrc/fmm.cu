@@ -24,8 +24,10 @@
 //   With the cells of a level stored parity-major (class p' = cell mod 2,
 // parent coordinates X = cell div 2), the source t + d of a target of class p
 // lies in class p' = (p + d) mod 2 at parent offset D = (p + d - p') / 2 in
-// {-1, 0, 1}^3, so for a z-row of targets the sources of one offset are one
-// contiguous run of rows of class p' (stored with a one-cell z halo).  The
+// {-1, 0, 1}^3.  Each class is stored as X planes of m + 2 z-row blocks (a
+// one-cell y halo) of S + 2 rows (a one-cell z halo), so the sources of one
+// offset for a tile of R z-rows of one plane are one 3-D box of R blocks of S
+// rows (one TMA copy for the levels with m >= 8).  The
 // contraction then runs on the tensor cores like the adjacent-leaf correction
 // (k_corr_tc.cu): one persistent launch over work items (level, class, tile of
 // R z-rows of S cells, 128-row slice of the target nodes) of all levels; the
@@ -67,6 +69,10 @@ __host__ __device__ inline int blk_of(int dx, int dy, int dz) { return ((dx + 3)
 
 struct M2MTab {
     float v[2][8][8];
+};
+
+struct B3Maps {
+    CUtensorMap hi[4], lo[4];   // levels e = 4 .. 7 (m >= 8)
 };
 
 // ---------------------------------------------------------------------------
@@ -130,10 +136,11 @@ k_m2m(const float *__restrict__ Mc, float *__restrict__ Mp, int ne, int ldm, con
 }
 
 // ---------------------------------------------------------------------------
-// Step 2 operands.  B: every level's expansions, parity-major, with a one-cell
-// z halo: row (class, z-row X m + Y, j) holds the cell (2X + px, 2Y + py,
-// 2Z + pz), Z = (j - 1) mod m, scaled by 2^eM(level) and split into fp16
-// hi + lo.  One thread per 8 nodes of a row; the padding rows j > m + 1 stay zero.
+// Step 2 operands.  B: every level's expansions, parity-major, with one-cell
+// y and z halos: row (class, X, Yh, j) of a level holds the cell
+// (2X + px, 2Y + py, 2Z + pz), Y = (Yh - 1) mod m, Z = (j - 1) mod m, scaled
+// by 2^eM(level) and split into fp16 hi + lo.  One thread per 8 nodes of a
+// row; the padding rows j > m + 1 stay zero.
 
 __global__ void __launch_bounds__(256)
 k_split_fmm(const __grid_constant__ FmmLevels lv, int E, int ldm, int ldk, int64_t rows,
@@ -150,9 +157,11 @@ k_split_fmm(const __grid_constant__ FmmLevels lv, int E, int ldm, int ldk, int64
     const int m = L.m, rr = r - L.rowbase;
     const int j = rr % L.rowstride, q = rr / L.rowstride;
     if (j > m + 1) return;
-    const int zr = q % (m * m), cls = q / (m * m);
+    const int Yh = q % (m + 2), q2 = q / (m + 2);
+    const int X = q2 % m, cls = q2 / m;
+    const int Y = Yh == 0 ? m - 1 : (Yh == m + 1 ? 0 : Yh - 1);
     const int Z = j == 0 ? m - 1 : (j == m + 1 ? 0 : j - 1);
-    const int X = zr / m, Y = zr % m, ne = 2 * m;
+    const int ne = 2 * m;
     const int64_t cell = ((int64_t)(2 * X + (cls >> 2)) * ne + 2 * Y + ((cls >> 1) & 1)) * ne + 2 * Z + (cls & 1);
     const float scale = ldexpf(1.f, split_exponent_dev(__uint_as_float(mmax[e])));
     float v[8];
@@ -229,7 +238,7 @@ k_pre_m2l(int E, int L, int ldk, int64_t arows, double box, double xi, const __g
 __global__ void __launch_bounds__(tcg::kThreads, 1)
 k_m2l_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
          const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo,
-         const FmmLevel *__restrict__ lvt, int ldm, int ldk, const int4 *__restrict__ items, int nitems,
+         const __grid_constant__ B3Maps b3, const FmmLevel *__restrict__ lvt, int ldm, int ldk, const int4 *__restrict__ items, int nitems,
          const int *__restrict__ tab, const unsigned *__restrict__ mmax, uint32_t tmem_cols,
          double *__restrict__ part, int *__restrict__ errflag)
 {
@@ -284,7 +293,8 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUte
         bool stop = false;
         for (int j = 0; j < nmine && !stop; ++j) {
             const int4 item = __ldg(&items[blockIdx.x + j * gridDim.x]);
-            const FmmLevel *L = lvt + (item.x & 15);
+            const int lev = item.x & 15;
+            const FmmLevel *L = lvt + lev;
             const int slice = item.x >> 8, m = L->m, nrow = m * m;
             const int R = L->R, S = L->S, rowbase = L->rowbase, rowstride = L->rowstride, acol = L->acol;
             const int nst = item.w * kch;
@@ -306,16 +316,26 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUte
                 mbar_expect_tx(&full[s], stage);
                 tma_2d(st, &tmAhi, &full[s], acol + blk * ldk + kc * kKc, slice * kRows);
                 tma_2d(st + kABytes, &tmAlo, &full[s], acol + blk * ldk + kc * kKc, slice * kRows);
-                for (int r = 0; r < R; ++r) {
-                    int zrow = item.y * R + r;
-                    if (zrow >= nrow) zrow = nrow - 1;
-                    const int cx = zrow / m, cy = zrow % m;
-                    const int ncx = (cx + Dx + m) % m, ncy = (cy + Dy + m) % m;
-                    const int brow = rowbase + (sc * nrow + ncx * m + ncy) * rowstride + 1 + Dz;
-                    for (int qb = 0; qb < S; qb += kBoxRows) {
-                        const size_t so = ((size_t)r * S + qb) * kRowBytes;
-                        tma_2d(st + 2 * kABytes + so, &tmBhi, &full[s], kc * kKc, brow + qb);
-                        tma_2d(st + 2 * kABytes + bbytes + so, &tmBlo, &full[s], kc * kKc, brow + qb);
+                if (m >= 8) {
+                    // R divides m: the tile's z-rows lie in one X plane, and the
+                    // sources are R consecutive y-halo blocks of class sc
+                    const int zrow0 = item.y * R, cx = zrow0 / m, cy0 = zrow0 - cx * m;
+                    const int ncx = (cx + Dx + m) % m;
+                    const int blk3 = (sc * m + ncx) * (m + 2) + cy0 + Dy + 1;
+                    tma_3d(st + 2 * kABytes, &b3.hi[lev - 4], &full[s], kc * kKc, 1 + Dz, blk3);
+                    tma_3d(st + 2 * kABytes + bbytes, &b3.lo[lev - 4], &full[s], kc * kKc, 1 + Dz, blk3);
+                } else {
+                    for (int r = 0; r < R; ++r) {
+                        int zrow = item.y * R + r;
+                        if (zrow >= nrow) zrow = nrow - 1;
+                        const int cx = zrow / m, cy = zrow % m;
+                        const int ncx = (cx + Dx + m) % m, ncy = (cy + Dy + m) % m;
+                        const int brow = rowbase + ((sc * m + ncx) * (m + 2) + ncy + 1) * rowstride + 1 + Dz;
+                        for (int qb = 0; qb < S; qb += kBoxRows) {
+                            const size_t so = ((size_t)r * S + qb) * kRowBytes;
+                            tma_2d(st + 2 * kABytes + so, &tmBhi, &full[s], kc * kKc, brow + qb);
+                            tma_2d(st + 2 * kABytes + bbytes + so, &tmBlo, &full[s], kc * kKc, brow + qb);
+                        }
                     }
                 }
                 *issued = gi + 1;
@@ -678,7 +698,7 @@ int fmm_prepare(Handle &H, double xi, bool include_rec, std::string &err)
         lv.tiles = (lv.m * lv.m + lv.R - 1) / lv.R;
         lv.rowstride = lv.S + 2;
         lv.rowbase = rowbase;
-        rowbase += 8 * lv.m * lv.m * lv.rowstride;
+        rowbase += 8 * lv.m * (lv.m + 2) * lv.rowstride;
         lv.acol = (e - 1) * kBlk * F.ldk;
         // largest |C_e|: the nearest node pair of an offset with |d|_inf = 2 is
         // h_e (2 - r_0) apart (o_k - o_l spans [-r_0, r_0])
@@ -764,6 +784,16 @@ int fmm_prepare(Handle &H, double xi, bool include_rec, std::string &err)
         !encode_2d(&F.mBhi, F.d_Bhi, (uint64_t)F.ldk, (uint64_t)F.brows, tcg::kKc, kBoxRows, err) ||
         !encode_2d(&F.mBlo, F.d_Blo, (uint64_t)F.ldk, (uint64_t)F.brows, tcg::kKc, kBoxRows, err))
         return ANKH_ECUDA;
+    for (int e = 4; e <= E; ++e) {
+        const FmmLevel &lv = F.lev.lv[e];
+        const uint64_t nblk = (uint64_t)8 * lv.m * (lv.m + 2);
+        const size_t off = (size_t)lv.rowbase * F.ldk;
+        if (!encode_3d(&F.mB3hi[e - 4], F.d_Bhi + off, (uint64_t)F.ldk, (uint64_t)lv.rowstride, nblk,
+                       (uint32_t)lv.S, (uint32_t)lv.R, err) ||
+            !encode_3d(&F.mB3lo[e - 4], F.d_Blo + off, (uint64_t)F.ldk, (uint64_t)lv.rowstride, nblk,
+                       (uint32_t)lv.S, (uint32_t)lv.R, err))
+            return ANKH_ECUDA;
+    }
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, H.device) != cudaSuccess || sms <= 0) {
         err = "cudaDeviceGetAttribute (SM count) failed";
@@ -809,7 +839,10 @@ static cudaError_t launch_m2l(Handle &H, cudaStream_t s)
                                                              F.d_Bhi, F.d_Blo);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_m2l_tc<<<F.grid, tcg::kThreads, m2l_smem_bytes(), s>>>(F.mAhi, F.mAlo, F.mBhi, F.mBlo, F.d_lev, H.g.ldm, F.ldk,
+    B3Maps b3;
+    std::memcpy(b3.hi, F.mB3hi, sizeof(b3.hi));
+    std::memcpy(b3.lo, F.mB3lo, sizeof(b3.lo));
+    k_m2l_tc<<<F.grid, tcg::kThreads, m2l_smem_bytes(), s>>>(F.mAhi, F.mAlo, F.mBhi, F.mBlo, b3, F.d_lev, H.g.ldm, F.ldk,
                                                              F.d_items, F.nitems, F.d_tab, H.d_mmax, F.tmem_cols,
                                                              H.d_part + H.part_off[kPartCorr], H.d_flag);
     return cudaGetLastError();

@@ -402,6 +402,36 @@ bool encode_2d(CUtensorMap *map, void *ptr, uint64_t inner, uint64_t outer, uint
     return true;
 }
 
+// 3-D fp16 tensor map {inner, mid, outer} with boxes {64, box_mid, box_outer} (128-byte swizzle)
+bool encode_3d(CUtensorMap *map, void *ptr, uint64_t inner, uint64_t mid, uint64_t outer, uint32_t box_mid,
+               uint32_t box_outer, std::string &err)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !p) {
+            err = "cuTensorMapEncodeTiled not available";
+            return false;
+        }
+        fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    cuuint64_t dims[3] = {inner, mid, outer};
+    cuuint64_t strides[2] = {inner * sizeof(__half), inner * mid * sizeof(__half)};
+    cuuint32_t box[3] = {(cuuint32_t)tcg::kKc, box_mid, box_outer};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, ptr, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        err = "cuTensorMapEncodeTiled (3-D) failed (" + std::to_string((int)r) + ")";
+        return false;
+    }
+    return true;
+}
+
 static size_t tc_smem_bytes(int N)
 {
     const size_t stage = 2 * (size_t)tcg::kABytes + 2 * (size_t)N * tcg::kRowBytes;
