@@ -86,31 +86,49 @@ k_m2m(const float *__restrict__ Mc, float *__restrict__ Mp, int ne, int ldm, con
 {
     constexpr int P = L * L * L;
     __shared__ float sA[8 * P], sB[8 * P];
+    __shared__ float sV[2][L][L];   // lane-dependent indices: shared memory, not the constant bank
     __shared__ float smax[4];
     const int parent = blockIdx.x;
     const int X = parent / (ne * ne), Y = (parent / ne) % ne, Z = parent % ne, nc = 2 * ne;
+    for (int i = threadIdx.x; i < 2 * L * L; i += blockDim.x) {
+        const int b = i / (L * L), k = (i / L) % L, l = i % L;
+        sV[b][k][l] = V.v[b][k][l];
+    }
     for (int i = threadIdx.x; i < 8 * P; i += blockDim.x) {
         const int b = i / P, l = i - b * P;
         const int child = ((2 * X + (b >> 2)) * nc + 2 * Y + ((b >> 1) & 1)) * nc + 2 * Z + (b & 1);
         sA[i] = Mc[(int64_t)child * ldm + l];
     }
     __syncthreads();
-    // z: sB[b][(l1 L + l2) L + k3] = sum_l3 V[bz][k3][l3] sA[b][(l1 L + l2) L + l3]
-    for (int i = threadIdx.x; i < 8 * P; i += blockDim.x) {
-        const int b = i / P, rem = i - b * P, k3 = rem % L, base = b * P + rem - k3;
-        float s = 0.f;
+    // z: sB[b][(l1 L + l2) L + k3] = sum_l3 V[bz][k3][l3] sA[b][(l1 L + l2) L + l3], one (b, l1, l2) row per thread
+    for (int r = threadIdx.x; r < 8 * L * L; r += blockDim.x) {
+        const int b = r / (L * L);
+        float x[L];
 #pragma unroll
-        for (int l = 0; l < L; ++l) s = fmaf(V.v[b & 1][k3][l], sA[base + l], s);
-        sB[i] = s;
+        for (int l = 0; l < L; ++l) x[l] = sA[r * L + l];
+#pragma unroll
+        for (int k = 0; k < L; ++k) {
+            float acc = 0.f;
+#pragma unroll
+            for (int l = 0; l < L; ++l) acc = fmaf(sV[b & 1][k][l], x[l], acc);
+            sB[r * L + k] = acc;
+        }
     }
     __syncthreads();
-    // y: sA[b][(l1 L + k2) L + k3] = sum_l2 V[by][k2][l2] sB[b][(l1 L + l2) L + k3]
-    for (int i = threadIdx.x; i < 8 * P; i += blockDim.x) {
-        const int b = i / P, rem = i - b * P, k3 = rem % L, k2 = (rem / L) % L, l1 = rem / (L * L);
-        float s = 0.f;
+    // y: sA[b][(l1 L + k2) L + k3] = sum_l2 V[by][k2][l2] sB[b][(l1 L + l2) L + k3], one (b, l1, k3) row per thread
+    for (int r = threadIdx.x; r < 8 * L * L; r += blockDim.x) {
+        const int b = r / (L * L), l1 = (r / L) % L, k3 = r % L;
+        const int base = b * P + l1 * L * L + k3;
+        float x[L];
 #pragma unroll
-        for (int l = 0; l < L; ++l) s = fmaf(V.v[(b >> 1) & 1][k2][l], sB[b * P + (l1 * L + l) * L + k3], s);
-        sA[i] = s;
+        for (int l = 0; l < L; ++l) x[l] = sB[base + l * L];
+#pragma unroll
+        for (int k = 0; k < L; ++k) {
+            float acc = 0.f;
+#pragma unroll
+            for (int l = 0; l < L; ++l) acc = fmaf(sV[(b >> 1) & 1][k][l], x[l], acc);
+            sA[base + k * L] = acc;
+        }
     }
     __syncthreads();
     // x: M_parent[(k1 L + k2) L + k3] = sum_b sum_l1 V[bx][k1][l1] sA[b][(l1 L + k2) L + k3]
@@ -121,7 +139,7 @@ k_m2m(const float *__restrict__ Mc, float *__restrict__ Mp, int ne, int ldm, con
 #pragma unroll
         for (int b = 0; b < 8; ++b)
 #pragma unroll
-            for (int l = 0; l < L; ++l) s = fmaf(V.v[b >> 2][k1][l], sA[b * P + l * L * L + k23], s);
+            for (int l = 0; l < L; ++l) s = fmaf(sV[b >> 2][k1][l], sA[b * P + l * L * L + k23], s);
         Mp[(int64_t)parent * ldm + k] = s;
         mx = fmaxf(mx, fabsf(s));
     }
