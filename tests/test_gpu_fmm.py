@@ -67,6 +67,50 @@ def test_terms_match_the_fp64_oracle(api, case):
         assert t["correction"] == pytest.approx(o["F_real"], rel=1e-5)
 
 
+@pytest.mark.parametrize("depth,L", [(2, 7), (3, 2)])
+def test_extreme_orders(api, depth, L):
+    """L = 7: 343 nodes in three 128-row slices (the last one partial) and six
+    K chunks; L = 2: the smallest order (8 nodes padded to 64)."""
+    b = synth.water_box(216, 11, box=18.64, multipoles=True)
+    o = fm.ankh_fmm_energy(b.x, b.q, b.mu, b.theta, b.box, depth, L)
+    m = api.Ankh(b.box, b.n, n_cells=2 ** depth, Lu=L, Lc=L, fmm=True)
+    E = m.energy(*to_dev(b))
+    t = m.terms()
+    assert E == pytest.approx(o["E"], rel=2e-6)
+    assert abs(t["correction"] - o["F_real"]) <= 1e-6 * abs(o["E"])
+    assert abs(t["far"] - (o["F_per"] + o["E_neut"])) <= 1e-6 * abs(o["E"])
+
+
+def test_single_charged_atom(api):
+    """One atom with a charge and a dipole (not neutral): only images
+    interact, through the M2L of the direct images and the root term; the
+    Q^2 constant of the lattice sum and the neutralising term are dropped
+    together on the GPU and kept (cancelling) in the oracle."""
+    import torch
+    x = np.array([[1.3, -2.2, 0.7]])
+    q, mu = np.array([0.8]), np.array([[0.1, -0.2, 0.3]])
+    o = fm.ankh_fmm_energy(x, q, mu, np.zeros((1, 6)), 12.0, 2, 5)
+    m = api.Ankh(12.0, 1, n_cells=4, Lu=5, Lc=5, fmm=True, max_order=1)
+    t32 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+    E = m.energy(t32(x), t32(q), t32(mu), None)
+    t = m.terms()
+    assert t["near"] == 0.0
+    assert t["correction"] == pytest.approx(o["F_real"], rel=2e-6)
+    assert t["far"] == pytest.approx(o["F_per"] + o["E_neut"], rel=2e-6)
+    assert E == pytest.approx(o["E"], abs=2e-6 * (abs(o["F_real"]) + abs(o["F_per"] + o["E_neut"])))
+
+
+def test_without_the_reciprocal_part(api):
+    """Paper-literal screening (E_rec(xi) neglected): the root operator then
+    carries only the band-limited difference of the second split."""
+    b = synth.water_box(216, 11, box=18.64, multipoles=True)
+    o = fm.ankh_fmm_energy(b.x, b.q, b.mu, b.theta, b.box, 3, 5, include_rec=False)
+    m = api.Ankh(b.box, b.n, n_cells=8, Lu=5, Lc=5, fmm=True, include_rec=False)
+    E = m.energy(*to_dev(b))
+    assert E == pytest.approx(o["E"], rel=2e-6)
+    assert abs(m.terms()["far"] - (o["F_per"] + o["E_neut"])) <= 1e-6 * abs(o["E"])
+
+
 def test_24000_atoms_depth4_matches_oracle_and_ewald(api):
     """The 24,000-atom water box (62.1 A) at depth 4 (16 leaves per axis, the
     level-4 z-rows of 8 cells padded to 16 columns): against the oracle at the
