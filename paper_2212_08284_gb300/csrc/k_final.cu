@@ -87,7 +87,7 @@ cudaError_t launch_reduce(Handle &H, cudaStream_t s)
     // ANKH-FMM: the far slot holds the root term itself and there is no k = 0 grid term
     const double invM2 = H.fmm.enabled ? 1.0 : 0.5 / (double)H.g.M;
     const double D0 = H.fmm.enabled ? 0.0 : H.D0;
-    k_reduce<<<1, 256, 0, s>>>(H.d_part, H.d_partoff, invM2, D0, H.d_flag, H.d_terms, 1, 1);
+    k_reduce<<<1, 1024, 0, s>>>(H.d_part, H.d_partoff, invM2, D0, H.d_flag, H.d_terms, 1, 1);
     return cudaGetLastError();
 }
 

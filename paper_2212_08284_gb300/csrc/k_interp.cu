@@ -208,31 +208,44 @@ __global__ void __launch_bounds__(128) k_fine(Geo g, const float *__restrict__ M
 {
     constexpr int Lm = LU - 1;
     const int gz = blockIdx.x * blockDim.x + threadIdx.x;
-    const int nf = g.nf, n = g.n;
+    const int nf = g.nf, n = g.n, ldm = g.ldm;
     if (gz >= g.ng) return;
     const int gg[3] = {(int)blockIdx.z, (int)blockIdx.y, gz};
-    int oc[3][2], on[3][2], lo[3], cnt[3];
+    // per axis: the (leaf, node) owners of the merged node -- the node itself
+    // and, on a face, the last node of the previous leaf -- as offsets into M
+    // (leaf strides n^2 ldm, n ldm, ldm; node strides LU^2, LU, 1)
+    int64_t offx[2];
+    int off[3][2];
+    bool has[3][2];
+    const int64_t cstride[3] = {(int64_t)n * n * ldm, (int64_t)n * ldm, (int64_t)ldm};
+    const int nstride[3] = {LU * LU, LU, 1};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const int q = gg[a] / Lm, r = gg[a] - q * Lm;
-        oc[a][0] = q; on[a][0] = r;
-        oc[a][1] = q == 0 ? n - 1 : q - 1;   // the node is also the last one of the previous leaf
-        on[a][1] = Lm;
-        lo[a] = 0;
-        cnt[a] = r == 0 ? 2 : 1;
+        const int qp = q == 0 ? n - 1 : q - 1;
+        const int64_t o0 = q * cstride[a] + r * nstride[a], o1 = qp * cstride[a] + Lm * nstride[a];
+        if (a == 0) {
+            offx[0] = o0;
+            offx[1] = o1;
+        } else {
+            off[a][0] = (int)o0;
+            off[a][1] = (int)o1;
+        }
+        has[a][0] = true;
+        has[a][1] = r == 0;
         if (NP) {
-            if (r == 0 && q == 0) cnt[a] = 1;             // first face: no previous leaf
-            if (q == n) { lo[a] = 1; cnt[a] = 2; }        // last face: previous leaf only
+            if (r == 0 && q == 0) has[a][1] = false;             // first face: no previous leaf
+            if (q == n) { has[a][0] = false; has[a][1] = true; } // last face: previous leaf only
         }
     }
     float s = 0.f;
-    for (int i = lo[0]; i < cnt[0]; ++i)
-        for (int j = lo[1]; j < cnt[1]; ++j)
-            for (int k = lo[2]; k < cnt[2]; ++k) {
-                const int cell = (oc[0][i] * n + oc[1][j]) * n + oc[2][k];
-                const int node = (on[0][i] * LU + on[1][j]) * LU + on[2][k];
-                s += __ldg(&M[(int64_t)cell * g.ldm + node]);
-            }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+                if (has[0][i] && has[1][j] && has[2][k]) s += __ldg(&M[offx[i] + off[1][j] + off[2][k]]);
     rho[((int64_t)gg[0] * nf + gg[1]) * nf + gz] = s;
 }
 
@@ -245,16 +258,18 @@ __global__ void __launch_bounds__(128) k_node_pot(Geo g, const float *__restrict
                                                   const float *__restrict__ psi, float *__restrict__ pi)
 {
     constexpr int P = LU * LU * LU, Lm = LU - 1;
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int cell = (int)(idx / P), node = (int)(idx - (int64_t)cell * P);
-    if (cell >= g.ncell) return;
+    // grid: x over the (leaf, node) pairs of one z-row of leaves, y = leaf y, z = leaf x
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = g.n, nf = g.nf;
+    const int cz = t / P, node = t - cz * P;
+    if (cz >= n) return;
+    const int cx = blockIdx.z, cy = blockIdx.y;
     const int a = node / (LU * LU), bb = (node / LU) % LU, c = node % LU;
-    int gx = (cell / (n * n)) * Lm + a, gy = ((cell / n) % n) * Lm + bb, gz = (cell % n) * Lm + c;
+    int gx = cx * Lm + a, gy = cy * Lm + bb, gz = cz * Lm + c;
     gx = gx >= nf ? gx - nf : gx;
     gy = gy >= nf ? gy - nf : gy;
     gz = gz >= nf ? gz - nf : gz;
-    const int64_t o = (int64_t)cell * g.ldm + node;
+    const int64_t o = ((int64_t)(cx * n + cy) * n + cz) * g.ldm + node;
     pi[o] = __ldg(&phi[((int64_t)gx * nf + gy) * nf + gz]) * invM - psi[o];
 }
 
@@ -449,8 +464,8 @@ static cudaError_t l2p_one(Handle &H, float *dEdx, float *dEdq, float *dEdmu, fl
 {
     constexpr int P = LU * LU * LU;
     const float invM = (float)(1.0 / (double)H.g.M);
-    const int64_t npot = (int64_t)H.g.ncell * P;
-    k_node_pot<LU><<<(unsigned)((npot + 127) / 128), 128, 0, s>>>(H.g, H.d_phi, invM, H.d_psi, H.d_pi);
+    const dim3 pgrid((unsigned)((H.g.n * P + 127) / 128), (unsigned)H.g.n, (unsigned)H.g.n);
+    k_node_pot<LU><<<pgrid, 128, 0, s>>>(H.g, H.d_phi, invM, H.d_psi, H.d_pi);
     const unsigned nb = (unsigned)((H.N + 127) / 128);
     if (H.g.Lc == LU)
         k_l2p<LU, true><<<nb, 128, 0, s>>>(H.g, H.d_scell, H.d_perm, H.d_A0, H.d_A1, H.d_A2, H.d_A3, H.d_W,
