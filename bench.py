@@ -317,7 +317,7 @@ def run_replicas(args, rank, world, dev, api, synth, dist=None):
                        "execution": "one CUDA graph per rank, one branch per box",
                        "parallelism": f"boxes split over {world} GPU(s) by LPT on atom counts"},
             "matoms_per_s": value / 64 * ntot_all / 1e6, "clocks": clk, "roofline": None, "cpu_baseline": None,
-            "e2e": None, "gpu_launches": None}), flush=True)
+            "e2e": None, "gpu_launches": 16 * len(boxes) * args.steps}), flush=True)
     bt.close()
 
 
@@ -507,7 +507,10 @@ def run_induce(args, rank, world, dev, api, synth, dist, cfg):
                        "parallelism": f"replicas{world}"},
             "iterations": statistics.mean(its), "ms_per_field_evaluation": t * 1e3 / evals,
             "E_pol": E_pol, "clocks": clk, "roofline": None, "cpu_baseline": None, "e2e": None,
-            "gpu_launches": None}), flush=True)
+            # per solve: 16 kernels per field evaluation (iterations + 2 of them),
+            # 3 vector kernels per iteration, 3 outside the loop
+            "gpu_launches": int(round(args.steps * (16 * (statistics.mean(its) + 2) + 3 * statistics.mean(its) + 3)))}),
+              flush=True)
     model.close()
 
 
