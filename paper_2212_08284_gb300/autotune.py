@@ -6,7 +6,8 @@ adjacent-leaf correction, the merged FFT grid and the P2M/L2P node work like
 h^-3, and the near-field kernel's lane use depends on the atoms per leaf.
 The autotuner measures one full energy + gradient evaluation on the device
 (CUDA events around the library call) for candidate n around a 4.0 A leaf
-edge and returns the fastest.  Results are cached per (box, N, orders,
+edge, extends the window while the fastest count sits at its edge, and
+returns the fastest.  Results are cached per (box, N, orders,
 precision) for the life of the process.
 """
 from __future__ import annotations
@@ -37,12 +38,14 @@ def autotune_n(box: float, x, q, mu=None, theta=None, Lu: int = 5, Lc: int = 0, 
            "dEdmu": torch.empty((n_atoms, 3), device=dev), "dEdtheta": torch.empty((n_atoms, 6), device=dev)}
     table = {}
     stream = torch.cuda.current_stream()
-    for n in (cands or candidates(box)):
+
+    def measure(n):
         try:
             m = api.Ankh(box, n_atoms, n_cells=n, Lu=Lu, Lc=Lc, mixed=mixed, max_order=max_order,
                          nonperiodic=nonperiodic)
         except api.AnkhError:
-            continue
+            table[n] = math.inf          # not creatable (grid too large): never chosen
+            return
         for _ in range(warm):
             api.ankh_energy_forces(m.h, x, q, mu, theta, sync=False, stream=stream, **out)
         e0 = torch.cuda.Event(enable_timing=True)
@@ -54,6 +57,26 @@ def autotune_n(box: float, x, q, mu=None, theta=None, Lu: int = 5, Lc: int = 0, 
         e1.synchronize()
         table[n] = e0.elapsed_time(e1) / reps
         m.close()
+
+    for n in (cands or candidates(box)):
+        measure(n)
+    if cands is None:
+        # while the fastest count sits at an edge of the window, extend the
+        # window past that edge (two counts at a time, at most 12 more)
+        for _ in range(6):
+            done = {k: v for k, v in table.items() if math.isfinite(v)}
+            if not done:
+                break
+            best = min(done, key=done.get)
+            if best == max(table):
+                ext = [best + 1, best + 2]
+            elif best == min(table) and best > 3:
+                ext = [k for k in (best - 1, best - 2) if k >= 3]
+            else:
+                break
+            for n in ext:
+                measure(n)
+    table = {k: v for k, v in table.items() if math.isfinite(v)}
     if not table:
         raise RuntimeError("no candidate leaf count could be created")
     best = min(table, key=table.get)
