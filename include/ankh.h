@@ -1,8 +1,10 @@
 /*
- * ankh.h -- C ABI of the GB300 implementation of ANKH-FFT: the periodic
+ * ankh.h -- C ABI of the GB300 implementation of ANKH: the periodic
  * point-multipole Coulomb energy of the paper's Eq. 1 (charges, dipoles,
  * quadrupoles on the lattice 2 r_B Z^3), evaluated by the interpolated-Ewald
- * split of Sec. 3-4 (Alg. 5), and its exact gradient.
+ * split of Sec. 3-4 (ANKH-FFT, Alg. 5) and its exact gradient; the energy by
+ * ANKH-FMM (Alg. 3, flag ANKH_FMM); the non-periodic energy of Sec. 5.2
+ * (flag ANKH_NONPERIODIC); induced dipoles on the same field (ankh_induce).
  *
  * Units: positions in Angstrom, charges in e, dipoles in e*A, quadrupoles in
  * e*A^2, energies in e^2/A (no Coulomb constant, as in Eq. 1).
