@@ -125,6 +125,34 @@ def test_24000_atoms_depth4_matches_oracle_and_ewald(api):
     assert abs(E - ref) <= abs(o["E"] - ref) + 2e-6 * abs(ref)
 
 
+def test_deepest_tree_charges_against_ewald(api):
+    """Depth 7 (128 leaves per axis; the level-7 copies are 3-D boxes of two
+    z-row blocks of 64 rows) on the 600-water box with charges only, against
+    Ewald.  With charges alone the method's error does not grow with the
+    depth (measured 1.8e-5 to 2.8e-5 at depths 2-7); with multipoles it does,
+    once the leaves are much smaller than the molecules (the FP64 oracle
+    shows the same), so multipoles are checked at depths 2-4 above."""
+    from oracle import ewald as ew
+    b = synth.water_box(600, 7, box=18.0, multipoles=False)
+    ref = ew.ewald(b.x, ew.pack_multipoles(b.q), b.box, grad=False)["E"]
+    import torch
+    m = api.Ankh(b.box, b.n, n_cells=128, Lu=5, Lc=5, fmm=True, max_order=0)
+    t32 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+    E = m.energy(t32(b.x), t32(b.q), None, None)
+    assert E == pytest.approx(ref, rel=1e-4)
+
+
+def test_charges_only_handle(api):
+    """max_order = 0 (no dipole or quadrupole arrays) against the oracle."""
+    import torch
+    b = synth.water_box(600, 7, box=18.0, multipoles=False)
+    o = fm.ankh_fmm_energy(b.x, b.q, None, None, b.box, 3, 5)
+    m = api.Ankh(b.box, b.n, n_cells=8, Lu=5, Lc=5, fmm=True, max_order=0)
+    t32 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+    E = m.energy(t32(b.x), t32(b.q), None, None)
+    assert E == pytest.approx(o["E"], rel=2e-6)
+
+
 def test_one_million_atoms_against_ewald(api):
     """The 1,008,000-atom box at the benchmarked tree (n = 64, L = 5): the FP64
     Ewald energy within the method's error at this leaf size (the oracle at the
