@@ -306,57 +306,67 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUte
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 4 && lane == 0) {
-        // TMA producer
+        // TMA producer.  A single thread issues every copy, so its per-stage
+        // integer work sits on the critical path: the stage loop is nested over
+        // (offset, K chunk) without divisions, the per-item leaf coordinates are
+        // hoisted, and neighbours wrap by compare (m is a power of two).
         int gi = 0;
         bool stop = false;
         for (int j = 0; j < nmine && !stop; ++j) {
             const int4 item = __ldg(&items[blockIdx.x + j * gridDim.x]);
             const int lev = item.x & 15;
             const FmmLevel *L = lvt + lev;
-            const int slice = item.x >> 8, m = L->m, nrow = m * m;
+            const int slice = item.x >> 8, m = L->m, nrow = m * m, lgm = __ffs(m) - 1;
             const int R = L->R, S = L->S, rowbase = L->rowbase, rowstride = L->rowstride, acol = L->acol;
-            const int nst = item.w * kch;
-            for (int it = 0; it < nst; ++it, ++gi) {
-                const int s = gi % kStages, k = gi / kStages;
-                if (gi >= kStages && !mbar_wait(&empty[s], (uint32_t)((k - 1) & 1), kBudget)) {
-                    *abort_flag = 1;
-                    stop = true;
-                    break;
-                }
-                if (*abort_flag) {
-                    stop = true;
-                    break;
-                }
-                const int ent = __ldg(&tab[item.z + it / kch]), kc = it % kch;
+            const int zrow0 = item.y * R, cx0 = zrow0 >> lgm, cy0 = zrow0 & (m - 1);
+            for (int oi = 0; oi < item.w && !stop; ++oi) {
+                const int ent = __ldg(&tab[item.z + oi]);
                 const int blk = ent & 511, sc = (ent >> 9) & 7;
                 const int Dx = ((ent >> 12) & 3) - 1, Dy = ((ent >> 14) & 3) - 1, Dz = ((ent >> 16) & 3) - 1;
-                unsigned char *st = smem + (size_t)s * stage;
-                mbar_expect_tx(&full[s], stage);
-                tma_2d(st, &tmAhi, &full[s], acol + blk * ldk + kc * kKc, slice * kRows);
-                tma_2d(st + kABytes, &tmAlo, &full[s], acol + blk * ldk + kc * kKc, slice * kRows);
-                if (m >= 8) {
-                    // R divides m: the tile's z-rows lie in one X plane, and the
-                    // sources are R consecutive y-halo blocks of class sc
-                    const int zrow0 = item.y * R, cx = zrow0 / m, cy0 = zrow0 - cx * m;
-                    const int ncx = (cx + Dx + m) % m;
-                    const int blk3 = (sc * m + ncx) * (m + 2) + cy0 + Dy + 1;
-                    tma_3d(st + 2 * kABytes, &b3.hi[lev - 4], &full[s], kc * kKc, 1 + Dz, blk3);
-                    tma_3d(st + 2 * kABytes + bbytes, &b3.lo[lev - 4], &full[s], kc * kKc, 1 + Dz, blk3);
-                } else {
-                    for (int r = 0; r < R; ++r) {
-                        int zrow = item.y * R + r;
-                        if (zrow >= nrow) zrow = nrow - 1;
-                        const int cx = zrow / m, cy = zrow % m;
-                        const int ncx = (cx + Dx + m) % m, ncy = (cy + Dy + m) % m;
-                        const int brow = rowbase + ((sc * m + ncx) * (m + 2) + ncy + 1) * rowstride + 1 + Dz;
-                        for (int qb = 0; qb < S; qb += kBoxRows) {
-                            const size_t so = ((size_t)r * S + qb) * kRowBytes;
-                            tma_2d(st + 2 * kABytes + so, &tmBhi, &full[s], kc * kKc, brow + qb);
-                            tma_2d(st + 2 * kABytes + bbytes + so, &tmBlo, &full[s], kc * kKc, brow + qb);
+                int ncx0 = cx0 + Dx;
+                ncx0 += ncx0 < 0 ? m : 0;
+                ncx0 -= ncx0 >= m ? m : 0;
+                const int blk3 = ((sc << lgm) + ncx0) * (m + 2) + cy0 + Dy + 1;
+                const int acol_d = acol + blk * ldk;
+                for (int kc = 0; kc < kch; ++kc, ++gi) {
+                    const int s = gi % kStages, k = gi / kStages;
+                    if (gi >= kStages && !mbar_wait(&empty[s], (uint32_t)((k - 1) & 1), kBudget)) {
+                        *abort_flag = 1;
+                        stop = true;
+                        break;
+                    }
+                    if (*abort_flag) {
+                        stop = true;
+                        break;
+                    }
+                    unsigned char *st = smem + (size_t)s * stage;
+                    mbar_expect_tx(&full[s], stage);
+                    tma_2d(st, &tmAhi, &full[s], acol_d + kc * kKc, slice * kRows);
+                    tma_2d(st + kABytes, &tmAlo, &full[s], acol_d + kc * kKc, slice * kRows);
+                    if (m >= 8) {
+                        // R divides m: the tile's z-rows lie in one X plane, and the
+                        // sources are R consecutive y-halo blocks of class sc
+                        tma_3d(st + 2 * kABytes, &b3.hi[lev - 4], &full[s], kc * kKc, 1 + Dz, blk3);
+                        tma_3d(st + 2 * kABytes + bbytes, &b3.lo[lev - 4], &full[s], kc * kKc, 1 + Dz, blk3);
+                    } else {
+                        for (int r = 0; r < R; ++r) {
+                            int zrow = zrow0 + r;
+                            if (zrow >= nrow) zrow = nrow - 1;
+                            int ncx = (zrow >> lgm) + Dx, ncy = (zrow & (m - 1)) + Dy;
+                            ncx += ncx < 0 ? m : 0;
+                            ncx -= ncx >= m ? m : 0;
+                            ncy += ncy < 0 ? m : 0;
+                            ncy -= ncy >= m ? m : 0;
+                            const int brow = rowbase + (((sc << lgm) + ncx) * (m + 2) + ncy + 1) * rowstride + 1 + Dz;
+                            for (int qb = 0; qb < S; qb += kBoxRows) {
+                                const size_t so = ((size_t)r * S + qb) * kRowBytes;
+                                tma_2d(st + 2 * kABytes + so, &tmBhi, &full[s], kc * kKc, brow + qb);
+                                tma_2d(st + 2 * kABytes + bbytes + so, &tmBlo, &full[s], kc * kKc, brow + qb);
+                            }
                         }
                     }
+                    *issued = gi + 1;
                 }
-                *issued = gi + 1;
             }
         }
     } else if (warp == 5 && lane == 0) {

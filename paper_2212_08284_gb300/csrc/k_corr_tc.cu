@@ -162,35 +162,64 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
     const int n = g.n, nrow = n * n;
 
     if (warp == 4 && lane == 0) {
-        // TMA producer
-        for (int gi = 0; gi < total; ++gi) {
-            const int s = gi % kStages, k = gi / kStages;
-            if (gi >= kStages && !mbar_wait(&empty[s], (uint32_t)((k - 1) & 1), kBudget)) {
-                *abort_flag = 1;
-                break;
-            }
-            if (*abort_flag) break;
-            const int w = (int)blockIdx.x + (gi / kIters) * (int)gridDim.x, it = gi % kIters;
+        // TMA producer.  A single thread issues every copy, so its per-stage
+        // integer work sits on the critical path: the stages are walked as
+        // nested loops (item, offset, K chunk) without divisions, the leaf
+        // coordinates of the item's z-rows are computed once per item, and
+        // neighbours wrap by compare.
+        int gi = 0;
+        bool stop = false;
+        for (int j = 0; j < nmine && !stop; ++j) {
+            const int w = (int)blockIdx.x + j * (int)gridDim.x;
             const int tile = w % ntiles, row0 = (w / ntiles) * kRows;
-            const int d = it / kch, kc = it % kch;
-            const int dx = d / 9 - 1, dy = (d / 3) % 3 - 1, dz = d % 3 - 1;
-            unsigned char *st = smem + (size_t)s * stage;
-            mbar_expect_tx(&full[s], stage);
-            tma_2d(st, &tmAhi, &full[s], d * ldk + kc * kKc, row0);
-            tma_2d(st + kABytes, &tmAlo, &full[s], d * ldk + kc * kKc, row0);
-            for (int r = 0; r < R; ++r) {
+            int cxr[8], cyr[8];
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
                 int zrow = tile * R + r;
                 if (zrow >= nrow) zrow = nrow - 1;
-                const int cx = zrow / n, cy = zrow % n;
-                const int ax = cx + dx, ay = cy + dy;
-                // a non-periodic box reads the all-zero z-row block n^2 beyond its faces
-                const bool outside = g.nonperiodic && (ax < 0 || ax >= n || ay < 0 || ay >= n);
-                const int ncx = (ax + n) % n, ncy = (ay + n) % n;
-                const int brow = (outside ? nrow : ncx * n + ncy) * rowstride + 1 + dz;
-                tma_2d(st + 2 * kABytes + (size_t)r * S * kRowBytes, &tmBhi, &full[s], kc * kKc, brow);
-                tma_2d(st + 2 * kABytes + bbytes + (size_t)r * S * kRowBytes, &tmBlo, &full[s], kc * kKc, brow);
+                cxr[r] = zrow / n;
+                cyr[r] = zrow - cxr[r] * n;
             }
-            *issued = gi + 1;
+            for (int d = 0; d < 27 && !stop; ++d) {
+                const int dx = d / 9 - 1, dy = (d / 3) % 3 - 1, dz = d % 3 - 1;
+                int brow[8];
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    int ax = cxr[r] + dx, ay = cyr[r] + dy;
+                    // a non-periodic box reads the all-zero z-row block n^2 beyond its faces
+                    const bool outside = g.nonperiodic && (ax < 0 || ax >= n || ay < 0 || ay >= n);
+                    ax += ax < 0 ? n : 0;
+                    ax -= ax >= n ? n : 0;
+                    ay += ay < 0 ? n : 0;
+                    ay -= ay >= n ? n : 0;
+                    brow[r] = (outside ? nrow : ax * n + ay) * rowstride + 1 + dz;
+                }
+                for (int kc = 0; kc < kch; ++kc, ++gi) {
+                    const int s = gi % kStages, k = gi / kStages;
+                    if (gi >= kStages && !mbar_wait(&empty[s], (uint32_t)((k - 1) & 1), kBudget)) {
+                        *abort_flag = 1;
+                        stop = true;
+                        break;
+                    }
+                    if (*abort_flag) {
+                        stop = true;
+                        break;
+                    }
+                    unsigned char *st = smem + (size_t)s * stage;
+                    mbar_expect_tx(&full[s], stage);
+                    tma_2d(st, &tmAhi, &full[s], d * ldk + kc * kKc, row0);
+                    tma_2d(st + kABytes, &tmAlo, &full[s], d * ldk + kc * kKc, row0);
+#pragma unroll
+                    for (int r = 0; r < 8; ++r) {
+                        if (r < R) {
+                            tma_2d(st + 2 * kABytes + (size_t)r * S * kRowBytes, &tmBhi, &full[s], kc * kKc, brow[r]);
+                            tma_2d(st + 2 * kABytes + bbytes + (size_t)r * S * kRowBytes, &tmBlo, &full[s], kc * kKc,
+                                   brow[r]);
+                        }
+                    }
+                    *issued = gi + 1;
+                }
+            }
         }
     } else if (warp == 5 && lane == 0) {
         // MMA issuer: large products of each stage into one of two TMEM buffers
