@@ -78,7 +78,8 @@ struct FmmPlan {
     float *d_Mlev[kFmmMaxLevels];   // levels 0 .. E-1 (level E is Handle::d_M)
     __half *d_Bhi, *d_Blo;  // [brows][ldk] parity-major split expansions, one-cell y and z halos
     __half *d_Ahi, *d_Alo;  // [slices*128][E * 343 * ldk] split M2L operators C_e(d), d in [-3,3]^3
-    int4 *d_items;          // work items (level | class << 4 | slice << 8, tile, first offset, offsets)
+    int4 *d_items;          // work items (level | class << 4 | slice << 8, tile, first offset, offsets), per CTA
+    int *d_ctaoff;          // [grid + 1] first item of each persistent CTA
     int *d_tab;             // interaction offsets per class (block | class' << 9 | (D + 1) << 12..16)
     double *d_K;            // [L^3][L^3] root operator of the images beyond the direct ones
     float V[2][8][8];       // M2M: V[b][k][l] = S_k((2b - 1 + r_l) / 2)

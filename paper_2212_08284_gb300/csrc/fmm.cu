@@ -256,7 +256,8 @@ k_pre_m2l(int E, int L, int ldk, int64_t arows, double box, double xi, const __g
 __global__ void __launch_bounds__(tcg::kThreads, 1)
 k_m2l_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
          const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo,
-         const __grid_constant__ B3Maps b3, const FmmLevel *__restrict__ lvt, int ldm, int ldk, const int4 *__restrict__ items, int nitems,
+         const __grid_constant__ B3Maps b3, const FmmLevel *__restrict__ lvt, int ldm, int ldk, const int4 *__restrict__ items,
+         const int *__restrict__ cta_off,
          const int *__restrict__ tab, const unsigned *__restrict__ mmax, uint32_t tmem_cols,
          double *__restrict__ part, int *__restrict__ errflag)
 {
@@ -279,7 +280,8 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUte
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int kch = ldk / kKc;
-    const int nmine = (int)blockIdx.x < nitems ? (nitems - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    // this CTA's work items: items[ibeg .. ibeg + nmine) (balanced on the host)
+    const int ibeg = __ldg(&cta_off[blockIdx.x]), nmine = __ldg(&cta_off[blockIdx.x + 1]) - ibeg;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&full[s], 1);
@@ -313,7 +315,7 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUte
         int gi = 0;
         bool stop = false;
         for (int j = 0; j < nmine && !stop; ++j) {
-            const int4 item = __ldg(&items[blockIdx.x + j * gridDim.x]);
+            const int4 item = __ldg(&items[ibeg + j]);
             const int lev = item.x & 15;
             const FmmLevel *L = lvt + lev;
             const int slice = item.x >> 8, m = L->m, nrow = m * m, lgm = __ffs(m) - 1;
@@ -376,7 +378,7 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUte
         int consumed = 0, gi = 0;
         bool stop = false;
         for (int j = 0; j < nmine && !stop; ++j) {
-            const int4 item = __ldg(&items[blockIdx.x + j * gridDim.x]);
+            const int4 item = __ldg(&items[ibeg + j]);
             const int nst = item.w * kch, par = j & 1;
             for (int it = 0; it < nst; ++it, ++gi) {
                 const int s = gi % kStages, k = gi / kStages, b = gi % kAccBufs, u = gi / kAccBufs;
@@ -430,7 +432,7 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUte
         const uint32_t lanebase = tmem + ((uint32_t)(warp * 32) << 16);
         int gi = 0;
         for (int j = 0; j < nmine && ok; ++j) {
-            const int4 item = __ldg(&items[blockIdx.x + j * gridDim.x]);
+            const int4 item = __ldg(&items[ibeg + j]);
             const int nst = item.w * kch;
             for (int it = 0; it < nst; ++it, ++gi) {
                 const int b = gi % kAccBufs, u = gi / kAccBufs;
@@ -675,7 +677,7 @@ void fmm_free(Handle &H)
     FmmPlan &F = H.fmm;
     for (int e = 0; e < kFmmMaxLevels; ++e)
         if (F.d_Mlev[e]) cudaFree(F.d_Mlev[e]);
-    void *ptrs[] = {F.d_Bhi, F.d_Blo, F.d_Ahi, F.d_Alo, F.d_items, F.d_tab, F.d_K, F.d_lev};
+    void *ptrs[] = {F.d_Bhi, F.d_Blo, F.d_Ahi, F.d_Alo, F.d_items, F.d_ctaoff, F.d_tab, F.d_K, F.d_lev};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     std::memset(&F, 0, sizeof(FmmPlan));
@@ -776,22 +778,65 @@ int fmm_prepare(Handle &H, double xi, bool include_rec, std::string &err)
     if (!cu(falloc(H, &F.d_lev, (size_t)kFmmMaxLevels), "cudaMalloc level table")) return ANKH_ENOMEM;
     if (!cu(cudaMemcpy(F.d_lev, F.lev.lv, sizeof(F.lev.lv), cudaMemcpyHostToDevice), "upload level table"))
         return ANKH_ECUDA;
-    // work items: leaves first; classes interleaved within a tile
-    std::vector<int4> items;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, H.device) != cudaSuccess || sms <= 0) {
+        err = "cudaDeviceGetAttribute (SM count) failed";
+        return ANKH_ECUDA;
+    }
+    // work items: (level, class, tile, slice) with a range of the class's
+    // offsets.  When there are few of them the offset ranges are split (the
+    // energy of an item is linear in its offsets, so the pieces add) to give
+    // about eight items per SM; then the items are dealt to the persistent
+    // CTAs longest first, each to the least-loaded CTA (ties: lowest index),
+    // and every CTA walks its own items in their original order.
+    std::vector<int4> base;
     for (int e = E; e >= 1; --e) {
         const FmmLevel &lv = F.lev.lv[e];
         for (int t = 0; t < lv.tiles; ++t)
             for (int cls = 0; cls < 8; ++cls)
                 for (int sl = 0; sl < F.slices; ++sl)
-                    items.push_back(make_int4(e | (cls << 4) | (sl << 8), t, cbeg[cls], ccnt[cls]));
+                    base.push_back(make_int4(e | (cls << 4) | (sl << 8), t, cbeg[cls], ccnt[cls]));
     }
+    const int split = std::max(1, std::min(8, (8 * sms + (int)base.size() - 1) / (int)base.size()));
+    std::vector<int4> items;
+    for (const int4 &it : base)
+        for (int c = 0; c < split; ++c) {
+            const int lo = it.z + (int)((int64_t)it.w * c / split), hi = it.z + (int)((int64_t)it.w * (c + 1) / split);
+            if (hi > lo) items.push_back(make_int4(it.x, it.y, lo, hi - lo));
+        }
     F.nitems = (int)items.size();
+    F.grid = std::min(F.nitems, sms);
+    std::vector<int> order(items.size()), owner(items.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return items[a].w > items[b].w; });
+    {
+        // cost of an item: its offsets plus ~2 offsets' worth for finishing it
+        std::vector<int64_t> load(F.grid, 0);
+        for (int i : order) {
+            int best = 0;
+            for (int c = 1; c < F.grid; ++c)
+                if (load[c] < load[best]) best = c;
+            owner[i] = best;
+            load[best] += (int64_t)items[i].w + 2;
+        }
+    }
+    std::vector<int> cta_off(F.grid + 1, 0);
+    for (size_t i = 0; i < items.size(); ++i) cta_off[owner[i] + 1]++;
+    for (int c = 0; c < F.grid; ++c) cta_off[c + 1] += cta_off[c];
+    std::vector<int4> dealt(items.size());
+    {
+        std::vector<int> fill(cta_off.begin(), cta_off.end() - 1);
+        for (size_t i = 0; i < items.size(); ++i) dealt[fill[owner[i]]++] = items[i];
+    }
     if (!cu(falloc(H, &F.d_tab, tab.size()), "cudaMalloc offsets") ||
-        !cu(falloc(H, &F.d_items, items.size()), "cudaMalloc items"))
+        !cu(falloc(H, &F.d_items, dealt.size()), "cudaMalloc items") ||
+        !cu(falloc(H, &F.d_ctaoff, cta_off.size()), "cudaMalloc item offsets"))
         return ANKH_ENOMEM;
     if (!cu(cudaMemcpy(F.d_tab, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice), "upload offsets") ||
-        !cu(cudaMemcpy(F.d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice),
-            "upload items"))
+        !cu(cudaMemcpy(F.d_items, dealt.data(), dealt.size() * sizeof(int4), cudaMemcpyHostToDevice),
+            "upload items") ||
+        !cu(cudaMemcpy(F.d_ctaoff, cta_off.data(), cta_off.size() * sizeof(int), cudaMemcpyHostToDevice),
+            "upload item offsets"))
         return ANKH_ECUDA;
     // M2M factors
     for (int b = 0; b < 2; ++b)
@@ -822,12 +867,6 @@ int fmm_prepare(Handle &H, double xi, bool include_rec, std::string &err)
                        (uint32_t)lv.S, (uint32_t)lv.R, err))
             return ANKH_ECUDA;
     }
-    int sms = 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, H.device) != cudaSuccess || sms <= 0) {
-        err = "cudaDeviceGetAttribute (SM count) failed";
-        return ANKH_ECUDA;
-    }
-    F.grid = std::min(F.nitems, sms);
     if (!cu(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m2l_smem_bytes()),
             "cudaFuncSetAttribute (shared memory)"))
         return ANKH_ECUDA;
@@ -871,7 +910,7 @@ static cudaError_t launch_m2l(Handle &H, cudaStream_t s)
     std::memcpy(b3.hi, F.mB3hi, sizeof(b3.hi));
     std::memcpy(b3.lo, F.mB3lo, sizeof(b3.lo));
     k_m2l_tc<<<F.grid, tcg::kThreads, m2l_smem_bytes(), s>>>(F.mAhi, F.mAlo, F.mBhi, F.mBlo, b3, F.d_lev, H.g.ldm, F.ldk,
-                                                             F.d_items, F.nitems, F.d_tab, H.d_mmax, F.tmem_cols,
+                                                             F.d_items, F.d_ctaoff, F.d_tab, H.d_mmax, F.tmem_cols,
                                                              H.d_part + H.part_off[kPartCorr], H.d_flag);
     return cudaGetLastError();
 }
