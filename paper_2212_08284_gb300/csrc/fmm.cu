@@ -248,12 +248,14 @@ k_pre_m2l(int E, int L, int ldk, int64_t arows, double box, double xi, const __g
 
 // ---------------------------------------------------------------------------
 // Step 2: persistent tcgen05 M2L over the work items of all levels (energy).
-// Roles as in k_corr_tc: warps 0-3 drain the tensor memory and finish items,
-// warp 4 issues the TMA copies, warp 5 the MMAs.  Every wait is bounded; on a
-// timeout the kernel raises bit 2 of the error flag, lets its own copies land,
-// frees its tensor memory and returns.
+// Warps 0-15 drain the tensor memory after every stage and finish the items
+// (warp w: TMEM lanes 32 (w mod 4), columns 32 (w div 4) .. + 32: sixteen
+// short drains in parallel keep the two large-product buffers turning over),
+// warp 16 issues the TMA copies, warp 17 the MMAs.  Every wait is bounded; on
+// a timeout the kernel raises bit 2 of the error flag, lets its own copies
+// land, frees its tensor memory and returns.
 
-__global__ void __launch_bounds__(tcg::kThreads, 1)
+__global__ void __launch_bounds__(576, 1)
 k_m2l_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
          const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo,
          const __grid_constant__ B3Maps b3, const FmmLevel *__restrict__ lvt, int ldm, int ldk, const int4 *__restrict__ items,
@@ -276,7 +278,7 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUte
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(small_free + 2);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     volatile int *issued = abort_flag + 1;
-    __shared__ double red[4];
+    __shared__ double red[16];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int kch = ldk / kKc;
@@ -289,14 +291,14 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUte
         }
         for (int b = 0; b < kAccBufs; ++b) {
             mbar_init(&acc_full[b], 1);
-            mbar_init(&acc_empty[b], 4);
+            mbar_init(&acc_empty[b], 16);
         }
-        for (int p = 0; p < 2; ++p) mbar_init(&small_free[p], 4);
+        for (int p = 0; p < 2; ++p) mbar_init(&small_free[p], 16);
         *abort_flag = 0;
         *issued = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 5) {
+    if (warp == 17) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
                      "r"(tmem_cols)
                      : "memory");
@@ -307,7 +309,7 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUte
     fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp == 4 && lane == 0) {
+    if (warp == 16 && lane == 0) {
         // TMA producer.  A single thread issues every copy, so its per-stage
         // integer work sits on the critical path: the stage loop is nested over
         // (offset, K chunk) without divisions, the per-item leaf coordinates are
@@ -371,7 +373,7 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUte
                 }
             }
         }
-    } else if (warp == 5 && lane == 0) {
+    } else if (warp == 17 && lane == 0) {
         // MMA issuer: large products into one of two buffers drained per stage,
         // small corrections into the item's accumulator (one per item parity)
         const uint32_t idesc = idesc_f16(kRows, N);
@@ -424,12 +426,14 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUte
         }
     }
     double e = 0.0;
-    if (warp < 4) {
-        float acc[N];
+    if (warp < 16) {
+        // warp w drains TMEM lanes 32 (w mod 4) and columns 32 (w div 4) .. + 32
+        const int qd = warp & 3, hf = warp >> 2;
+        float acc[32];
 #pragma unroll
-        for (int q = 0; q < N; ++q) acc[q] = 0.f;
+        for (int q = 0; q < 32; ++q) acc[q] = 0.f;
         bool ok = true;
-        const uint32_t lanebase = tmem + ((uint32_t)(warp * 32) << 16);
+        const uint32_t lanebase = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(hf * 32);
         int gi = 0;
         for (int j = 0; j < nmine && ok; ++j) {
             const int4 item = __ldg(&items[ibeg + j]);
@@ -441,15 +445,11 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUte
                 if (!ok) break;
                 fence_after();
                 const uint32_t ta = lanebase + (uint32_t)(b * N);
+                uint32_t v[32];
+                tmem_ld32_nowait(ta, v);
+                tmem_wait_ld();
 #pragma unroll
-                for (int c = 0; c < N / 32; c += 2) {
-                    uint32_t v[64];
-                    tmem_ld32_nowait(ta + (uint32_t)(c * 32), v);
-                    tmem_ld32_nowait(ta + (uint32_t)((c + 1) * 32), v + 32);
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int q = 0; q < 64; ++q) acc[c * 32 + q] += __uint_as_float(v[q]);
-                }
+                for (int q = 0; q < 32; ++q) acc[q] += __uint_as_float(v[q]);
                 fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&acc_empty[b]);
@@ -462,7 +462,7 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUte
             const float unscale = ldexpf(1.f, -(L->eC + split_exponent_dev(__uint_as_float(mmax[lev]))));
             const uint32_t ts = lanebase + (uint32_t)((kAccBufs + (j & 1)) * N);
 #pragma unroll
-            for (int c = 0; c < N / 32; ++c) {
+            for (int c = 0; c < 1; ++c) {
                 uint32_t v[32];
                 tmem_ld32_nowait(ts + (uint32_t)(c * 32), v);
                 tmem_wait_ld();
@@ -475,16 +475,16 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUte
                 tmem_st32(ts + (uint32_t)(c * 32), o);
             }
             tmem_wait_st();
-            const int node = slice * kRows + warp * 32 + lane;
+            const int node = slice * kRows + qd * 32 + lane;
             const int m = L->m, S = L->S, R = L->R, ne = 2 * m, nrow = m * m;
             const float *Ml = L->M;
             const int px = cls >> 2, py = (cls >> 1) & 1, pz = cls & 1;
             float pe0 = 0.f, pe1 = 0.f;
-            for (int c0 = 0; c0 < N; c0 += 8) {
+            for (int c0 = 0; c0 < 32; c0 += 8) {
                 float mv[8];
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
-                    const int col = c0 + q, slab = col / S, z = col - slab * S, zrow = item.y * R + slab;
+                    const int col = hf * 32 + c0 + q, slab = col / S, z = col - slab * S, zrow = item.y * R + slab;
                     mv[q] = 0.f;
                     if (node < ldm && z < m && zrow < nrow) {
                         const int X = zrow / m, Y = zrow - X * m;
@@ -514,10 +514,12 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUte
     fence_before();
     __syncthreads();
     if (threadIdx.x == 0) {
-        part[blockIdx.x] = red[0] + red[1] + red[2] + red[3];
+        double t = 0.0;
+        for (int w = 0; w < 16; ++w) t += red[w];
+        part[blockIdx.x] = t;
         if (*abort_flag) atomicOr(errflag, 2);
     }
-    if (warp == 5) {
+    if (warp == 17) {
         __syncwarp();
         fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
@@ -909,7 +911,7 @@ static cudaError_t launch_m2l(Handle &H, cudaStream_t s)
     B3Maps b3;
     std::memcpy(b3.hi, F.mB3hi, sizeof(b3.hi));
     std::memcpy(b3.lo, F.mB3lo, sizeof(b3.lo));
-    k_m2l_tc<<<F.grid, tcg::kThreads, m2l_smem_bytes(), s>>>(F.mAhi, F.mAlo, F.mBhi, F.mBlo, b3, F.d_lev, H.g.ldm, F.ldk,
+    k_m2l_tc<<<F.grid, 576, m2l_smem_bytes(), s>>>(F.mAhi, F.mAlo, F.mBhi, F.mBlo, b3, F.d_lev, H.g.ldm, F.ldk,
                                                              F.d_items, F.d_ctaoff, F.d_tab, H.d_mmax, F.tmem_cols,
                                                              H.d_part + H.part_off[kPartCorr], H.d_flag);
     return cudaGetLastError();

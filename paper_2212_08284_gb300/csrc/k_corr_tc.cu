@@ -104,8 +104,11 @@ k_split_f16(Geo g, int ldk, int rowstride, const float *__restrict__ M, const un
 // that item's small accumulator (which then holds psi) and finish it -- the
 // energy dot with M and the psi write, 8 columns per stage -- while the next
 // item's MMAs run; the small accumulator is then released for the item after.
+constexpr int kCorrEpiWarps = 16;                        // warp w: TMEM lanes 32 (w mod 4), columns 32 (w div 4)
+constexpr int kCorrThreads = (kCorrEpiWarps + 2) * 32;   // + TMA producer + MMA issuer
+
 template <bool FORCES>
-__global__ void __launch_bounds__(tcg::kThreads, 1)
+__global__ void __launch_bounds__(kCorrThreads, 1)
 k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
           const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo, Geo g, int S,
           int R, int rowstride, int ldk, int eC, const unsigned *__restrict__ mmax, int ntiles, int nwork,
@@ -127,7 +130,7 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(small_free + 2);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     volatile int *issued = abort_flag + 1;
-    __shared__ double red[4];
+    __shared__ double red[kCorrEpiWarps];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ldm = g.ldm;
@@ -142,14 +145,15 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
         }
         for (int b = 0; b < kAccBufs; ++b) {
             mbar_init(&acc_full[b], 1);
-            mbar_init(&acc_empty[b], 4);
+            mbar_init(&acc_empty[b], kCorrEpiWarps);
         }
-        for (int p = 0; p < 2; ++p) mbar_init(&small_free[p], 4);
+        for (int p = 0; p < 2; ++p) mbar_init(&small_free[p], kCorrEpiWarps);
         *abort_flag = 0;
         *issued = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 5) {
+    const int wprod = kCorrEpiWarps, wmma = kCorrEpiWarps + 1;
+    if (warp == wmma) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tcg::su32(tmem_slot)),
                      "r"(tmem_cols)
                      : "memory");
@@ -161,7 +165,7 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
     const uint32_t tmem = *tmem_slot;
     const int n = g.n, nrow = n * n;
 
-    if (warp == 4 && lane == 0) {
+    if (warp == wprod && lane == 0) {
         // TMA producer.  A single thread issues every copy, so its per-stage
         // integer work sits on the critical path: the stages are walked as
         // nested loops (item, offset, K chunk) without divisions, the leaf
@@ -221,7 +225,7 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
                 }
             }
         }
-    } else if (warp == 5 && lane == 0) {
+    } else if (warp == wmma && lane == 0) {
         // MMA issuer: large products of each stage into one of two TMEM buffers
         // (drained by the epilogue warps), small corrections into the item's
         // small accumulator
@@ -268,26 +272,30 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
         }
     }
     double e = 0.0;
-    if (warp < 4) {
-        float acc[kMaxN];
+    if (warp < kCorrEpiWarps) {
+        // sixteen epilogue warps: warp w owns TMEM lanes 32 (w mod 4) and the 32
+        // columns 32 (w div 4) .. (a group past N owns none but keeps the barriers)
+        const int qd = warp & 3, grp = warp >> 2, col0 = grp * 32;
+        const bool have = col0 < N;
+        float acc[32];
 #pragma unroll
-        for (int q = 0; q < kMaxN; ++q) acc[q] = 0.f;
+        for (int q = 0; q < 32; ++q) acc[q] = 0.f;
         bool ok = true;
-        const uint32_t lanebase = tmem + ((uint32_t)(warp * 32) << 16);
+        const uint32_t lanebase = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)col0;
         const float unscale = ldexpf(1.f, -(eC + split_exponent_dev(__uint_as_float(*mmax))));
         // the item whose small accumulator (= psi) is being finished, and the
-        // next column to finish
+        // next of this warp's columns to finish
         int pend = -1, pcol = 0;
         float pe0 = 0.f, pe1 = 0.f;   // FP32 partial dot of the pending item (two chains)
         auto finish_chunk = [&](int c0) {
-            // columns c0 .. c0+7 of item pend: psi from TMEM, M from global
+            // columns col0 + c0 .. + 7 of item pend: psi from TMEM, M from global
             const int w = (int)blockIdx.x + pend * (int)gridDim.x;
-            const int tile = w % ntiles, m = (w / ntiles) * kRows + warp * 32 + lane;
+            const int tile = w % ntiles, m = (w / ntiles) * kRows + qd * 32 + lane;
             float mv[8];
             int64_t ofs[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-                const int c = c0 + q, slab = c / S, z = c % S, zrow = tile * R + slab;
+                const int c = col0 + c0 + q, slab = c / S, z = c % S, zrow = tile * R + slab;
                 const bool valid = (m < ldm) && (c < N) && (z < n) && (zrow < nrow);
                 ofs[q] = valid ? ((int64_t)zrow * n + z) * ldm + m : -1;
                 mv[q] = valid ? __ldg(&M[ofs[q]]) : 0.f;
@@ -311,6 +319,7 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
             if (lane == 0) mbar_arrive(&small_free[pend & 1]);
             pend = -1;
         };
+        const int ncols = have ? 32 : 0;   // N is a multiple of 32 (tc_tile_shape)
         for (int gi = 0; gi < total; ++gi) {
             const int b = gi % kAccBufs, u = gi / kAccBufs;
             const int j = gi / kIters, it = gi % kIters;
@@ -318,65 +327,53 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
             ok = __all_sync(0xffffffffu, wok && !*abort_flag);
             if (!ok) break;
             fence_after();
-            const uint32_t ta = lanebase + (uint32_t)(b * N);
+            if (have) {
+                uint32_t v[32];
+                tmem_ld32_nowait(lanebase + (uint32_t)(b * N), v);
+                tmem_wait_ld();
 #pragma unroll
-            for (int c = 0; c < kMaxN / 32; c += 2) {
-                if (c * 32 < N) {
-                    uint32_t v[64];
-                    tmem_ld32_nowait(ta + (uint32_t)(c * 32), v);
-                    if ((c + 1) * 32 < N) tmem_ld32_nowait(ta + (uint32_t)((c + 1) * 32), v + 32);
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int q = 0; q < 32; ++q) acc[c * 32 + q] += __uint_as_float(v[q]);
-                    if ((c + 1) * 32 < N) {
-#pragma unroll
-                        for (int q = 0; q < 32; ++q) acc[(c + 1) * 32 + q] += __uint_as_float(v[32 + q]);
-                    }
-                }
+                for (int q = 0; q < 32; ++q) acc[q] += __uint_as_float(v[q]);
             }
             fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[b]);
             // finish 8 columns of the previous item while this one streams
             if (pend >= 0) {
-                finish_chunk(pcol);
+                if (pcol < ncols) finish_chunk(pcol);
                 pcol += 8;
-                if (pcol >= N) release_pending();
+                if (pcol >= ncols) release_pending();
             }
             if (it == kIters - 1) {
                 // item j complete (this arrival follows all of its MMAs): fold
                 // the drained large products into its small accumulator
-                while (pend >= 0) {              // (only if N / 8 > kIters)
-                    finish_chunk(pcol);
+                while (pend >= 0) {
+                    if (pcol < ncols) finish_chunk(pcol);
                     pcol += 8;
-                    if (pcol >= N) release_pending();
+                    if (pcol >= ncols) release_pending();
                 }
-                const uint32_t ts = lanebase + (uint32_t)((kAccBufs + (j & 1)) * N);
+                if (have) {
+                    const uint32_t ts = lanebase + (uint32_t)((kAccBufs + (j & 1)) * N);
+                    uint32_t v[32];
+                    tmem_ld32_nowait(ts, v);
+                    tmem_wait_ld();
+                    float o[32];
 #pragma unroll
-                for (int c = 0; c < kMaxN / 32; ++c) {
-                    if (c * 32 < N) {
-                        uint32_t v[32];
-                        tmem_ld32_nowait(ts + (uint32_t)(c * 32), v);
-                        tmem_wait_ld();
-                        float o[32];
-#pragma unroll
-                        for (int q = 0; q < 32; ++q) {
-                            o[q] = (acc[c * 32 + q] + __uint_as_float(v[q])) * unscale;
-                            acc[c * 32 + q] = 0.f;
-                        }
-                        tmem_st32(ts + (uint32_t)(c * 32), o);
+                    for (int q = 0; q < 32; ++q) {
+                        o[q] = (acc[q] + __uint_as_float(v[q])) * unscale;
+                        acc[q] = 0.f;
                     }
+                    tmem_st32(ts, o);
+                    tmem_wait_st();
                 }
-                tmem_wait_st();
                 pend = j;
                 pcol = 0;
             }
         }
         if (ok) {
             while (pend >= 0) {
-                finish_chunk(pcol);
+                if (pcol < ncols) finish_chunk(pcol);
                 pcol += 8;
-                if (pcol >= N) release_pending();
+                if (pcol >= ncols) release_pending();
             }
         } else {
             *abort_flag = 1;
@@ -388,10 +385,12 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
     fence_before();
     __syncthreads();
     if (threadIdx.x == 0) {
-        part[blockIdx.x] = -0.5 * (red[0] + red[1] + red[2] + red[3]);
+        double t = 0.0;
+        for (int w = 0; w < kCorrEpiWarps; ++w) t += red[w];
+        part[blockIdx.x] = -0.5 * t;
         if (*abort_flag) atomicOr(errflag, 2);
     }
-    if (warp == 5) {
+    if (warp == wmma) {
         __syncwarp();
         fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
@@ -467,10 +466,11 @@ static size_t tc_smem_bytes(int N)
     return (size_t)tcg::kStages * stage + 1024 + 256;
 }
 
-// Tile of R z-rows of S (>= n, multiple of 16) leaves, N = R S <= 128.
+// Tile of R z-rows of S (>= n, multiple of 32) leaves, N = R S <= 128: N is
+// then a multiple of 32, the column group of one epilogue warp.
 void tc_tile_shape(int n, int &S, int &R)
 {
-    S = ((n + 15) / 16) * 16;
+    S = ((n + 31) / 32) * 32;
     R = std::max(1, tcg::kMaxN / S);
 }
 
@@ -543,7 +543,7 @@ cudaError_t launch_corr_tc(Handle &H, bool forces, cudaStream_t s)
     double *part = H.d_part + H.part_off[kPartCorr];
     const int nwork = H.tc.tiles * H.tc.halves;
 #define ANKH_CORR_LAUNCH(F)                                                                                     \
-    k_corr_tc<F><<<H.tc.grid, tcg::kThreads, smem, s>>>(H.tc.mAhi, H.tc.mAlo, H.tc.mBhi, H.tc.mBlo, H.g, H.tc.S,  \
+    k_corr_tc<F><<<H.tc.grid, kCorrThreads, smem, s>>>(H.tc.mAhi, H.tc.mAlo, H.tc.mBhi, H.tc.mBlo, H.g, H.tc.S,  \
                                                         H.tc.R, H.tc.rowstride, H.tc.ldk, H.tc.eC, H.d_mmax,      \
                                                         H.tc.tiles, nwork, H.tc.tmem_cols, H.d_M, H.d_psi, part,  \
                                                         H.d_flag)

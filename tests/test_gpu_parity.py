@@ -287,7 +287,8 @@ def test_autograd_backward_is_the_adjoint(api):
 
 
 @pytest.mark.parametrize("boxname,n,Lu", [("w3000", 7, 5), ("w24000", 14, 5), ("w24000", 20, 5),
-                                           ("w24000", 36, 5), ("w24000", 14, 6), ("w3000", 8, 4)])
+                                           ("w24000", 36, 5), ("w24000", 14, 6), ("w3000", 8, 4),
+                                           ("w1m", 70, 5)])   # z-rows of 96: the last epilogue column group idle
 def test_tensor_core_correction_matches_fp32(api, boxname, n, Lu):
     """The tcgen05 2xFP16 correction reproduces the plain FP32 contraction:
     psi to 1e-5 of max|psi|, and the correction energy to 1e-6 of the total
@@ -295,8 +296,13 @@ def test_tensor_core_correction_matches_fp32(api, boxname, n, Lu):
     tensor core truncates while accumulating, so the bar is on the energy
     the correction enters, not on the correction alone, which can be a
     small difference of large terms).  Ragged tiles, z-rows padded to
-    16/32/48 leaves, 64/128/224 target-node rows."""
-    b = synth.small_box(1000, 31, box=31.1) if boxname == "w3000" else synth.config_box(2)
+    32/64/96 leaves, 64/128/224 target-node rows; n = 70 on the 1,008,000-atom
+    box (3.1 A leaves: the same bar on the 62 A box would put the leaves at
+    0.9 A, where the correction is ~80x the total energy)."""
+    if boxname == "w3000":
+        b = synth.small_box(1000, 31, box=31.1)
+    else:
+        b = synth.config_box(4 if boxname == "w1m" else 2)
     x, q, mu, th = to_dev(b)
     res = {}
     for mixed in (False, True):
