@@ -137,7 +137,6 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
     const int kch = ldk / kKc;            // K chunks per offset d
     const int kIters = 27 * kch;          // stages per work item
     const int nmine = blockIdx.x < nwork ? (nwork - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    const int total = nmine * kIters;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&full[s], 1);
@@ -230,21 +229,27 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
         // (drained by the epilogue warps), small corrections into the item's
         // small accumulator
         const uint32_t idesc = idesc_f16(kRows, N);
-        int consumed = 0;
-        for (int gi = 0; gi < total; ++gi) {
+        int consumed = 0, gi = 0;
+        bool stop = false;
+        for (int j = 0; j < nmine && !stop; ++j)
+        for (int it = 0; it < kIters; ++it, ++gi) {
+            // (item j, stage it) walked as nested loops: no divisions per stage
             const int s = gi % kStages, k = gi / kStages, b = gi % kAccBufs, u = gi / kAccBufs;
-            const int j = gi / kIters, it = gi % kIters, par = j & 1;
+            const int par = j & 1;
             if (it == 0 && j >= 2 &&
                 !mbar_wait(&small_free[par], (uint32_t)(((j >> 1) - 1) & 1), kBudget)) {
                 *abort_flag = 1;
+                stop = true;
                 break;
             }
             if (gi >= kAccBufs && !mbar_wait(&acc_empty[b], (uint32_t)((u - 1) & 1), kBudget)) {
                 *abort_flag = 1;
+                stop = true;
                 break;
             }
             if (!mbar_wait(&full[s], (uint32_t)(k & 1), kBudget)) {
                 *abort_flag = 1;
+                stop = true;
                 break;
             }
             consumed = gi + 1;
@@ -267,8 +272,8 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
             // release the epilogue and let every copy this CTA issued land
             for (int b = 0; b < kAccBufs; ++b) mma_commit(&acc_full[b]);
             const int nis = *issued;
-            for (int gi = consumed; gi < nis; ++gi)
-                mbar_wait(&full[gi % kStages], (uint32_t)((gi / kStages) & 1), kBudget);
+            for (int g2 = consumed; g2 < nis; ++g2)
+                mbar_wait(&full[g2 % kStages], (uint32_t)((g2 / kStages) & 1), kBudget);
         }
     }
     double e = 0.0;
@@ -320,9 +325,10 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
             pend = -1;
         };
         const int ncols = have ? 32 : 0;   // N is a multiple of 32 (tc_tile_shape)
-        for (int gi = 0; gi < total; ++gi) {
+        int gi = 0;
+        for (int j = 0; j < nmine && ok; ++j)
+        for (int it = 0; it < kIters; ++it, ++gi) {
             const int b = gi % kAccBufs, u = gi / kAccBufs;
-            const int j = gi / kIters, it = gi % kIters;
             bool wok = mbar_wait(&acc_full[b], (uint32_t)(u & 1), 2 * kBudget);
             ok = __all_sync(0xffffffffu, wok && !*abort_flag);
             if (!ok) break;
