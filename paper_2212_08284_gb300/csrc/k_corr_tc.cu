@@ -258,12 +258,15 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
             const uint32_t small = tmem + (uint32_t)((kAccBufs + par) * N);
             const uint32_t base = su32(smem + (size_t)s * stage);
             const uint32_t ahi = base, alo = base + kABytes, bhi = base + 2 * kABytes, blo = bhi + bbytes;
+            // descriptors built once per stage; a K step of 16 halves (32 bytes
+            // along the swizzled row) adds 2 to the encoded start address
+            const uint64_t dah = desc_sw128(ahi), dal = desc_sw128(alo), dbh = desc_sw128(bhi), dbl = desc_sw128(blo);
 #pragma unroll
             for (int k16 = 0; k16 < kKc / 16; ++k16) {
-                const uint32_t off = k16 * 32;   // 16 halves = 32 bytes along the swizzled row
-                mma_f16(big, desc_sw128(ahi + off), desc_sw128(bhi + off), idesc, k16 > 0 ? 1u : 0u);
-                mma_f16(small, desc_sw128(ahi + off), desc_sw128(blo + off), idesc, (it > 0 || k16 > 0) ? 1u : 0u);
-                mma_f16(small, desc_sw128(alo + off), desc_sw128(bhi + off), idesc, 1u);
+                const uint64_t o = 2u * k16;
+                mma_f16(big, dah + o, dbh + o, idesc, k16 > 0 ? 1u : 0u);
+                mma_f16(small, dah + o, dbl + o, idesc, (it > 0 || k16 > 0) ? 1u : 0u);
+                mma_f16(small, dal + o, dbh + o, idesc, 1u);
             }
             mma_commit(&empty[s]);
             mma_commit(&acc_full[b]);
