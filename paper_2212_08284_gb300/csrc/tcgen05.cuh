@@ -48,6 +48,7 @@ __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity)
 
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long budget)
 {
+    if (mbar_try(bar, parity)) return true;   // the common case: no clock read
     const long long t0 = clock64();
     while (!mbar_try(bar, parity))
         if (clock64() - t0 > budget) return false;
