@@ -314,7 +314,8 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUte
         // integer work sits on the critical path: the stage loop is nested over
         // (offset, K chunk) without divisions, the per-item leaf coordinates are
         // hoisted, and neighbours wrap by compare (m is a power of two).
-        int gi = 0;
+        int gi = 0, s = 0;
+        uint32_t ph = 0;
         bool stop = false;
         for (int j = 0; j < nmine && !stop; ++j) {
             const int4 item = __ldg(&items[ibeg + j]);
@@ -332,9 +333,9 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUte
                 ncx0 -= ncx0 >= m ? m : 0;
                 const int blk3 = ((sc << lgm) + ncx0) * (m + 2) + cy0 + Dy + 1;
                 const int acol_d = acol + blk * ldk;
-                for (int kc = 0; kc < kch; ++kc, ++gi) {
-                    const int s = gi % kStages, k = gi / kStages;
-                    if (gi >= kStages && !mbar_wait(&empty[s], (uint32_t)((k - 1) & 1), kBudget)) {
+                for (int kc = 0; kc < kch; ++kc, ++gi, s = (s + 1 == kStages ? 0 : s + 1), ph ^= (s == 0 ? 1u : 0u)) {
+                    // ring slot s = gi mod kStages, phase ph = (gi div kStages) mod 2
+                    if (gi >= kStages && !mbar_wait(&empty[s], ph ^ 1u, kBudget)) {
                         *abort_flag = 1;
                         stop = true;
                         break;
@@ -377,13 +378,15 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUte
         // MMA issuer: large products into one of two buffers drained per stage,
         // small corrections into the item's accumulator (one per item parity)
         const uint32_t idesc = idesc_f16(kRows, N);
-        int consumed = 0, gi = 0;
+        int consumed = 0, gi = 0, s = 0;
+        uint32_t ph = 0;
         bool stop = false;
         for (int j = 0; j < nmine && !stop; ++j) {
             const int4 item = __ldg(&items[ibeg + j]);
             const int nst = item.w * kch, par = j & 1;
-            for (int it = 0; it < nst; ++it, ++gi) {
-                const int s = gi % kStages, k = gi / kStages, b = gi % kAccBufs, u = gi / kAccBufs;
+            for (int it = 0; it < nst; ++it, ++gi, s = (s + 1 == kStages ? 0 : s + 1), ph ^= (s == 0 ? 1u : 0u)) {
+                // ring slot s = gi mod kStages, phase ph = (gi div kStages) mod 2
+                const int b = gi % kAccBufs, u = gi / kAccBufs;
                 if (it == 0 && j >= 2 &&
                     !mbar_wait(&small_free[par], (uint32_t)(((j >> 1) - 1) & 1), kBudget)) {
                     *abort_flag = 1;
@@ -395,7 +398,7 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUte
                     stop = true;
                     break;
                 }
-                if (!mbar_wait(&full[s], (uint32_t)(k & 1), kBudget)) {
+                if (!mbar_wait(&full[s], ph, kBudget)) {
                     *abort_flag = 1;
                     stop = true;
                     break;

@@ -170,7 +170,8 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
         // nested loops (item, offset, K chunk) without divisions, the leaf
         // coordinates of the item's z-rows are computed once per item, and
         // neighbours wrap by compare.
-        int gi = 0;
+        int gi = 0, s = 0;
+        uint32_t ph = 0;
         bool stop = false;
         for (int j = 0; j < nmine && !stop; ++j) {
             const int w = (int)blockIdx.x + j * (int)gridDim.x;
@@ -197,9 +198,9 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
                     ay -= ay >= n ? n : 0;
                     brow[r] = (outside ? nrow : ax * n + ay) * rowstride + 1 + dz;
                 }
-                for (int kc = 0; kc < kch; ++kc, ++gi) {
-                    const int s = gi % kStages, k = gi / kStages;
-                    if (gi >= kStages && !mbar_wait(&empty[s], (uint32_t)((k - 1) & 1), kBudget)) {
+                for (int kc = 0; kc < kch; ++kc, ++gi, s = (s + 1 == kStages ? 0 : s + 1), ph ^= (s == 0 ? 1u : 0u)) {
+                    // ring slot s = gi mod kStages, phase ph = (gi div kStages) mod 2
+                    if (gi >= kStages && !mbar_wait(&empty[s], ph ^ 1u, kBudget)) {
                         *abort_flag = 1;
                         stop = true;
                         break;
@@ -229,12 +230,14 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
         // (drained by the epilogue warps), small corrections into the item's
         // small accumulator
         const uint32_t idesc = idesc_f16(kRows, N);
-        int consumed = 0, gi = 0;
+        int consumed = 0, gi = 0, s = 0;
+        uint32_t ph = 0;
         bool stop = false;
         for (int j = 0; j < nmine && !stop; ++j)
-        for (int it = 0; it < kIters; ++it, ++gi) {
-            // (item j, stage it) walked as nested loops: no divisions per stage
-            const int s = gi % kStages, k = gi / kStages, b = gi % kAccBufs, u = gi / kAccBufs;
+        for (int it = 0; it < kIters; ++it, ++gi, s = (s + 1 == kStages ? 0 : s + 1), ph ^= (s == 0 ? 1u : 0u)) {
+            // (item j, stage it) walked as nested loops: no divisions per stage;
+            // ring slot s = gi mod kStages, phase ph = (gi div kStages) mod 2
+            const int b = gi % kAccBufs, u = gi / kAccBufs;
             const int par = j & 1;
             if (it == 0 && j >= 2 &&
                 !mbar_wait(&small_free[par], (uint32_t)(((j >> 1) - 1) & 1), kBudget)) {
@@ -247,7 +250,7 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
                 stop = true;
                 break;
             }
-            if (!mbar_wait(&full[s], (uint32_t)(k & 1), kBudget)) {
+            if (!mbar_wait(&full[s], ph, kBudget)) {
                 *abort_flag = 1;
                 stop = true;
                 break;
