@@ -172,10 +172,10 @@ static int choose_n_fmm(double box)
 static void free_device(Handle *H)
 {
     if (!H) return;
-    void *ptrs[] = {H->d_cellid, H->d_rank, H->d_count, H->d_start, H->d_perm, H->d_inv, H->d_loc, H->d_scell, H->d_flag, H->d_bsum,
+    void *ptrs[] = {H->d_cellid, H->d_rank, H->d_count, H->d_start, H->d_perm, H->d_inv, H->d_loc, H->d_ctr, H->d_scell, H->d_flag, H->d_bsum,
                     H->d_A0, H->d_A1, H->d_A2, H->d_A3, H->d_W, H->d_M, H->d_rho, H->d_rhohat, H->d_D,
                     H->d_phi, H->d_C, H->d_Chi, H->d_Clo, H->d_psi, H->d_gnear, H->d_pi, H->d_part,
-                    H->d_partoff, H->d_terms, H->d_hostbuf, H->d_Mhi, H->d_Mlo, H->d_mmax, H->d_ind, H->d_ind_part};
+                    H->d_partoff, H->d_rscr, H->d_ticket, H->d_terms, H->d_hostbuf, H->d_Mhi, H->d_Mlo, H->d_mmax, H->d_ind, H->d_ind_part};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     fmm_free(*H);
@@ -347,6 +347,7 @@ int ankh_create(double box_edge, int64_t N, const ankh_params *params, ankh_hand
     g.hf_lo = (float)(g.h - (double)g.hf);
     g.two_over_h = (float)(2.0 / g.h);
     g.xi = (float)p.xi;
+    g.Kf = (float)((double)n / box_edge);
 
     auto bail = [&](int code, const std::string &msg) {
         free_device(&H);
@@ -368,6 +369,20 @@ int ankh_create(double box_edge, int64_t N, const ankh_params *params, ankh_hand
     ANKH_AL(H.d_perm, N);
     ANKH_AL(H.d_inv, N);
     ANKH_AL(H.d_loc, N);
+    ANKH_AL(H.d_ctr, 3 * n);
+    {
+        // leaf centres of the binning's fast path, for leaf coordinates
+        // c = -n .. 2n-1 (atoms up to one box length outside the box)
+        std::vector<float> ctr(6 * (size_t)n);
+        for (int c = -n; c < 2 * n; ++c) {
+            const double v = -g.rB + ((double)c + 0.5) * g.h;
+            const float hi = (float)v;
+            ctr[2 * (size_t)(c + n)] = hi;
+            ctr[2 * (size_t)(c + n) + 1] = (float)(v - (double)hi);
+        }
+        if (cudaMemcpy(H.d_ctr, ctr.data(), sizeof(float) * ctr.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(ANKH_ECUDA, "cudaMemcpy leaf centres");
+    }
     ANKH_AL(H.d_scell, N);
     ANKH_AL(H.d_flag, 4);
     ANKH_AL(H.d_A0, N);
@@ -399,6 +414,9 @@ int ankh_create(double box_edge, int64_t N, const ankh_params *params, ankh_hand
     for (int k = 0; k < kPartCount; ++k) H.part_off[k + 1] = H.part_off[k] + nb[k];
     ANKH_AL(H.d_part, H.part_off[kPartCount]);
     ANKH_AL(H.d_partoff, kPartCount + 1);
+    ANKH_AL(H.d_rscr, kReduceBlocks * kPartCount);
+    ANKH_AL(H.d_ticket, 1);
+    cudaMemset(H.d_ticket, 0, sizeof(unsigned));
     ANKH_AL(H.d_terms, 9);
     if (cudaMallocHost(&H.h_terms, 9 * sizeof(double)) != cudaSuccess)
         return bail(ANKH_ENOMEM, "cudaMallocHost");

@@ -32,6 +32,7 @@ struct Geo {
     float hf_lo;      // h - hf (float): hf + hf_lo carries the FP64 leaf edge
     float two_over_h; // chain-rule factor of x_hat = 2 (x - ctr) / h
     float xi;
+    float Kf;         // n / L rounded to FP32 (the binning's FP32 screen)
 };
 
 // Pipeline stages (for the optional per-stage timing)
@@ -40,6 +41,7 @@ enum Stage { kStSort = 0, kStSelf, kStP2M, kStMerge, kStFFTf, kStSpectral, kStCo
 
 // Energy partial slots (FP64 per block, reduced in a fixed order).
 enum PartSlot { kPartNear = 0, kPartGlob = 1, kPartCorr = 2, kPartSelf = 3, kPartQ = 4, kPartCount = 5 };
+constexpr int kReduceBlocks = 32;   // blocks of the energy reduction (k_final.cu)
 
 // Tensor-core correction (k_corr_tc.cu): tile geometry and TMA descriptors.
 struct TcPlan {
@@ -110,6 +112,7 @@ struct Handle {
     int *d_cellid, *d_rank, *d_count, *d_start, *d_perm, *d_scell, *d_flag, *d_bsum;
     int *d_inv;             // [N] sorted slot of each atom (inverse of perm)
     float4 *d_loc;          // [N] coordinates relative to the leaf centre (caller's order)
+    float2 *d_ctr;          // [3n] leaf centres -r_B + (c + 1/2) h, c = -n .. 2n-1, as FP32 hi + lo
     float4 *d_A0, *d_A1, *d_A2, *d_A3;   // (lx, ly, lz, q) (mu, 0) (txx, txy, txz, tyy) (tyz, tzz, 0, 0)
     // interpolation
     float *d_W;             // [4][Lu][Lc] derivative matrices (2/h)^p E H D^p (E = I for ANKH-FMM)
@@ -126,6 +129,8 @@ struct Handle {
     double *d_part;         // energy partials
     int part_off[kPartCount + 1];
     int *d_partoff;         // device copy of part_off
+    double *d_rscr;         // [kReduceBlocks][kPartCount] per-block sums of the energy reduction
+    unsigned *d_ticket;     // blocks of the energy reduction done (the last one resets it to 0)
     double *d_terms;        // [8] reduced energy terms
     double *h_terms;        // pinned host copy
     float *d_hostbuf;       // staging for the host-buffer entry point

@@ -13,38 +13,61 @@ namespace ankh {
 
 int self_blocks(const Handle &H) { return (int)((H.N + 255) / 256); }
 
-// total charge and the k = 0 potential D0 Q / M -> terms[6], terms[7] (Q)
-__global__ void __launch_bounds__(256) k_dc(const double *__restrict__ part_q, int nq, double D0, double invM,
-                                            double *__restrict__ terms)
+// Sum of p[k] for k = b + tid, b + tid + nthr, ... < e in a fixed order.  The
+// loads of eight consecutive strides are issued before they are added, so
+// that their memory latencies overlap (one block reads tens of thousands of
+// partials; a load-add chain per thread would wait for every load in turn).
+__device__ __forceinline__ double strided_sum(const double *__restrict__ p, int b, int e, int tid, int nthr)
 {
-    __shared__ double sh[8];
-    double Q = 0.0;
-    for (int b = threadIdx.x; b < nq; b += 256) Q += part_q[b];
+    double v = 0.0;
+    int k = b + tid;
+    for (; k + 7 * nthr < e; k += 8 * nthr) {
+        double t[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) t[u] = __ldg(&p[k + u * nthr]);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v += t[u];
+    }
+    for (; k < e; k += nthr) v += __ldg(&p[k]);
+    return v;
+}
+
+// total charge and the k = 0 potential D0 Q / M -> terms[6], terms[7] (Q)
+__global__ void __launch_bounds__(1024) k_dc(const double *__restrict__ part_q, int nq, double D0, double invM,
+                                             double *__restrict__ terms)
+{
+    __shared__ double sh[32];
+    double Q = strided_sum(part_q, 0, nq, (int)threadIdx.x, 1024);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) Q += __shfl_down_sync(0xffffffffu, Q, o);
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = Q;
     __syncthreads();
     if (threadIdx.x == 0) {
         double u = 0.0;
-        for (int w = 0; w < 8; ++w) u += sh[w];
+        for (int w = 0; w < 32; ++w) u += sh[w];
         terms[7] = u;
         terms[6] = D0 * u * invM;
     }
 }
 
-// Fixed-order FP64 reduction of all energy partials.
+// Fixed-order FP64 reduction of all energy partials, over kReduceBlocks
+// blocks: block b sums the b-th contiguous share of every slot, and the last
+// block to finish (ticket) adds the per-block sums in block order, so the
+// result does not depend on which block finishes when.
 // terms: [0] near [1] far (k != 0) [2] k = 0 [3] correction [4] self [5] total
-//        [6] k = 0 potential [7] Q
-__global__ void k_reduce(const double *__restrict__ part, const int *__restrict__ off_dev,
-                         double invM2, double D0, const int *__restrict__ flag, double *__restrict__ terms,
-                         int have_glob, int have_corr)
+//        [6] k = 0 potential [7] Q [8] error flag
+__global__ void __launch_bounds__(256)
+k_reduce(const double *__restrict__ part, const int *__restrict__ off_dev, double invM2, double D0,
+         const int *__restrict__ flag, double *__restrict__ terms, double *__restrict__ scr,
+         unsigned *__restrict__ ticket)
 {
-    __shared__ double sh[32];
-    __shared__ double res[kPartCount];
-    for (int slot = 0; slot < kPartCount; ++slot) {
-        const int b = off_dev[slot], e = off_dev[slot + 1];
-        double v = 0.0;
-        for (int k = b + threadIdx.x; k < e; k += blockDim.x) v += part[k];
+    __shared__ double sh[8];
+    __shared__ bool last;
+    for (int slot = 0; slot < kPartQ; ++slot) {   // near, far, correction, self (Q is k_dc's)
+        const int b = off_dev[slot], len = off_dev[slot + 1] - b;
+        const int per = (len + (int)gridDim.x - 1) / (int)gridDim.x;
+        const int lo = b + min(len, (int)blockIdx.x * per), hi = b + min(len, ((int)blockIdx.x + 1) * per);
+        double v = strided_sum(part, lo, hi, (int)threadIdx.x, (int)blockDim.x);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
@@ -52,33 +75,43 @@ __global__ void k_reduce(const double *__restrict__ part, const int *__restrict_
         if (threadIdx.x == 0) {
             double u = 0.0;
             for (int w = 0; w < (int)(blockDim.x >> 5); ++w) u += sh[w];
-            res[slot] = u;
+            scr[blockIdx.x * kPartCount + slot] = u;
         }
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        const double Q = terms[7];
-        const double near = res[kPartNear];
-        const double glob = have_glob ? res[kPartGlob] * invM2 : 0.0;
-        const double dc = have_glob ? D0 * Q * Q * invM2 : 0.0;
-        const double corr = have_corr ? res[kPartCorr] : 0.0;
-        const double self = res[kPartSelf];
-        terms[0] = near;
-        terms[1] = glob;
-        terms[2] = dc;
-        terms[3] = corr;
-        terms[4] = self;
-        terms[5] = near + glob + dc + corr + self;
-        terms[8] = (double)(*flag);
-        if (*flag) terms[5] = __longlong_as_double(0x7ff8000000000000LL);
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
     }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    double res[kPartQ] = {0.0, 0.0, 0.0, 0.0};
+    for (int bq = 0; bq < (int)gridDim.x; ++bq)
+#pragma unroll
+        for (int slot = 0; slot < kPartQ; ++slot) res[slot] += __ldcg(&scr[bq * kPartCount + slot]);
+    *ticket = 0u;
+    const double Q = terms[7];
+    const double near = res[kPartNear];
+    const double glob = res[kPartGlob] * invM2;
+    const double dc = D0 * Q * Q * invM2;
+    const double corr = res[kPartCorr];
+    const double self = res[kPartSelf];
+    terms[0] = near;
+    terms[1] = glob;
+    terms[2] = dc;
+    terms[3] = corr;
+    terms[4] = self;
+    terms[5] = near + glob + dc + corr + self;
+    terms[8] = (double)(*flag);
+    if (*flag) terms[5] = __longlong_as_double(0x7ff8000000000000LL);
 }
 
 // the self term and Q partials are produced by the gather kernel (k_sort.cu)
 cudaError_t launch_self_dc(Handle &H, cudaStream_t s)
 {
-    k_dc<<<1, 256, 0, s>>>(H.d_part + H.part_off[kPartQ], self_blocks(H), H.D0, 1.0 / (double)H.g.M,
-                           H.d_terms);
+    k_dc<<<1, 1024, 0, s>>>(H.d_part + H.part_off[kPartQ], self_blocks(H), H.D0, 1.0 / (double)H.g.M,
+                            H.d_terms);
     return cudaGetLastError();
 }
 
@@ -87,7 +120,8 @@ cudaError_t launch_reduce(Handle &H, cudaStream_t s)
     // ANKH-FMM: the far slot holds the root term itself and there is no k = 0 grid term
     const double invM2 = H.fmm.enabled ? 1.0 : 0.5 / (double)H.g.M;
     const double D0 = H.fmm.enabled ? 0.0 : H.D0;
-    k_reduce<<<1, 1024, 0, s>>>(H.d_part, H.d_partoff, invM2, D0, H.d_flag, H.d_terms, 1, 1);
+    k_reduce<<<kReduceBlocks, 256, 0, s>>>(H.d_part, H.d_partoff, invM2, D0, H.d_flag, H.d_terms, H.d_rscr,
+                                           H.d_ticket);
     return cudaGetLastError();
 }
 

@@ -57,6 +57,11 @@ enum { kErfcLib = 0, kSeriesLong = 1, kSeriesShort = 2 };
 
 constexpr int kNearWarps = 4;
 constexpr int kNearChunk = 64;
+// Leaves per warp: the launch covers the leaves with ncell / (4 kNearWarps)
+// blocks, which the hardware hands to the SMs as earlier blocks retire.  A
+// persistent grid (a fixed share of leaves per warp) left the SMs idle at the
+// end, waiting for the warps that drew the heaviest leaves.
+constexpr int kNearLeavesPerWarp = 4;
 
 template <bool FORCES>
 struct NAcc {
@@ -318,8 +323,9 @@ k_near(Geo g, const int *__restrict__ start, const float4 *__restrict__ A0, cons
 
 int near_blocks(const Handle &H)
 {
-    (void)H;
-    return 152 * 7;   // 7 blocks of 128 threads per SM (<= 73 registers per thread)
+    // 7 blocks of 128 threads are resident per SM (<= 73 registers per thread)
+    const int per_block = kNearWarps * kNearLeavesPerWarp;
+    return (H.g.ncell + per_block - 1) / per_block;
 }
 
 cudaError_t launch_near(Handle &H, bool forces, cudaStream_t s)

@@ -42,11 +42,39 @@ __global__ void k_bin(int N, const float *__restrict__ x, Geo g, int *__restrict
     rank[i] = atomicAdd(&count[cell], 1);
 }
 
+// FP32 screen in front of the FP64 chain (GB300's FP64 rate made the chain
+// the largest cost of the sort).  a = fl32(x K + n/2), K = fl32(n / L), lies
+// within 4.5 n 2^-24 of S = (x + r_B) n / L for a in [-n, 2n) (one rounding
+// of K, one of the fused multiply-add).  When no integer lies within
+// n 2^-20 of a, floor(S) = floor(a), and the FP64 chain (error below
+// 2^-50 |S|) also returns floor(S) mod n: the leaf is the same bit for bit.
+// The leaf-relative coordinate is x minus the centre of the unwrapped leaf,
+// the centre carried as FP32 hi + lo (within one FP32 ulp of the FP64
+// chain's value).  Returns false where the FP64 chain must decide: a close
+// to a leaf face, more than one box length outside the box, or not finite.
+__device__ __forceinline__ bool leaf_coord_fast(float x, const Geo &g, const float2 *__restrict__ ctr, int *c,
+                                                float *loc)
+{
+    const float nf = (float)g.n;
+    const float a = fmaf(x, g.Kf, 0.5f * nf);
+    if (!(a >= -nf && a < 2.f * nf)) return false;
+    const float fa = floorf(a);
+    const float fr = a - fa;                        // exact: |a| < 2^23
+    const float err = nf * 9.5367431640625e-07f;    // n 2^-20
+    if (!(fr > err && fr < 1.f - err)) return false;
+    const int cs = (int)fa;                         // -n .. 2n-1
+    *c = cs < 0 ? cs + g.n : (cs >= g.n ? cs - g.n : cs);
+    const float2 ce = __ldg(&ctr[cs + g.n]);
+    *loc = (x - ce.x) - ce.y;
+    return true;
+}
+
 // Same, and the coordinates relative to the leaf centre, loc = (s n - c - 1/2) h
-// (FP64, rounded once to FP32), for the move into leaf order.
-__global__ void k_bin_loc(int N, const float *__restrict__ x, Geo g, int *__restrict__ cellid,
-                          int *__restrict__ rank, int *__restrict__ count, int *__restrict__ flag,
-                          float4 *__restrict__ loc)
+// (FP64, rounded once to FP32; x - centre in FP32 on the fast path), for the
+// move into leaf order.
+__global__ void k_bin_loc(int N, const float *__restrict__ x, Geo g, const float2 *__restrict__ ctr,
+                          int *__restrict__ cellid, int *__restrict__ rank, int *__restrict__ count,
+                          int *__restrict__ flag, float4 *__restrict__ loc)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -55,7 +83,9 @@ __global__ void k_bin_loc(int N, const float *__restrict__ x, Geo g, int *__rest
     bool bad = false;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        double xv = (double)x[3 * (int64_t)i + a];
+        const float xf = x[3 * (int64_t)i + a];
+        if (leaf_coord_fast(xf, g, ctr, &c[a], &l[a])) continue;
+        double xv = (double)xf;
         if (!isfinite(xv)) { bad = true; xv = 0.0; }
         double sn;
         c[a] = leaf_coord(xv, g, &sn);
@@ -82,9 +112,9 @@ __device__ __forceinline__ int leaf_coord_np(double xv, const Geo &g, double *fr
     return c;
 }
 
-__global__ void k_bin_np(int N, const float *__restrict__ x, Geo g, int *__restrict__ cellid,
-                         int *__restrict__ rank, int *__restrict__ count, int *__restrict__ flag,
-                         float4 *__restrict__ loc)
+__global__ void k_bin_np(int N, const float *__restrict__ x, Geo g, const float2 *__restrict__ ctr,
+                         int *__restrict__ cellid, int *__restrict__ rank, int *__restrict__ count,
+                         int *__restrict__ flag, float4 *__restrict__ loc)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -93,7 +123,18 @@ __global__ void k_bin_np(int N, const float *__restrict__ x, Geo g, int *__restr
     bool bad = false, out = false;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        double xv = (double)x[3 * (int64_t)i + a];
+        const float xf = x[3 * (int64_t)i + a];
+        // the FP32 screen of the periodic binning; inside the box (leaf in
+        // [0, n), away from every face) the clamped chain gives the same leaf
+        int cf;
+        float lf;
+        const float af = fmaf(xf, g.Kf, 0.5f * (float)g.n);   // the screen's a
+        if (af > 0.f && af < (float)g.n && leaf_coord_fast(xf, g, ctr, &cf, &lf)) {
+            c[a] = cf;
+            l[a] = lf;
+            continue;
+        }
+        double xv = (double)xf;
         if (!isfinite(xv)) { bad = true; xv = 0.0; }
         double sn;
         bool o;
@@ -321,11 +362,11 @@ cudaError_t launch_bin(Handle &H, const float *x, cudaStream_t s)
     cudaMemsetAsync(H.d_flag, 0, sizeof(int), s);
     int N = (int)H.N;
     if (H.g.nonperiodic)
-        k_bin_np<<<(N + 255) / 256, 256, 0, s>>>(N, x, H.g, H.d_cellid, H.d_rank, H.d_count, H.d_flag,
-                                                  H.d_loc);
+        k_bin_np<<<(N + 255) / 256, 256, 0, s>>>(N, x, H.g, H.d_ctr, H.d_cellid, H.d_rank, H.d_count,
+                                                  H.d_flag, H.d_loc);
     else
-        k_bin_loc<<<(N + 255) / 256, 256, 0, s>>>(N, x, H.g, H.d_cellid, H.d_rank, H.d_count, H.d_flag,
-                                                   H.d_loc);
+        k_bin_loc<<<(N + 255) / 256, 256, 0, s>>>(N, x, H.g, H.d_ctr, H.d_cellid, H.d_rank, H.d_count,
+                                                   H.d_flag, H.d_loc);
     return cudaGetLastError();
 }
 
