@@ -42,7 +42,7 @@ N_SM = 152
 # DRAM bytes (read + write) per launch from one ncu capture of the same kernel
 # code on the same workload (profiles/); keyed by (kernel, workload, n, L_u)
 DRAM_TRAFFIC = {
-    ("near", "water_1008000_qmuTheta", 54, 5): 61.925659e9 * 1.633120e-3,   # profiles/k_near_water1008000_n54.md
+    ("near", "water_1008000_qmuTheta", 54, 5): 74.012928e6 + 25.202432e6,   # profiles/k_near_water1008000_n54.md
     ("m2l", "water_1008000_qmuTheta", 64, 5): 627.331328e6 + 3.399680e6,    # profiles/k_m2l_tc_water1008000_n64.md
 }
 
