@@ -87,6 +87,65 @@ def test_binning_is_bit_exact(api):
     del torch
 
 
+def face_coords(rng, box, n, count, lo, hi):
+    """FP32 coordinates next to the leaf faces k L / n - L / 2, k = lo .. hi:
+    the first half on a face or up to three FP32 steps either side of it, the
+    second half 1 to 4 times n 2^-20 leaf edges away from it (just outside the
+    band that the binning's FP32 screen hands to the FP64 chain)."""
+    k = rng.integers(lo, hi + 1, size=count)
+    h = box / n
+    far = np.arange(count) >= count // 2
+    delta = rng.uniform(1.0, 4.0, size=count) * n * 2.0 ** -20 * h * rng.choice([-1.0, 1.0], size=count)
+    v = (k * h - box / 2 + np.where(far, delta, 0.0)).astype(np.float32)
+    steps = np.where(far, 0, rng.integers(-3, 4, size=count))
+    for s in range(3):
+        up, dn = steps > s, steps < -s
+        v[up] = np.nextafter(v[up], np.float32(np.inf))
+        v[dn] = np.nextafter(v[dn], np.float32(-np.inf))
+    return v
+
+
+@pytest.mark.parametrize("nonperiodic", [False, True], ids=["periodic", "nonperiodic"])
+def test_binning_is_bit_exact_next_to_faces(api, nonperiodic):
+    """The leaf binning decides most coordinates with an FP32 screen and the
+    rest with the correctly rounded FP64 chain; the leaves must still match
+    the FP64 definition bit for bit.  4,000 of the 24,000 atoms get one
+    coordinate next to a leaf face (periodic: faces up to one box length
+    outside the box, which wrap), on both sides of the screen's band."""
+    b = synth.config_box(2)
+    n = 14
+    rng = np.random.default_rng(2212)
+    count = 4000
+    idx = rng.choice(b.n, size=count, replace=False)
+    axis = rng.integers(0, 3, size=count)
+    fc = face_coords(rng, b.box, n, count, 0 if nonperiodic else -n, n if nonperiodic else 2 * n)
+    if nonperiodic:
+        # keep every atom inside [-L/2, L/2)
+        hi = np.float32(b.box / 2)
+        if float(hi) >= b.box / 2:
+            hi = np.nextafter(hi, np.float32(-np.inf))
+        lo = np.float32(-b.box / 2)
+        if float(lo) < -b.box / 2:
+            lo = np.nextafter(lo, np.float32(np.inf))
+        fc = np.clip(fc, lo, hi)
+    x = b.x.copy()
+    x[idx, axis] = fc
+    b.x = x.astype(np.float32)
+    m = api.Ankh(b.box, b.n, n_cells=n, Lu=5, max_order=0, nonperiodic=nonperiodic)
+    xd, qd, _, _ = to_dev(b)
+    m.energy(xd, qd, None, None)
+    perm = api.ankh_debug_copy(m.h, api.BUF_PERM).cpu().numpy()
+    start = api.ankh_debug_copy(m.h, api.BUF_START).cpu().numpy()
+    scell = api.ankh_debug_copy(m.h, api.BUF_SCELL).cpu().numpy()
+    m.close()
+    binf = ar.bin_atoms_nonperiodic if nonperiodic else ar.bin_atoms
+    cell, _, _, operm = binf(b.x, b.box, n)
+    ostart = np.concatenate([[0], np.cumsum(np.bincount(cell, minlength=n ** 3))])
+    assert np.array_equal(perm, operm)
+    assert np.array_equal(start, ostart)
+    assert np.array_equal(scell, cell[operm])
+
+
 def test_modified_charges_match_alg2(api):
     b = synth.small_box(1000, 31, box=31.1)
     n, Lu, Lc = 7, 5, 6
