@@ -50,9 +50,11 @@ __global__ void __launch_bounds__(1024) k_dc(const double *__restrict__ part_q, 
     }
 }
 
+static_assert(kReduceBlocks <= 32, "the last block adds the block sums within one warp");
+
 // Fixed-order FP64 reduction of all energy partials, over kReduceBlocks
 // blocks: block b sums the b-th contiguous share of every slot, and the last
-// block to finish (ticket) adds the per-block sums in block order, so the
+// block to finish (ticket) adds the per-block sums in a fixed tree, so the
 // result does not depend on which block finishes when.
 // terms: [0] near [1] far (k != 0) [2] k = 0 [3] correction [4] self [5] total
 //        [6] k = 0 potential [7] Q [8] error flag
@@ -84,12 +86,19 @@ k_reduce(const double *__restrict__ part, const int *__restrict__ off_dev, doubl
         last = atomicAdd(ticket, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (!last || threadIdx.x != 0) return;
+    if (!last || threadIdx.x >= 32) return;
     __threadfence();
-    double res[kPartQ] = {0.0, 0.0, 0.0, 0.0};
-    for (int bq = 0; bq < (int)gridDim.x; ++bq)
+    // lane l loads block l's sums (all loads in flight at once) and the warp
+    // adds them in a fixed shuffle tree (kReduceBlocks <= 32)
+    double res[kPartQ];
 #pragma unroll
-        for (int slot = 0; slot < kPartQ; ++slot) res[slot] += __ldcg(&scr[bq * kPartCount + slot]);
+    for (int slot = 0; slot < kPartQ; ++slot)
+        res[slot] = threadIdx.x < gridDim.x ? __ldcg(&scr[threadIdx.x * kPartCount + slot]) : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int slot = 0; slot < kPartQ; ++slot) res[slot] += __shfl_down_sync(0xffffffffu, res[slot], o);
+    if (threadIdx.x != 0) return;
     *ticket = 0u;
     const double Q = terms[7];
     const double near = res[kPartNear];
