@@ -10,7 +10,10 @@
     pairs, node pairs and images (Thm. 1 indexing, DFT normalisation);
   * geometric convergence towards the independent Ewald oracle;
   * the analytic adjoint against central finite differences;
-  * bit-exact binning of atoms on and next to leaf faces.
+  * bit-exact binning of atoms on and next to leaf faces;
+  * moments of the modified charges: the leaf interpolation reproduces
+    polynomials of degree < L_u, so per leaf sum_b M_b f(y_b) =
+    sum_i (q_i + mu_i . grad + Theta_i : grad grad) f(x_i) for f = 1, y, y y^T.
 """
 import math
 
@@ -223,3 +226,56 @@ def test_binning_on_faces():
     assert list(cvec[:, 0]) == [0, 1, 4, 0, 4, 2, 2, 3, 4, 3]
     assert np.all(xw >= -box / 2) and np.all(xw < box / 2)
     assert np.array_equal(perm, np.argsort(cell, kind="stable"))
+
+
+@pytest.mark.parametrize("Lu,Lc", [(3, 3), (5, 6), (6, 6)])
+def test_modified_charge_moments(Lu, Lc):
+    """Alg. 2 with the E_c re-interpolation (reading of Sec. 4.1): the nodes'
+    modified charges carry the atoms' multipole moments about the leaf
+    centre exactly (to FP64 rounding): total charge; charge-weighted position
+    plus dipole; charge-weighted second moment plus the dipole terms plus
+    twice the quadrupole.  A sign slip on mu, a missing factor on an
+    off-diagonal Theta entry or on the chain factor 2/h breaks one of them."""
+    b = synth.small_box(400, 77, box=22.0)
+    n = 4
+    p = ar.Params(b.box, n, Lu, Lc)
+    mp = ew.pack_multipoles(b.q, b.mu, b.theta)
+    cell, cvec, xw, perm = ar.bin_atoms(b.x, p.box, n)
+    S = ar.basis_derivs(xw, cvec, p, pmax=2)
+    Q = ar.modified_charges(cell, S, mp, p)
+    E = ar.reinterp_E(Lu, Lc)
+    M = np.einsum("ak,bl,cm,sklm->sabc", E, E, E, Q)            # (n^3, Lu, Lu, Lu)
+    h = p.box / n
+    ctr = -p.box / 2.0 + (cvec + 0.5) * h
+    r = xw - ctr                                                 # atom about its leaf centre
+    e = ar.equi_nodes(Lu) * (h / 2.0)                            # node offsets about the centre
+    ones = np.ones(Lu)
+    ax = [np.einsum("a,b,c->abc", e, ones, ones), np.einsum("a,b,c->abc", ones, e, ones),
+          np.einsum("a,b,c->abc", ones, ones, e)]
+    q = mp[:, 0]
+    mu = mp[:, 1:4]
+    th = np.zeros((len(q), 3, 3))
+    iu = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+    for k, (a, c) in enumerate(iu):
+        th[:, a, c] = th[:, c, a] = mp[:, 4 + k]
+
+    def per_leaf(v):
+        out = np.zeros((n ** 3,) + v.shape[1:])
+        np.add.at(out, cell, v)
+        return out
+
+    scale = np.max(np.abs(M))
+    # f = 1
+    assert np.allclose(M.sum(axis=(1, 2, 3)), per_leaf(q), atol=1e-12 * scale * Lu ** 3)
+    # f = y_a
+    for a in range(3):
+        lhs = np.einsum("sabc,abc->s", M, ax[a])
+        rhs = per_leaf(q * r[:, a] + mu[:, a])
+        assert np.allclose(lhs, rhs, atol=1e-11 * scale * Lu ** 3 * h)
+    # f = y_a y_c
+    for a in range(3):
+        for c in range(3):
+            lhs = np.einsum("sabc,abc->s", M, ax[a] * ax[c])
+            rhs = per_leaf(q * r[:, a] * r[:, c] + mu[:, a] * r[:, c] + mu[:, c] * r[:, a] + 2.0 * th[:, a, c])
+            assert np.allclose(lhs, rhs, atol=1e-11 * scale * Lu ** 3 * h * h)
+
