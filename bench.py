@@ -32,19 +32,19 @@ sys.path.insert(0, ROOT)
 WORKLOADS = {"water_1008000": 4, "water_96000": 3, "water_24000": 2, "replicas64": 5}
 METRIC = "energy+force evals/s and Matoms/s at <=1e-5 rel. energy error vs FP64 Ewald"
 UNIT = "evals/s"
-# FP32 operations per UNORDERED near-field pair of the energy + gradient + field
-# evaluation in the mutual formulation of the pair formula (counted from the
-# code: ~190 for the energy, ~120 for the shared force, ~2 x 130 for the
-# potential / field / field gradient of both atoms; FMA = 2).
-NEAR_FLOPS_PER_PAIR = 560
+# Algorithmic FP32 work of the near field per UNORDERED pair of atoms in
+# adjacent leaves: 400 flop for the energy, forces, fields and field gradients
+# of both atoms (FMA = 2).  The kernel evaluates every ordered pair once in its
+# source-field form, 262 flop each (150 for the potential, field and field
+# gradient, 112 for the quadrupole force), i.e. 524 flop per unordered pair
+# executed; both rates are reported.
+NEAR_FLOPS_PER_PAIR = 400
+NEAR_FLOPS_EXECUTED_PER_ORDERED_PAIR = 262
 FP32_LANES_PER_SM = 128
-N_SM = 152
 # DRAM bytes (read + write) per launch from one ncu capture of the same kernel
-# code on the same workload (profiles/); keyed by (kernel, workload, n, L_u)
-DRAM_TRAFFIC = {
-    ("near", "water_1008000_qmuTheta", 54, 5): 74.012928e6 + 25.202432e6,   # profiles/k_near_water1008000_n54.md
-    ("m2l", "water_1008000_qmuTheta", 64, 5): 627.331328e6 + 3.399680e6,    # profiles/k_m2l_tc_water1008000_n64.md
-}
+# code on the same workload and leaf count; keyed by (kernel, workload, n, L_u).
+# Entries are removed whenever the kernel changes and re-measured.
+DRAM_TRAFFIC: dict = {}
 
 
 def env_int(k, d):
@@ -63,12 +63,12 @@ class ClockSampler:
         self.lines = []
 
     def start(self):
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+        q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             threading.Thread(target=self._read, daemon=True).start()
         except OSError:
@@ -76,7 +76,11 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self, name):
+        """Wall-clock mark (the start or end of the timed region)."""
+        setattr(self, name, time.time())
 
     def stop(self):
         if self.proc:
@@ -85,22 +89,66 @@ class ClockSampler:
                 self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
-        sm, mx, reasons = [], None, set()
+        sm, mx, reasons, inside = [], None, set(), 0
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        t0, t1 = getattr(self, "load_start", None), getattr(self, "timed_end", None)
+        ts0 = getattr(self, "timed_start", None)
+        for tr, ln in self.lines:
             p = [x.strip() for x in ln.split(",")]
-            if len(p) < 9:
+            if len(p) < 10:
+                continue
+            # samples while the GPU runs the step: the untimed pre-roll and the timed region
+            if t0 is not None and t1 is not None and not (t0 <= tr <= t1 + 0.06):
                 continue
             try:
-                sm.append(float(p[1]))
-                mx = float(p[2])
+                sm.append(float(p[2]))
+                mx = float(p[3])
             except ValueError:
                 continue
-            for nm, v in zip(names, p[5:9]):
+            if ts0 is not None and ts0 <= tr <= t1 + 0.06:
+                inside += 1
+            for nm, v in zip(names, p[6:10]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "samples_in_timed_region": inside,
+                "sampling": "nvidia-smi every 50 ms while the step runs (an untimed pre-roll of the same "
+                            "step, then the timed steps)"}
+
+
+def radix_passes(ncell: int) -> int:
+    """Digit passes of the library's leaf sort (ids of B bits, <= 10 bits a pass)."""
+    B = 1
+    while B < 31 and (1 << B) < ncell:
+        B += 1
+    return (B + 9) // 10
+
+
+def launches_per_step(ncell: int, plain: bool) -> int:
+    """Kernels of one energy + gradient evaluation: bin, leaf scan (2), radix
+    sort (histogram, 2 scan kernels, scatter per pass), gather, k = 0 term,
+    P2M, merge, spectral product, [fp16 split,] correction, near field, node
+    potentials, L2P, energy reduction (cuFFT's two transforms not counted)."""
+    return 1 + 2 + 4 * radix_passes(ncell) + 1 + 1 + 1 + 1 + 1 + (0 if plain else 1) + 1 + 1 + 1 + 1 + 1
+
+
+def batch_box_cells(api, bt, i: int) -> int:
+    """Leaves per axis of box i of a batch."""
+    return int(api.ankh_get_info(api.ankh_batch_box(bt.h, i))["n_cells"])
+
+
+def preroll(clocks, step, seconds=0.4):
+    """Start the clock sampler and run the untimed step for `seconds` so that
+    the samples (and the clocks) are those of the loaded GPU; marks the start
+    of the timed region."""
+    import torch
+    clocks.start()
+    time.sleep(0.15)                    # the sampler process starts
+    clocks.mark("load_start")
+    t = time.perf_counter()
+    while time.perf_counter() - t < seconds:
+        step()
+        torch.cuda.synchronize()
 
 
 def measured_peaks():
@@ -289,8 +337,11 @@ def run_replicas(args, rank, world, dev, api, synth, dist=None):
     for _ in range(max(args.warmup, 3)):
         bt.energy_forces(x, q, mu, th, out=out)
     clocks = ClockSampler(dev.index)
-    clocks.start()
-    time.sleep(0.3)
+    preroll(clocks, lambda: bt.energy_forces(x, q, mu, th, out=out))
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.mark("timed_start")
     tot = 0.0
     for k in range(args.steps):
         flush.fill_(float(k))
@@ -301,6 +352,8 @@ def run_replicas(args, rank, world, dev, api, synth, dist=None):
         e1.record(stream)
         e1.synchronize()
         tot += e0.elapsed_time(e1) / 1e3
+    torch.cuda.synchronize()
+    clocks.mark("timed_end")
     clk = clocks.stop()
     if dist:
         dist.barrier()
@@ -317,7 +370,8 @@ def run_replicas(args, rank, world, dev, api, synth, dist=None):
                        "execution": "one CUDA graph per rank, one branch per box",
                        "parallelism": f"boxes split over {world} GPU(s) by LPT on atom counts"},
             "matoms_per_s": value / 64 * ntot_all / 1e6, "clocks": clk, "roofline": None, "cpu_baseline": None,
-            "e2e": None, "gpu_launches": 16 * len(boxes) * args.steps}), flush=True)
+            "e2e": None, "gpu_launches": sum(launches_per_step(batch_box_cells(api, bt, i) ** 3, args.plain)
+                                             for i in range(len(boxes))) * args.steps}), flush=True)
     bt.close()
 
 
@@ -365,11 +419,11 @@ def run_fmm(args, rank, world, dev, api, synth, dist, cfg):
         flush.fill_(1.0)
         api.ankh_energy(model.h, x, q, mu, th, stream=stream)
     clocks = ClockSampler(dev.index)
+    preroll(clocks, lambda: api.ankh_energy(model.h, x, q, mu, th, stream=stream))
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks.start()
-    time.sleep(0.3)
+    clocks.mark("timed_start")
     names = {"sort": "sort", "self": "self", "p2m": "p2m", "merge": "m2m", "spectral": "root", "corr": "m2l",
              "near": "near", "reduce": "reduce"}
     stage_sum = {v: 0.0 for v in names.values()}
@@ -387,6 +441,8 @@ def run_fmm(args, rank, world, dev, api, synth, dist, cfg):
         for s_, v in api.ankh_stage_times(model.h).items():
             if s_ in names:
                 stage_sum[names[s_]] += v
+    torch.cuda.synchronize()
+    clocks.mark("timed_end")
     clk = clocks.stop()
     if dist:
         dist.barrier()
@@ -453,7 +509,9 @@ def run_fmm(args, rank, world, dev, api, synth, dist, cfg):
             "precompute_s": t_pre, "accuracy": acc, "clocks": clk, "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": world * args.e2e_steps / t_e2e, "unit": "evals/s",
                     "h2d_bytes_per_step": 4 * N * (3 + 1 + 3 + 6), "d2h_bytes_per_step": 9 * 8},
-            "gpu_launches": (13 + depth) * args.steps}), flush=True)
+            # sort (bin, leaf scan, radix passes, gather), self, P2M, M2M per level,
+            # split, M2L, root, near, reduce
+            "gpu_launches": (4 + 4 * radix_passes(n ** 3) + 7 + depth) * args.steps}), flush=True)
     model.close()
 
 
@@ -479,10 +537,11 @@ def run_induce(args, rank, world, dev, api, synth, dist, cfg):
     for _ in range(max(args.warmup, 3)):
         E_pol, it = api.ankh_induce(model.h, x, q, mu, th, alpha, out, tol=1e-6, stream=stream)
     clocks = ClockSampler(dev.index)
+    preroll(clocks, lambda: api.ankh_induce(model.h, x, q, mu, th, alpha, out, tol=1e-6, stream=stream))
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks.start()
+    clocks.mark("timed_start")
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -492,6 +551,7 @@ def run_induce(args, rank, world, dev, api, synth, dist, cfg):
         its.append(it)
     e1.record(stream)
     e1.synchronize()
+    clocks.mark("timed_end")
     clk = clocks.stop()
     t = max_over_ranks(e0.elapsed_time(e1) / 1e3, dist, dev)
     value = world * args.steps / t
@@ -507,9 +567,10 @@ def run_induce(args, rank, world, dev, api, synth, dist, cfg):
                        "parallelism": f"replicas{world}"},
             "iterations": statistics.mean(its), "ms_per_field_evaluation": t * 1e3 / evals,
             "E_pol": E_pol, "clocks": clk, "roofline": None, "cpu_baseline": None, "e2e": None,
-            # per solve: 16 kernels per field evaluation (iterations + 2 of them),
-            # 3 vector kernels per iteration, 3 outside the loop
-            "gpu_launches": int(round(args.steps * (16 * (statistics.mean(its) + 2) + 3 * statistics.mean(its) + 3)))}),
+            # per solve: one evaluation's kernels per field evaluation (iterations + 2
+            # of them), 3 vector kernels per iteration, 3 outside the loop
+            "gpu_launches": int(round(args.steps * (launches_per_step(n_cells ** 3, args.plain)
+                                                    * (statistics.mean(its) + 2) + 3 * statistics.mean(its) + 3)))}),
               flush=True)
     model.close()
 
@@ -601,12 +662,19 @@ def main():
     torch.cuda.synchronize()
     E = api.ankh_energy_forces(model.h, x, q, mu, th, stream=stream, **out)
 
+    # FP32 FMA throughput of this GPU (the near field's roofline denominator)
+    fp32_meas, _ = api.ankh_measure_fp32_peak(stream)
+
+    def flushed_step():
+        flush.fill_(1.0)
+        step()
+
     clocks = ClockSampler(dev.index)
+    preroll(clocks, flushed_step)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks.start()
-    time.sleep(0.3)
+    clocks.mark("timed_start")
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     stage_sum = {k: 0.0 for k in api.STAGES}
@@ -621,6 +689,7 @@ def main():
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
+    clocks.mark("timed_end")
     clk = clocks.stop()
     t_dev = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1)) / 1e3   # seconds, device time
     t_max = max_over_ranks(t_dev, dist, dev)
@@ -677,26 +746,43 @@ def main():
     pairs = unordered_near_pairs(start, n, args.nonperiodic)
     dom = max(stage_ms, key=stage_ms.get)
     sm_mhz = clk["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12   # TF/s at the sampled clock
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_nominal = n_sm * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12   # TF/s at the sampled clock
+    fp32_peak = fp32_meas
     P = info["Lu"] ** 3
     ncell = n ** 3
+    M_grid = info["nf"] ** 3
+    # Correction: psi_t = sum_d C_d M_(t+d) over all 27 offsets d (the forces
+    # need psi at every leaf: the 13 mutual offsets give the energy alone, and
+    # C_(-d) = C_d^T still has to be applied to M_t for psi_(t+d)), one
+    # P x P block product per (leaf, offset), three products for the 2xFP16
+    # split; unpadded P nodes, n^3 leaves.
+    corr_flop = 2 * 27 * P * P * ncell * (3 if not args.plain else 1)
     models = {
         "near": ("alu", pairs * NEAR_FLOPS_PER_PAIR / 1e12, fp32_peak, "TFLOP/s"),
-        # algorithmic flop of the correction (unpadded P nodes, n^3 leaves); the
-        # fp16 split executes three products of each, at the fp16 = bf16 rate
-        "corr": ("tensor" if not args.plain else "alu", 2 * 27 * P * P * ncell / 1e12,
+        "corr": ("tensor" if not args.plain else "alu", corr_flop / 1e12,
                  peaks["bf16_tflops"] if not args.plain else fp32_peak, "TFLOP/s"),
+        # P2M: read 52 B per atom (position, q, mu, Theta), write 4 B per leaf node
         "p2m": ("hbm", (52 * N + 4 * ncell * P) / 1e9, peaks["hbm_gbs"], "GB/s"),
-        "l2p": ("hbm", (52 * N + 8 * ncell * P + 52 * N) / 1e9, peaks["hbm_gbs"], "GB/s"),
+        # L2P (node potentials + gradient assembly): read the grid potential
+        # (4 B per grid point), the correction potential (4 B per leaf node)
+        # and 52 B per atom; write 64 B per atom (dE/dx, dE/dq, dE/dmu,
+        # dE/dTheta, torque)
+        "l2p": ("hbm", (4 * M_grid + 4 * ncell * P + 52 * N + 64 * N) / 1e9, peaks["hbm_gbs"], "GB/s"),
     }
 
     def roofline(k):
         bound, work, peak, unit = models[k]
         achieved = work / (stage_ms[k] / 1e3)
-        return {"kernel": k, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": DRAM_TRAFFIC.get((k, wname, n, info["Lu"])),
-                "peak_source": (f"FP32: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz "
-                                f"(sampled clock)" if bound == "alu" else f"{peak_kind} MEASURED_PEAKS")}
+        r = {"kernel": k, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+             "frac": achieved / peak, "traffic": DRAM_TRAFFIC.get((k, wname, n, info["Lu"])),
+             "peak_source": ("FP32 FMA throughput measured on this GPU (ankh_measure_fp32_peak); nominal "
+                             f"{n_sm} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz sampled = "
+                             f"{fp32_nominal:.1f} TFLOP/s" if bound == "alu" else
+                             f"{peak_kind} MEASURED_PEAKS")}
+        if k == "near":
+            r["executed_tflops"] = 2 * pairs * NEAR_FLOPS_EXECUTED_PER_ORDERED_PAIR / 1e12 / (stage_ms[k] / 1e3)
+        return r
 
     roof = roofline(dom) if dom in models else None
     roof_all = [roofline(k) for k in models if k in stage_ms and stage_ms[k] > 0]
@@ -734,9 +820,7 @@ def main():
             "cpu_baseline_ankh": cpu_ankh,
             "e2e": {"value": world * args.e2e_steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            # per step: bin, 2 scans, scatter, leaf sort, gather, k = 0 term, P2M,
-            # merge, spectral, split, correction, near, node potentials, L2P, reduce
-            "gpu_launches": 16 * args.steps,
+            "gpu_launches": launches_per_step(ncell, args.plain) * args.steps,
         }
         print(json.dumps(line), flush=True)
     model.close()

@@ -213,18 +213,22 @@ int ankh_stage_times(const ankh_handle *h, double ms[ANKH_NUM_STAGES]);
  * counterpart: this entry point exists for callers that cannot call
  * cudaMalloc (an engine that plans all device memory at start-up, code that
  * runs while its stream is captured into a CUDA graph, a host whose device
- * allocator belongs to another runtime).  It runs the same kernels as the
- * sort stage of ankh_energy, with its scratch in a static device array of
- * the library instead of allocated memory.
+ * allocator belongs to another runtime).  Its output equals the output of the
+ * sort stage of ankh_energy (the leaf of each atom by the correctly rounded
+ * FP64 chain of that stage, without its FP32 screen, then the stable radix
+ * sort by leaf), with its scratch in a static device array of the library
+ * instead of allocated memory.
  *   x: N x 3 device positions; n_cells leaves per axis of a cubic box of edge
  *   box_edge; outputs (device, caller-owned): perm[N] = atom index of each
  *   sorted slot (ordered by leaf, then by atom index), leaf_start[n^3 + 1] =
- *   first slot of each leaf.
+ *   first slot of each leaf.  The cost per atom does not depend on how the
+ *   atoms are spread over the leaves (all of them in one leaf included).
  *   Limits: N <= ANKH_NOALLOC_MAX_ATOMS, n_cells^3 <= ANKH_NOALLOC_MAX_LEAVES;
  *   larger sizes return ANKH_EINVAL with a message naming the limit.
- *   The static array (9 MiB + 256 B) is held by every GPU that loads the
- *   library until the process exits.  The first call on a device looks up
- *   the array's device address (cudaGetSymbolAddress); make that first call
+ *   The static array (11 MiB) is held by every GPU that loads the library
+ *   until the process exits.  Every call looks up the array's device address
+ *   on the current device (cudaGetSymbolAddress); the first call on a device
+ *   also loads the library's device code there, so make that first call
  *   before any stream capture.  All calls share the one array, which keeps
  *   the last call's contents: each call clears what must start at zero, but
  *   calls that overlap on the GPU (other streams, other threads) race.
@@ -234,6 +238,14 @@ int ankh_stage_times(const ankh_handle *h, double ms[ANKH_NUM_STAGES]);
 #define ANKH_NOALLOC_MAX_LEAVES 262144
 int ankh_bin_sort_noalloc(const float *x, int64_t N, double box_edge, int n_cells, int32_t *perm,
                           int32_t *leaf_start, void *cuda_stream);
+
+/* Measurement utility (not part of the method): the FP32 FMA throughput of
+ * the current device in TFLOP/s (FMA = 2 flop), measured with CUDA events
+ * over ten launches of independent FMA chains (8 blocks of 256 threads per
+ * multiprocessor) on cuda_stream, after three warm-up launches; *ms (may be
+ * NULL) receives the time of one launch.  It is the denominator of the near
+ * field's roofline.  Synchronises the stream. */
+int ankh_measure_fp32_peak(double *tflops, double *ms, void *cuda_stream);
 
 /* Free everything the handle owns.  NULL is ignored. */
 void ankh_destroy(ankh_handle *h);

@@ -31,7 +31,7 @@ EXPORTED = ["ankh_default_params", "ankh_create", "ankh_energy", "ankh_energy_fo
             "ankh_energy_forces_host", "ankh_last_terms", "ankh_get_info", "ankh_debug_copy",
             "ankh_ldm", "ankh_set_timing", "ankh_stage_times", "ankh_bin_sort_noalloc", "ankh_destroy",
             "ankh_last_error", "ankh_version", "ankh_create_batch", "ankh_energy_forces_batch",
-            "ankh_batch_box", "ankh_destroy_batch", "ankh_induce"]
+            "ankh_batch_box", "ankh_destroy_batch", "ankh_induce", "ankh_measure_fp32_peak"]
 STAGES = ["sort", "self", "p2m", "merge", "fft_fwd", "spectral", "corr", "near", "fft_inv", "l2p",
           "unused", "reduce"]
 
@@ -111,6 +111,8 @@ def load_library(path: str = LIB_PATH):
         lib.ankh_destroy.restype = None
         lib.ankh_last_error.argtypes = []
         lib.ankh_last_error.restype = ctypes.c_char_p
+        lib.ankh_measure_fp32_peak.argtypes = [dp, dp, vp]
+        lib.ankh_measure_fp32_peak.restype = ctypes.c_int
         lib.ankh_version.argtypes = []
         lib.ankh_version.restype = ctypes.c_int
         _lib = lib
@@ -235,6 +237,13 @@ def ankh_stage_times(h) -> dict:
     t = (ctypes.c_double * len(STAGES))()
     _check(load_library().ankh_stage_times(h, t))
     return dict(zip(STAGES, list(t)))
+
+
+def ankh_measure_fp32_peak(stream=None) -> tuple[float, float]:
+    """FP32 FMA throughput of the current device: (TFLOP/s, ms per launch)."""
+    t, ms = ctypes.c_double(), ctypes.c_double()
+    _check(load_library().ankh_measure_fp32_peak(ctypes.byref(t), ctypes.byref(ms), _stream_ptr(stream)))
+    return t.value, ms.value
 
 
 def ankh_bin_sort_noalloc(x, box_edge: float, n_cells: int, perm, leaf_start, stream=None) -> None:

@@ -172,7 +172,8 @@ static int choose_n_fmm(double box)
 static void free_device(Handle *H)
 {
     if (!H) return;
-    void *ptrs[] = {H->d_cellid, H->d_rank, H->d_count, H->d_start, H->d_perm, H->d_inv, H->d_loc, H->d_ctr, H->d_scell, H->d_flag, H->d_bsum,
+    void *ptrs[] = {H->d_cellid, H->rsb.vtmp[0], H->rsb.vtmp[1], H->rsb.hist, H->rsb.goff, H->rsb.bsum,
+                    H->d_items, H->d_nitems, H->d_count, H->d_start, H->d_perm, H->d_inv, H->d_loc, H->d_ctr, H->d_scell, H->d_flag, H->d_bsum,
                     H->d_A0, H->d_A1, H->d_A2, H->d_A3, H->d_W, H->d_M, H->d_rho, H->d_rhohat, H->d_D,
                     H->d_phi, H->d_C, H->d_Chi, H->d_Clo, H->d_psi, H->d_gnear, H->d_pi, H->d_part,
                     H->d_partoff, H->d_rscr, H->d_ticket, H->d_terms, H->d_hostbuf, H->d_Mhi, H->d_Mlo, H->d_mmax, H->d_ind, H->d_ind_part};
@@ -324,6 +325,11 @@ int ankh_create(double box_edge, int64_t N, const ankh_params *params, ankh_hand
     Handle &H = hh->h;
     std::memset(&H, 0, sizeof(Handle));
     cudaGetDevice(&H.device);
+    if (cudaDeviceGetAttribute(&H.sm_count, cudaDevAttrMultiProcessorCount, H.device) != cudaSuccess ||
+        H.sm_count <= 0) {
+        delete hh;
+        return fail(ANKH_ECUDA, "cudaDeviceGetAttribute (multiprocessor count)");
+    }
     H.N = N;
     H.max_order = p.max_order;
     H.flags = p.flags;
@@ -362,10 +368,19 @@ int ankh_create(double box_edge, int64_t N, const ankh_params *params, ankh_hand
 
     const int64_t nspec = (int64_t)g.nf * g.nf * g.nfh;
     ANKH_AL(H.d_cellid, N);
-    ANKH_AL(H.d_rank, N);
     ANKH_AL(H.d_count, g.ncell);
     ANKH_AL(H.d_start, g.ncell + 1);
-    ANKH_AL(H.d_bsum, (g.ncell + 1023) / 1024 + 1);
+    ANKH_AL(H.d_bsum, 2 * ((g.ncell + 1023) / 1024) + 2);   // count and item totals of the leaf scan
+    H.max_items = (int)std::min<int64_t>((int64_t)g.ncell + (N + kNearItemTargets - 1) / kNearItemTargets,
+                                         (int64_t)1 << 30);
+    ANKH_AL(H.d_items, H.max_items);
+    ANKH_AL(H.d_nitems, 1);
+    H.rs = radix_plan(N, g.ncell);
+    ANKH_AL(H.rsb.vtmp[0], N);
+    if (H.rs.npass > 2) ANKH_AL(H.rsb.vtmp[1], N);
+    ANKH_AL(H.rsb.hist, H.rs.hist_len);
+    ANKH_AL(H.rsb.goff, H.rs.hist_len + 1);
+    ANKH_AL(H.rsb.bsum, H.rs.bsum_len);
     ANKH_AL(H.d_perm, N);
     ANKH_AL(H.d_inv, N);
     ANKH_AL(H.d_loc, N);

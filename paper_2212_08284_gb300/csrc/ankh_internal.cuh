@@ -35,6 +35,25 @@ struct Geo {
     float Kf;         // n / L rounded to FP32 (the binning's FP32 screen)
 };
 
+// Near-field work items: a leaf's targets in chunks of at most this many
+// (one warp each), laid out by the leaf-count scan.
+constexpr int kNearItemTargets = 32;
+
+// Stable LSD radix sort of the atoms by leaf id (k_sort.cu).
+struct RadixPlan {
+    int npass;              // 1 .. 3 digit passes, lowest digit first
+    int bits[3], shift[3];  // digit width (<= 10 bits) and position of each pass
+    int ntiles;             // tiles of 4096 consecutive elements
+    int64_t hist_len;       // largest 2^bits * ntiles over the passes
+    int bsum_len;           // block totals of the histogram scan
+};
+struct RadixBufs {
+    int *vtmp[2];           // [N] values between passes (vtmp[1] only for three passes)
+    int *hist, *goff;       // [hist_len] digit counts per tile, [hist_len + 1] their exclusive scan
+    int *bsum;              // block totals of the scans
+};
+RadixPlan radix_plan(int64_t N, int ncell);
+
 // Pipeline stages (for the optional per-stage timing)
 enum Stage { kStSort = 0, kStSelf, kStP2M, kStMerge, kStFFTf, kStSpectral, kStCorr, kStNear, kStFFTi,
              kStL2P, kStUnused, kStReduce, kNumStages };
@@ -104,12 +123,18 @@ struct Handle {
     int max_order;
     unsigned flags;
     int device;
+    int sm_count;           // multiprocessors of the device (grid sizing)
     double D0;              // k = 0 value of the far-field kernel spectrum (FP64)
     double precompute_ms;
     int64_t device_bytes;
 
     // atoms (sorted by leaf)
-    int *d_cellid, *d_rank, *d_count, *d_start, *d_perm, *d_scell, *d_flag, *d_bsum;
+    int *d_cellid, *d_count, *d_start, *d_perm, *d_scell, *d_flag, *d_bsum;
+    int2 *d_items;          // near-field work items (leaf, first target), laid out by the leaf-count scan
+    int *d_nitems;          // number of items of the call
+    int max_items;          // ncell + ceil(N / kNearItemTargets): bound on the items of any input
+    RadixPlan rs;           // leaf sort
+    RadixBufs rsb;
     int *d_inv;             // [N] sorted slot of each atom (inverse of perm)
     float4 *d_loc;          // [N] coordinates relative to the leaf centre (caller's order)
     float2 *d_ctr;          // [3n] leaf centres -r_B + (c + 1/2) h, c = -n .. 2n-1, as FP32 hi + lo
@@ -157,8 +182,10 @@ cudaError_t launch_bin(Handle &H, const float *x, cudaStream_t s);
 cudaError_t launch_scan(Handle &H, cudaStream_t s);
 cudaError_t launch_scatter_sort_gather(Handle &H, const float *x, const float *q, const float *mu,
                                        const float *theta, cudaStream_t s);
-cudaError_t launch_bin_sort_raw(int N, const float *x, const Geo &g, int *cellid, int *rank, int *count,
-                                int *flag, int *start, int *perm, cudaStream_t s);
+cudaError_t launch_radix(int N, const int *cellid, const RadixPlan &rp, const RadixBufs &b, int *perm, int *inv,
+                         cudaStream_t s);
+cudaError_t launch_bin_sort_raw(int N, const float *x, const Geo &g, int *cellid, int *count, int *flag,
+                                const RadixPlan &rp, const RadixBufs &b, int *start, int *perm, cudaStream_t s);
 cudaError_t launch_p2m(Handle &H, cudaStream_t s);
 cudaError_t launch_fine_gather(Handle &H, cudaStream_t s);
 cudaError_t launch_spectral(Handle &H, bool forces, cudaStream_t s);

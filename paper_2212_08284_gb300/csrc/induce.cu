@@ -19,7 +19,10 @@ namespace ankh {
 
 constexpr int kIndThreads = 256;
 
-int induce_blocks(int64_t n3) { return (int)std::min<int64_t>((n3 + kIndThreads - 1) / kIndThreads, 152 * 8); }
+int induce_blocks(int64_t n3, int sm_count)
+{
+    return (int)std::min<int64_t>((n3 + kIndThreads - 1) / kIndThreads, (int64_t)sm_count * 8);
+}
 
 __device__ __forceinline__ double ind_block_sum(double v, double *sh)
 {
@@ -156,18 +159,18 @@ int induce_dipoles(Handle &H, const float *x, const float *q, const float *mu, c
                    cudaStream_t s, std::string &err)
 {
     const int64_t N = H.N, n3 = 3 * N;
-    const int nb = induce_blocks(n3);
+    const int nb = induce_blocks(n3, H.sm_count);
     if (!H.d_ind) {
         // workspace: F, r, z, p, Ap, dE/dmu (3N each), zero charges (N), partials
         if (cudaMalloc(&H.d_ind, sizeof(float) * (6 * n3 + N)) != cudaSuccess) {
             err = "cudaMalloc induced-dipole workspace";
             return ANKH_ENOMEM;
         }
-        if (cudaMalloc(&H.d_ind_part, sizeof(double) * 3 * 152 * 8) != cudaSuccess) {
+        if (cudaMalloc(&H.d_ind_part, sizeof(double) * 3 * H.sm_count * 8) != cudaSuccess) {
             err = "cudaMalloc induced-dipole partials";
             return ANKH_ENOMEM;
         }
-        H.device_bytes += (int64_t)sizeof(float) * (6 * n3 + N) + (int64_t)sizeof(double) * 3 * 152 * 8;
+        H.device_bytes += (int64_t)sizeof(float) * (6 * n3 + N) + (int64_t)sizeof(double) * 3 * H.sm_count * 8;
         if (cudaMemset(H.d_ind + 6 * n3, 0, sizeof(float) * N) != cudaSuccess) {
             err = "cudaMemset zero charges";
             return ANKH_ECUDA;

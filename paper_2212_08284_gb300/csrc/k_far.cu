@@ -74,8 +74,7 @@ k_spectral(Geo g, cufftComplex *__restrict__ rh, const float *__restrict__ D, in
 
 int spectral_blocks(const Handle &H)
 {
-    (void)H;
-    return 152 * 4;
+    return H.sm_count * 4;
 }
 
 cudaError_t launch_spectral(Handle &H, bool forces, cudaStream_t s)

@@ -28,7 +28,9 @@
 // R = Theta_i r, u_i = r.R:
 //   F = tr(Theta_i) W + 2 Theta_i W + u_i (Z - r A3) + r (2 R.Z - Theta_i:Y) - 2 Y R.
 //
-// Work layout: one warp per target leaf.  The atoms of the 27 leaves around
+// Work layout: one warp per work item, an item being up to 32 targets of one
+// leaf (the leaf-count scan lays the items out in leaf order, so a leaf with
+// many atoms is spread over many warps).  The atoms of the 27 leaves around
 // it are staged in shared memory (chunks of 64, coordinates shifted by the
 // leaf offset); the warp's lanes are split into G = 32 / n_t groups, lane
 // (i, g) accumulating target i over sources g, g + G, ...; the group partials
@@ -57,10 +59,11 @@ enum { kErfcLib = 0, kSeriesLong = 1, kSeriesShort = 2 };
 
 constexpr int kNearWarps = 4;
 constexpr int kNearChunk = 64;
-// Leaves per warp: the launch covers the leaves with ncell / (4 kNearWarps)
-// blocks, which the hardware hands to the SMs as earlier blocks retire.  A
-// persistent grid (a fixed share of leaves per warp) left the SMs idle at the
-// end, waiting for the warps that drew the heaviest leaves.
+// Items per warp: the launch covers the largest possible item count with
+// max_items / (4 kNearWarps) blocks, which the hardware hands to the SMs as
+// earlier blocks retire.  A persistent grid (a fixed share of leaves per
+// warp) left the SMs idle at the end, waiting for the warps that drew the
+// heaviest leaves.
 constexpr int kNearLeavesPerWarp = 4;
 
 template <bool FORCES>
@@ -159,7 +162,8 @@ __device__ __forceinline__ void src_fields(float rx, float ry, float rz, const f
 
 template <bool FORCES, int MODE>
 __global__ void __launch_bounds__(kNearWarps * 32, 7)
-k_near(Geo g, const int *__restrict__ start, const float4 *__restrict__ A0, const float4 *__restrict__ A1,
+k_near(Geo g, const int *__restrict__ start, const int2 *__restrict__ items, const int *__restrict__ nitems,
+       const float4 *__restrict__ A0, const float4 *__restrict__ A1,
        const float4 *__restrict__ A2, const float4 *__restrict__ A3, BCoef bc, float *__restrict__ gnear,
        int64_t Nslot, double *__restrict__ part, int *__restrict__ flag)
 {
@@ -173,9 +177,11 @@ k_near(Geo g, const int *__restrict__ start, const float4 *__restrict__ A0, cons
     const int n = g.n;
     const float h = g.hf, hlo = g.hf_lo;
     double ew = 0.0;
-    for (int t = blockIdx.x * kNearWarps + warp; t < g.ncell; t += gridDim.x * kNearWarps) {
+    const int nit = *nitems;
+    for (int it = blockIdx.x * kNearWarps + warp; it < nit; it += gridDim.x * kNearWarps) {
+        const int2 item = items[it];
+        const int t = item.x, t0 = item.y;
         const int tb = start[t], nt_all = start[t + 1] - tb;
-        if (nt_all == 0) continue;
         const int cx = t / (n * n), cy = (t / n) % n, cz = t % n;
         // neighbour leaves: begin offsets and exclusive prefix of their counts
         int cnt = 0, beg = 0;
@@ -203,7 +209,7 @@ k_near(Geo g, const int *__restrict__ start, const float4 *__restrict__ A0, cons
         }
         if (lane == 27) sPre[warp][27] = ns;
         __syncwarp();
-        for (int t0 = 0; t0 < nt_all; t0 += 32) {
+        {
             const int nt = min(32, nt_all - t0);
             const int G = 32 / nt;
             const int il = lane % nt, grp = lane / nt;
@@ -325,7 +331,7 @@ int near_blocks(const Handle &H)
 {
     // 7 blocks of 128 threads are resident per SM (<= 73 registers per thread)
     const int per_block = kNearWarps * kNearLeavesPerWarp;
-    return (H.g.ncell + per_block - 1) / per_block;
+    return (H.max_items + per_block - 1) / per_block;
 }
 
 cudaError_t launch_near(Handle &H, bool forces, cudaStream_t s)
@@ -361,8 +367,8 @@ cudaError_t launch_near(Handle &H, bool forces, cudaStream_t s)
     const int64_t S = H.N;
     const dim3 grid(nb), block(kNearWarps * 32);
 #define ANKH_NEAR_LAUNCH(F, M) \
-    k_near<F, M><<<grid, block, 0, s>>>(H.g, H.d_start, H.d_A0, H.d_A1, H.d_A2, H.d_A3, bc, H.d_gnear, S, part, \
-                                        H.d_flag)
+    k_near<F, M><<<grid, block, 0, s>>>(H.g, H.d_start, H.d_items, H.d_nitems, H.d_A0, H.d_A1, H.d_A2, H.d_A3, bc, \
+                                        H.d_gnear, S, part, H.d_flag)
     if (forces) {
         if (mode == kSeriesShort) ANKH_NEAR_LAUNCH(true, kSeriesShort);
         else if (mode == kSeriesLong) ANKH_NEAR_LAUNCH(true, kSeriesLong);

@@ -4,9 +4,11 @@
 // Bit-exact contract: the leaf of atom i is computed in correctly rounded
 // FP64 without fused operations,
 //     s = (x + r_B) * (1/L);  s = s - floor(s);  c = min(floor(s * n), n - 1),
-// and the atoms are ordered by (leaf, original index).  Counting uses
-// atomics (any order), then each leaf's slots are sorted by atom index, so the
-// final permutation is deterministic.
+// and the atoms are ordered by (leaf, original index).  The leaf counts use
+// atomics (sums: any order gives the same counts); the order is a stable LSD
+// radix sort of the atom indices keyed on the leaf id, whose cost per atom is
+// the same however the atoms are spread over the leaves (one leaf holding
+// every atom included), and whose result is unique.
 #include "ankh_internal.cuh"
 
 namespace ankh {
@@ -23,7 +25,7 @@ __device__ __forceinline__ int leaf_coord(double xv, const Geo &g, double *frac_
 }
 
 __global__ void k_bin(int N, const float *__restrict__ x, Geo g, int *__restrict__ cellid,
-                      int *__restrict__ rank, int *__restrict__ count, int *__restrict__ flag)
+                      int *__restrict__ count, int *__restrict__ flag)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -39,7 +41,7 @@ __global__ void k_bin(int N, const float *__restrict__ x, Geo g, int *__restrict
     if (bad) atomicOr(flag, 1);
     int cell = (c[0] * g.n + c[1]) * g.n + c[2];
     cellid[i] = cell;
-    rank[i] = atomicAdd(&count[cell], 1);
+    atomicAdd(&count[cell], 1);
 }
 
 // FP32 screen in front of the FP64 chain (GB300's FP64 rate made the chain
@@ -73,8 +75,8 @@ __device__ __forceinline__ bool leaf_coord_fast(float x, const Geo &g, const flo
 // (FP64, rounded once to FP32; x - centre in FP32 on the fast path), for the
 // move into leaf order.
 __global__ void k_bin_loc(int N, const float *__restrict__ x, Geo g, const float2 *__restrict__ ctr,
-                          int *__restrict__ cellid, int *__restrict__ rank, int *__restrict__ count,
-                          int *__restrict__ flag, float4 *__restrict__ loc)
+                          int *__restrict__ cellid, int *__restrict__ count, int *__restrict__ flag,
+                          float4 *__restrict__ loc)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -95,7 +97,7 @@ __global__ void k_bin_loc(int N, const float *__restrict__ x, Geo g, const float
     int cell = (c[0] * g.n + c[1]) * g.n + c[2];
     cellid[i] = cell;
     loc[i] = make_float4(l[0], l[1], l[2], 0.f);
-    rank[i] = atomicAdd(&count[cell], 1);
+    atomicAdd(&count[cell], 1);
 }
 
 // Non-periodic box (no wrapping): s = (x + r_B) * (1/L) must lie in [0, 1);
@@ -113,8 +115,8 @@ __device__ __forceinline__ int leaf_coord_np(double xv, const Geo &g, double *fr
 }
 
 __global__ void k_bin_np(int N, const float *__restrict__ x, Geo g, const float2 *__restrict__ ctr,
-                         int *__restrict__ cellid, int *__restrict__ rank, int *__restrict__ count,
-                         int *__restrict__ flag, float4 *__restrict__ loc)
+                         int *__restrict__ cellid, int *__restrict__ count, int *__restrict__ flag,
+                         float4 *__restrict__ loc)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -147,49 +149,10 @@ __global__ void k_bin_np(int N, const float *__restrict__ x, Geo g, const float2
     int cell = (c[0] * g.n + c[1]) * g.n + c[2];
     cellid[i] = cell;
     loc[i] = make_float4(l[0], l[1], l[2], 0.f);
-    rank[i] = atomicAdd(&count[cell], 1);
+    atomicAdd(&count[cell], 1);
 }
 
-// Exclusive scan of the per-leaf counts (single block, 1024 threads).
-__global__ void k_scan(int ncell, const int *__restrict__ count, int *__restrict__ start)
-{
-    __shared__ int warp_tot[32];
-    const int nt = blockDim.x;
-    const int tid = threadIdx.x;
-    const int chunk = (ncell + nt - 1) / nt;
-    const int b = min(tid * chunk, ncell), e = min(b + chunk, ncell);
-    int sum = 0;
-    for (int k = b; k < e; ++k) sum += count[k];
-    // inclusive warp scan
-    int v = sum;
-    const int lane = tid & 31, wid = tid >> 5;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int t = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += t;
-    }
-    if (lane == 31) warp_tot[wid] = v;
-    __syncthreads();
-    if (wid == 0) {
-        int w = (lane < (nt >> 5)) ? warp_tot[lane] : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int t = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += t;
-        }
-        warp_tot[lane] = w;
-    }
-    __syncthreads();
-    int excl = v - sum + (wid > 0 ? warp_tot[wid - 1] : 0);
-    for (int k = b; k < e; ++k) {
-        start[k] = excl;
-        excl += count[k];
-    }
-    if (tid == nt - 1) start[ncell] = excl;
-}
-
-// Multi-block exclusive scan: (1) per-block totals, (2) every block adds the
-// totals of the blocks before it and scans its own 1024 counts.
+// Exclusive scan of a block of 1024 values; *total = the block's sum.
 __device__ __forceinline__ int block_excl_scan_1024(int v, int *warp_tot, int *total)
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -215,78 +178,228 @@ __device__ __forceinline__ int block_excl_scan_1024(int v, int *warp_tot, int *t
     return x - v + (wid > 0 ? warp_tot[wid - 1] : 0);
 }
 
-__global__ void __launch_bounds__(1024) k_scan_totals(int ncell, const int *__restrict__ count, int *__restrict__ bsum)
+// Sum of bsum[0 .. nb) by the first warp (for the base of block nb).
+__device__ __forceinline__ int warp_prefix_total(const int *__restrict__ bsum, int nb)
+{
+    int s = 0;
+    for (int b = (int)(threadIdx.x & 31); b < nb; b += 32) s += bsum[b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// Multi-block exclusive scan of len values: (1) per-block totals, (2) every
+// block adds the totals of the blocks before it and scans its own 1024 values;
+// out[len] = the total.
+__global__ void __launch_bounds__(1024) k_scan_totals(int len, const int *__restrict__ v, int *__restrict__ bsum)
 {
     __shared__ int wt[32];
     const int i = blockIdx.x * 1024 + threadIdx.x;
     int tot;
-    block_excl_scan_1024(i < ncell ? count[i] : 0, wt, &tot);
+    block_excl_scan_1024(i < len ? v[i] : 0, wt, &tot);
     if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
 }
 
-__global__ void __launch_bounds__(1024) k_scan_apply(int ncell, const int *__restrict__ count,
-                                                     const int *__restrict__ bsum, int *__restrict__ start)
+__global__ void __launch_bounds__(1024) k_scan_apply(int len, const int *__restrict__ v,
+                                                     const int *__restrict__ bsum, int *__restrict__ out)
 {
     __shared__ int wt[32];
     __shared__ int base;
     if (threadIdx.x < 32) {
-        int s = 0;
-        for (int b = threadIdx.x; b < (int)blockIdx.x; b += 32) s += bsum[b];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        const int s = warp_prefix_total(bsum, (int)blockIdx.x);
         if (threadIdx.x == 0) base = s;
     }
     const int i = blockIdx.x * 1024 + threadIdx.x;
-    const int c = i < ncell ? count[i] : 0;
+    const int c = i < len ? v[i] : 0;
     int tot;
     const int ex = block_excl_scan_1024(c, wt, &tot);
+    if (i < len) out[i] = base + ex;
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 1023) out[len] = base + tot;
+}
+
+// Scan of the leaf counts that also lays out the near-field work items: leaf
+// t with c_t atoms gives ceil(c_t / kNearItemTargets) items (t, first target),
+// in leaf order, so a leaf holding many atoms is spread over many warps.
+// bsum holds the per-block count totals, then the per-block item totals.
+__global__ void __launch_bounds__(1024) k_leafscan_totals(int ncell, const int *__restrict__ count,
+                                                          int *__restrict__ bsum)
+{
+    __shared__ int wt[32];
+    const int i = blockIdx.x * 1024 + threadIdx.x;
+    const int c = i < ncell ? count[i] : 0;
+    int tc, ti;
+    block_excl_scan_1024(c, wt, &tc);
     __syncthreads();
-    if (i < ncell) start[i] = base + ex;
-    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 1023) start[ncell] = base + tot;
-}
-
-__global__ void k_scatter(int N, const int *__restrict__ cellid, const int *__restrict__ rank,
-                          const int *__restrict__ start, int *__restrict__ perm)
-{
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    perm[start[cellid[i]] + rank[i]] = i;
-}
-
-// One thread per leaf: insertion sort of its slots by original atom index.
-__global__ void k_leafsort(int ncell, const int *__restrict__ start, int *__restrict__ perm)
-{
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncell) return;
-    int b = start[c], e = start[c + 1];
-    for (int k = b + 1; k < e; ++k) {
-        int v = perm[k];
-        int j = k - 1;
-        while (j >= b && perm[j] > v) {
-            perm[j + 1] = perm[j];
-            --j;
-        }
-        perm[j + 1] = v;
+    block_excl_scan_1024((c + kNearItemTargets - 1) / kNearItemTargets, wt, &ti);
+    if (threadIdx.x == 0) {
+        bsum[blockIdx.x] = tc;
+        bsum[gridDim.x + blockIdx.x] = ti;
     }
 }
 
-// Same, and the inverse permutation inv[perm[k]] = k (slot of each atom).
-__global__ void k_leafsort_inv(int ncell, const int *__restrict__ start, int *__restrict__ perm,
-                               int *__restrict__ inv)
+__global__ void __launch_bounds__(1024) k_leafscan_apply(int ncell, const int *__restrict__ count,
+                                                         const int *__restrict__ bsum, int *__restrict__ start,
+                                                         int2 *__restrict__ items, int *__restrict__ nitems)
 {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncell) return;
-    int b = start[c], e = start[c + 1];
-    for (int k = b + 1; k < e; ++k) {
-        int v = perm[k];
-        int j = k - 1;
-        while (j >= b && perm[j] > v) {
-            perm[j + 1] = perm[j];
-            --j;
-        }
-        perm[j + 1] = v;
+    __shared__ int wt[32];
+    __shared__ int base[2];
+    if (threadIdx.x < 64) {
+        const int w = threadIdx.x >> 5;
+        const int s = warp_prefix_total(bsum + w * gridDim.x, (int)blockIdx.x);
+        if ((threadIdx.x & 31) == 0) base[w] = s;
     }
-    for (int k = b; k < e; ++k) inv[perm[k]] = k;
+    const int i = blockIdx.x * 1024 + threadIdx.x;
+    const int c = i < ncell ? count[i] : 0;
+    const int ch = (c + kNearItemTargets - 1) / kNearItemTargets;
+    int tc, ti;
+    const int exc = block_excl_scan_1024(c, wt, &tc);
+    __syncthreads();
+    const int exi = block_excl_scan_1024(ch, wt, &ti);
+    if (i < ncell) {
+        start[i] = base[0] + exc;
+        const int io = base[1] + exi;
+        for (int j = 0; j < ch; ++j) items[io + j] = make_int2(i, j * kNearItemTargets);
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 1023) {
+        start[ncell] = base[0] + tc;
+        *nitems = base[1] + ti;
+    }
+}
+
+// Stable LSD radix sort of the atom indices by leaf id.  Pass p orders by the
+// digit (id >> shift_p) & (2^bits_p - 1), lowest digit first; each pass is
+// stable, so the result is ordered by (leaf, atom index).  The input is cut
+// into tiles of kRsTile consecutive elements:
+//   k_rs_hist     per-tile digit counts, stored digit-major: hist[d][tile];
+//   scan          exclusive scan of hist: the first output slot of each
+//                 (digit, tile), all earlier tiles' elements of that digit first;
+//   k_rs_scatter  the rank of each element among the tile's elements of its
+//                 digit, in index order: each warp walks 32 consecutive
+//                 elements at a time, groups equal digits with a match
+//                 (lanes in order), and keeps per-warp digit counts in shared
+//                 memory; the warps' counts are then prefixed in warp order.
+// Keys are read as cellid[value] (the value is the atom index), so only the
+// values move.  Every element costs the same whatever the leaf occupancy.
+constexpr int kRsThreads = 256;
+constexpr int kRsWarps = kRsThreads / 32;
+constexpr int kRsRounds = 16;                          // 32-element rounds per warp
+constexpr int kRsTile = kRsWarps * 32 * kRsRounds;     // 4096 elements per tile
+constexpr int kRsMaxBits = 10;                         // <= 36 KB shared memory per scatter block
+
+__global__ void __launch_bounds__(kRsThreads) k_rs_hist(int N, const int *__restrict__ cellid,
+                                                        const int *__restrict__ vin, int shift, int bits,
+                                                        int ntiles, int *__restrict__ hist)
+{
+    extern __shared__ int sh[];
+    const int nb = 1 << bits, mask = nb - 1;
+    for (int d = threadIdx.x; d < nb; d += kRsThreads) sh[d] = 0;
+    __syncthreads();
+    const int base = blockIdx.x * kRsTile;
+    for (int k = threadIdx.x; k < kRsTile; k += kRsThreads) {
+        const int i = base + k;
+        if (i < N) {
+            const int key = cellid[vin ? vin[i] : i];
+            atomicAdd(&sh[(key >> shift) & mask], 1);
+        }
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < nb; d += kRsThreads) hist[(int64_t)d * ntiles + blockIdx.x] = sh[d];
+}
+
+__global__ void __launch_bounds__(kRsThreads) k_rs_scatter(int N, const int *__restrict__ cellid,
+                                                           const int *__restrict__ vin, int shift, int bits,
+                                                           int ntiles, const int *__restrict__ goff,
+                                                           int *__restrict__ vout, int *__restrict__ inv)
+{
+    extern __shared__ int sh[];   // [kRsWarps][nb] per-warp digit counts, then [nb] tile offsets
+    const int nb = 1 << bits, mask = nb - 1;
+    int *wcnt = sh, *toff = sh + kRsWarps * nb;
+    for (int k = threadIdx.x; k < kRsWarps * nb; k += kRsThreads) wcnt[k] = 0;
+    for (int d = threadIdx.x; d < nb; d += kRsThreads) toff[d] = goff[(int64_t)d * ntiles + blockIdx.x];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    int *wc = wcnt + warp * nb;
+    const int base = blockIdx.x * kRsTile + warp * 32 * kRsRounds;
+    int rk[kRsRounds], dg[kRsRounds], val[kRsRounds];
+#pragma unroll
+    for (int r = 0; r < kRsRounds; ++r) {
+        const int i = base + r * 32 + lane;
+        int v = 0, d = -1;   // lanes past the end carry digit -1 and touch nothing
+        if (i < N) {
+            v = vin ? vin[i] : i;
+            d = (cellid[v] >> shift) & mask;
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int c = d >= 0 ? wc[d] : 0;
+        __syncwarp();
+        if (d >= 0 && (peers & below) == 0) wc[d] = c + __popc(peers);   // lowest lane of the group
+        __syncwarp();
+        rk[r] = c + __popc(peers & below);
+        dg[r] = d;
+        val[r] = v;
+    }
+    __syncthreads();
+    // first slot of every (warp, digit): the tile's offset plus the counts of the earlier warps
+    for (int d = threadIdx.x; d < nb; d += kRsThreads) {
+        int run = toff[d];
+        for (int w = 0; w < kRsWarps; ++w) {
+            const int t = wcnt[w * nb + d];
+            wcnt[w * nb + d] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kRsRounds; ++r) {
+        if (dg[r] >= 0) {
+            const int pos = wc[dg[r]] + rk[r];
+            vout[pos] = val[r];
+            if (inv) inv[val[r]] = pos;
+        }
+    }
+}
+
+RadixPlan radix_plan(int64_t N, int ncell)
+{
+    RadixPlan rp;
+    int B = 1;
+    while (B < 31 && ((int64_t)1 << B) < ncell) ++B;   // ids 0 .. ncell - 1 fit in B bits
+    rp.npass = (B + kRsMaxBits - 1) / kRsMaxBits;
+    const int base = B / rp.npass, rem = B % rp.npass;
+    int sh = 0;
+    for (int p = 0; p < 3; ++p) {
+        rp.bits[p] = p < rp.npass ? base + (p < rem ? 1 : 0) : 0;
+        rp.shift[p] = sh;
+        sh += rp.bits[p];
+    }
+    rp.ntiles = (int)((N + kRsTile - 1) / kRsTile);
+    int maxbits = 0;
+    for (int p = 0; p < rp.npass; ++p) maxbits = rp.bits[p] > maxbits ? rp.bits[p] : maxbits;
+    rp.hist_len = ((int64_t)1 << maxbits) * rp.ntiles;
+    rp.bsum_len = (int)((rp.hist_len + 1023) / 1024) + 1;
+    return rp;
+}
+
+cudaError_t launch_radix(int N, const int *cellid, const RadixPlan &rp, const RadixBufs &b, int *perm, int *inv,
+                         cudaStream_t s)
+{
+    const int *vin = nullptr;
+    for (int p = 0; p < rp.npass; ++p) {
+        const bool last = p == rp.npass - 1;
+        int *vout = last ? perm : b.vtmp[p & 1];
+        const int nb = 1 << rp.bits[p];
+        const int len = nb * rp.ntiles;
+        const int sb = (len + 1023) / 1024;
+        k_rs_hist<<<rp.ntiles, kRsThreads, nb * sizeof(int), s>>>(N, cellid, vin, rp.shift[p], rp.bits[p],
+                                                                  rp.ntiles, b.hist);
+        k_scan_totals<<<sb, 1024, 0, s>>>(len, b.hist, b.bsum);
+        k_scan_apply<<<sb, 1024, 0, s>>>(len, b.hist, b.bsum, b.goff);
+        k_rs_scatter<<<rp.ntiles, kRsThreads, (kRsWarps + 1) * nb * sizeof(int), s>>>(
+            N, cellid, vin, rp.shift[p], rp.bits[p], rp.ntiles, b.goff, vout, last ? inv : nullptr);
+        vin = vout;
+    }
+    return cudaGetLastError();
 }
 
 // Move the atoms into leaf order, one thread per atom in the caller's order
@@ -362,19 +475,17 @@ cudaError_t launch_bin(Handle &H, const float *x, cudaStream_t s)
     cudaMemsetAsync(H.d_flag, 0, sizeof(int), s);
     int N = (int)H.N;
     if (H.g.nonperiodic)
-        k_bin_np<<<(N + 255) / 256, 256, 0, s>>>(N, x, H.g, H.d_ctr, H.d_cellid, H.d_rank, H.d_count,
-                                                  H.d_flag, H.d_loc);
+        k_bin_np<<<(N + 255) / 256, 256, 0, s>>>(N, x, H.g, H.d_ctr, H.d_cellid, H.d_count, H.d_flag, H.d_loc);
     else
-        k_bin_loc<<<(N + 255) / 256, 256, 0, s>>>(N, x, H.g, H.d_ctr, H.d_cellid, H.d_rank, H.d_count,
-                                                   H.d_flag, H.d_loc);
+        k_bin_loc<<<(N + 255) / 256, 256, 0, s>>>(N, x, H.g, H.d_ctr, H.d_cellid, H.d_count, H.d_flag, H.d_loc);
     return cudaGetLastError();
 }
 
 cudaError_t launch_scan(Handle &H, cudaStream_t s)
 {
     const int nb = (H.g.ncell + 1023) / 1024;
-    k_scan_totals<<<nb, 1024, 0, s>>>(H.g.ncell, H.d_count, H.d_bsum);
-    k_scan_apply<<<nb, 1024, 0, s>>>(H.g.ncell, H.d_count, H.d_bsum, H.d_start);
+    k_leafscan_totals<<<nb, 1024, 0, s>>>(H.g.ncell, H.d_count, H.d_bsum);
+    k_leafscan_apply<<<nb, 1024, 0, s>>>(H.g.ncell, H.d_count, H.d_bsum, H.d_start, H.d_items, H.d_nitems);
     return cudaGetLastError();
 }
 
@@ -382,9 +493,9 @@ cudaError_t launch_scatter_sort_gather(Handle &H, const float *x, const float *q
                                        const float *theta, cudaStream_t s)
 {
     int N = (int)H.N;
-    k_scatter<<<(N + 255) / 256, 256, 0, s>>>(N, H.d_cellid, H.d_rank, H.d_start, H.d_perm);
-    k_leafsort_inv<<<(H.g.ncell + 127) / 128, 128, 0, s>>>(H.g.ncell, H.d_start, H.d_perm, H.d_inv);
     (void)x;
+    const cudaError_t e = launch_radix(N, H.d_cellid, H.rs, H.rsb, H.d_perm, H.d_inv, s);
+    if (e != cudaSuccess) return e;
     k_gather<<<(N + 255) / 256, 256, 0, s>>>(N, H.d_inv, H.d_cellid, H.d_loc, q, H.max_order >= 1 ? mu : nullptr,
                                               H.max_order >= 2 ? theta : nullptr, H.g, H.d_scell,
                                               H.d_A0, H.d_A1, H.d_A2, H.d_A3, H.d_part + H.part_off[kPartSelf],
@@ -392,20 +503,24 @@ cudaError_t launch_scatter_sort_gather(Handle &H, const float *x, const float *q
     return cudaGetLastError();
 }
 
-// Same kernels on caller-provided buffers (used by the allocation-free entry
-// point): count and flag are cleared here; start receives ncell + 1 offsets.
-cudaError_t launch_bin_sort_raw(int N, const float *x, const Geo &g, int *cellid, int *rank, int *count,
-                                int *flag, int *start, int *perm, cudaStream_t s)
+// The same ordering on caller-provided buffers (the allocation-free entry
+// point), with the FP64 binning chain alone (k_bin): count and flag are
+// cleared here; start receives ncell + 1 offsets; b.bsum must hold
+// max(ceil(ncell / 1024), rp.bsum_len) values.
+cudaError_t launch_bin_sort_raw(int N, const float *x, const Geo &g, int *cellid, int *count, int *flag,
+                                const RadixPlan &rp, const RadixBufs &b, int *start, int *perm, cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * g.ncell, s);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(flag, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
-    k_bin<<<(N + 255) / 256, 256, 0, s>>>(N, x, g, cellid, rank, count, flag);
-    k_scan<<<1, 1024, 0, s>>>(g.ncell, count, start);
-    k_scatter<<<(N + 255) / 256, 256, 0, s>>>(N, cellid, rank, start, perm);
-    k_leafsort<<<(g.ncell + 127) / 128, 128, 0, s>>>(g.ncell, start, perm);
-    return cudaGetLastError();
+    k_bin<<<(N + 255) / 256, 256, 0, s>>>(N, x, g, cellid, count, flag);
+    const int nb = (g.ncell + 1023) / 1024;
+    k_scan_totals<<<nb, 1024, 0, s>>>(g.ncell, count, b.bsum);
+    k_scan_apply<<<nb, 1024, 0, s>>>(g.ncell, count, b.bsum, start);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_radix(N, cellid, rp, b, perm, nullptr, s);
 }
 
 }  // namespace ankh

@@ -50,5 +50,7 @@ def test_batch_matches_single_boxes_and_reference(api):
             assert E1[i] == pytest.approx(o["E"], rel=2e-6)
             gx = g1["dEdx"][off[i]:off[i + 1]].cpu().numpy().astype(np.float64)
             ref = o["grad"][:, :3]
-            assert np.sqrt(np.mean((gx - ref) ** 2)) / np.sqrt(np.mean(ref ** 2)) < 3e-5
+            rms = np.sqrt(np.mean(ref ** 2))
+            assert np.sqrt(np.mean((gx - ref) ** 2)) / rms < 3e-5
+            assert np.max(np.abs(gx - ref)) / rms < 20 * 3e-5
     bt.close()

@@ -35,6 +35,16 @@ def rel_rms(a, b):
     return float(np.sqrt(np.mean((a - b) ** 2)) / max(np.sqrt(np.mean(b ** 2)), 1e-300))
 
 
+def rel_max(a, b):
+    """Largest entry error relative to the RMS value of the reference."""
+    return float(np.max(np.abs(a - b)) / max(np.sqrt(np.mean(b ** 2)), 1e-300))
+
+
+def close_grad(a, b, bar=3e-5):
+    """RMS error within the bar and every entry within 20 times it."""
+    return rel_rms(a, b) <= bar and rel_max(a, b) <= 20 * bar
+
+
 CASES = [  # (n_waters, seed, box, multipoles, n, Lu)
     (216, 11, 18.64, True, 3, 5),
     (216, 11, 18.64, True, 4, 4),
@@ -55,11 +65,11 @@ def test_matches_fp64_nonperiodic_ankh(api, case, mixed):
     o = ar.ankh_energy_nonperiodic(b.x, b.q, b.mu, b.theta, ar.Params(b.box, n, Lu, Lu), grad=True)
     assert E == pytest.approx(o["E"], rel=2e-6)
     ref = o["grad"]
-    assert rel_rms(g["dEdx"].cpu().numpy().astype(np.float64), ref[:, :3]) <= 3e-5
-    assert rel_rms(g["dEdq"].cpu().numpy().astype(np.float64), ref[:, 3]) <= 3e-5
+    assert close_grad(g["dEdx"].cpu().numpy().astype(np.float64), ref[:, :3])
+    assert close_grad(g["dEdq"].cpu().numpy().astype(np.float64), ref[:, 3])
     if mpl:
-        assert rel_rms(g["dEdmu"].cpu().numpy().astype(np.float64), ref[:, 4:7]) <= 3e-5
-        assert rel_rms(g["dEdtheta"].cpu().numpy().astype(np.float64), ref[:, 7:13]) <= 3e-5
+        assert close_grad(g["dEdmu"].cpu().numpy().astype(np.float64), ref[:, 4:7])
+        assert close_grad(g["dEdtheta"].cpu().numpy().astype(np.float64), ref[:, 7:13])
 
 
 def test_against_the_direct_sum(api):
@@ -70,7 +80,7 @@ def test_against_the_direct_sum(api):
     m = api.Ankh(b.box, b.n, n_cells=3, Lu=7, Lc=7, nonperiodic=True)
     E, g = m.energy_forces(*to_dev(b))
     assert E == pytest.approx(Ed, rel=3e-6)
-    assert rel_rms(g["dEdx"].cpu().numpy().astype(np.float64), gd[:, :3]) <= 3e-5
+    assert close_grad(g["dEdx"].cpu().numpy().astype(np.float64), gd[:, :3])
 
 
 def test_energy_only_equals_energy_with_forces(api):

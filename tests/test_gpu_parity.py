@@ -7,7 +7,10 @@ operation accumulated over a few hundred terms per atom and the FP32 FFT):
   * energy vs the literal FP64 ANKH-FFT at the same (n, L_u, L_c, xi):
     relative error <= 2e-6;
   * gradient vs the oracle's analytic adjoint: RMS error <= 3e-5 of the RMS
-    value, per group (dE/dx, dE/dq, dE/dmu, dE/dTheta);
+    value, per group (dE/dx, dE/dq, dE/dmu, dE/dTheta), and every entry
+    within 20 times that bar (6e-4 of the RMS value), so that an error
+    confined to a few atoms (a wrapped leaf, the last near-field chunk, a
+    ragged tensor-core tile) cannot hide in the RMS;
   * vs the FP64 Ewald energy of the workload: relative error <= 1e-5
     (the target of the method), RMS force error <= 1e-4 of the RMS force.
 """
@@ -23,6 +26,7 @@ pytestmark = pytest.mark.gpu
 from oracle import ankh_ref as ar          # noqa: E402
 from oracle import ewald as ew             # noqa: E402
 from paper_2212_08284_gb300 import synth   # noqa: E402
+from cases import face_box                 # noqa: E402
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 
@@ -61,6 +65,16 @@ def rms_rel(a, b):
     return float(np.sqrt(np.mean((a - b) ** 2)) / max(np.sqrt(np.mean(b ** 2)), 1e-300))
 
 
+def max_rel(a, b):
+    """Largest entry error relative to the RMS value of the reference."""
+    return float(np.max(np.abs(a - b)) / max(np.sqrt(np.mean(b ** 2)), 1e-300))
+
+
+def check_gradient(G, ref, bar=3e-5, key=""):
+    assert rms_rel(G, ref) < bar, key
+    assert max_rel(G, ref) < 20 * bar, key
+
+
 GROUPS = {"dEdx": slice(0, 3), "dEdq": slice(3, 4), "dEdmu": slice(4, 7), "dEdtheta": slice(7, 13)}
 
 
@@ -87,24 +101,6 @@ def test_binning_is_bit_exact(api):
     del torch
 
 
-def face_coords(rng, box, n, count, lo, hi):
-    """FP32 coordinates next to the leaf faces k L / n - L / 2, k = lo .. hi:
-    the first half on a face or up to three FP32 steps either side of it, the
-    second half 1 to 4 times n 2^-20 leaf edges away from it (just outside the
-    band that the binning's FP32 screen hands to the FP64 chain)."""
-    k = rng.integers(lo, hi + 1, size=count)
-    h = box / n
-    far = np.arange(count) >= count // 2
-    delta = rng.uniform(1.0, 4.0, size=count) * n * 2.0 ** -20 * h * rng.choice([-1.0, 1.0], size=count)
-    v = (k * h - box / 2 + np.where(far, delta, 0.0)).astype(np.float32)
-    steps = np.where(far, 0, rng.integers(-3, 4, size=count))
-    for s in range(3):
-        up, dn = steps > s, steps < -s
-        v[up] = np.nextafter(v[up], np.float32(np.inf))
-        v[dn] = np.nextafter(v[dn], np.float32(-np.inf))
-    return v
-
-
 @pytest.mark.parametrize("nonperiodic", [False, True], ids=["periodic", "nonperiodic"])
 def test_binning_is_bit_exact_next_to_faces(api, nonperiodic):
     """The leaf binning decides most coordinates with an FP32 screen and the
@@ -112,25 +108,7 @@ def test_binning_is_bit_exact_next_to_faces(api, nonperiodic):
     the FP64 definition bit for bit.  4,000 of the 24,000 atoms get one
     coordinate next to a leaf face (periodic: faces up to one box length
     outside the box, which wrap), on both sides of the screen's band."""
-    b = synth.config_box(2)
-    n = 14
-    rng = np.random.default_rng(2212)
-    count = 4000
-    idx = rng.choice(b.n, size=count, replace=False)
-    axis = rng.integers(0, 3, size=count)
-    fc = face_coords(rng, b.box, n, count, 0 if nonperiodic else -n, n if nonperiodic else 2 * n)
-    if nonperiodic:
-        # keep every atom inside [-L/2, L/2)
-        hi = np.float32(b.box / 2)
-        if float(hi) >= b.box / 2:
-            hi = np.nextafter(hi, np.float32(-np.inf))
-        lo = np.float32(-b.box / 2)
-        if float(lo) < -b.box / 2:
-            lo = np.nextafter(lo, np.float32(np.inf))
-        fc = np.clip(fc, lo, hi)
-    x = b.x.copy()
-    x[idx, axis] = fc
-    b.x = x.astype(np.float32)
+    b, n = face_box(nonperiodic)
     m = api.Ankh(b.box, b.n, n_cells=n, Lu=5, max_order=0, nonperiodic=nonperiodic)
     xd, qd, _, _ = to_dev(b)
     m.energy(xd, qd, None, None)
@@ -161,26 +139,30 @@ def test_modified_charges_match_alg2(api):
 
 
 CASES = [
-    # (name, box factory, n, Lu, Lc, max_order)
-    ("water648_q_n5_Lu5", lambda: synth.config_box(1), 5, 5, 5, 0),
-    ("water648_q_n4_Lu6", lambda: synth.config_box(1), 4, 6, 6, 0),
-    ("water3000_n7_Lu5", lambda: synth.small_box(1000, 31, box=31.1), 7, 5, 5, 2),
-    ("water3000_n8_Lu4", lambda: synth.small_box(1000, 32, box=31.1), 8, 4, 6, 2),
-    ("water1500_n3_Lu3", lambda: synth.small_box(500, 33, box=24.7), 3, 3, 3, 2),
-    ("water24000_n14_Lu5", lambda: synth.config_box(2), 14, 5, 5, 2),
+    # (name, box factory, n, Lu, Lc, max_order, xi)
+    ("water648_q_n5_Lu5", lambda: synth.config_box(1), 5, 5, 5, 0, 0.01),
+    ("water648_q_n4_Lu6", lambda: synth.config_box(1), 4, 6, 6, 0, 0.01),
+    ("water3000_n7_Lu5", lambda: synth.small_box(1000, 31, box=31.1), 7, 5, 5, 2, 0.01),
+    ("water3000_n8_Lu4", lambda: synth.small_box(1000, 32, box=31.1), 8, 4, 6, 2, 0.01),
+    ("water1500_n3_Lu3", lambda: synth.small_box(500, 33, box=24.7), 3, 3, 3, 2, 0.01),
+    ("water24000_n14_Lu5", lambda: synth.config_box(2), 14, 5, 5, 2, 0.01),
+    # the same box with screening large enough for the near field's other B0
+    # evaluations: xi r_max = xi 2 sqrt(3) h = 0.38 (8-term series) and 1.54 (erfcf)
+    ("water3000_n7_Lu5_xi0.025", lambda: synth.small_box(1000, 31, box=31.1), 7, 5, 5, 2, 0.025),
+    ("water3000_n7_Lu6_xi0.1", lambda: synth.small_box(1000, 31, box=31.1), 7, 6, 6, 2, 0.1),
 ]
 
 
 @pytest.mark.parametrize("mixed", [False, True])
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
 def test_energy_and_gradient_match_fp64_ankh(api, case, mixed):
-    name, mk, n, Lu, Lc, order = case
+    name, mk, n, Lu, Lc, order, xi = case
     b = mk()
     if order == 0:
         b.mu[:] = 0
         b.theta[:] = 0
-    m, E, g = run_gpu(api, b, n=n, Lu=Lu, Lc=Lc, max_order=order, mixed=mixed)
-    o = ar.ankh_energy(b.x, b.q, b.mu, b.theta, ar.Params(b.box, n, Lu, Lc))
+    m, E, g = run_gpu(api, b, n=n, Lu=Lu, Lc=Lc, max_order=order, mixed=mixed, xi=xi)
+    o = ar.ankh_energy(b.x, b.q, b.mu, b.theta, ar.Params(b.box, n, Lu, Lc, xi=xi))
     assert E == pytest.approx(o["E"], rel=2e-6)
     t = m.terms()
     assert t["near"] == pytest.approx(o["E_near"], rel=2e-6)
@@ -190,10 +172,10 @@ def test_energy_and_gradient_match_fp64_ankh(api, case, mixed):
     for k, sl in GROUPS.items():
         if order == 0 and k in ("dEdmu", "dEdtheta"):
             continue
-        assert rms_rel(G[:, sl], o["grad"][:, sl]) < 3e-5, k
+        check_gradient(G[:, sl], o["grad"][:, sl], key=k)
     tau = ar.torques(ew.pack_multipoles(b.q, b.mu, b.theta), o["grad"])
     if order > 0:
-        assert rms_rel(g["torque"], tau) < 3e-5
+        check_gradient(g["torque"], tau, key="torque")
 
 
 def golden(name):
