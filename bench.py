@@ -256,6 +256,99 @@ def oracle_sample_nonperiodic(box, nthreads: int | None = None, rows: int = 64):
             "sample_seconds": time.perf_counter() - t0}
 
 
+def oracle_time(box, nthreads=None):
+    """Seconds of one FP64 Ewald energy + gradient evaluation of the box on the
+    host cores: the full oracle for boxes up to 5,000 atoms, else the bounded
+    sample of oracle_sample extrapolated to a full evaluation."""
+    if box.n <= 5000:
+        from oracle import ewald as ew
+        mp = ew.pack_multipoles(box.q, box.mu, box.theta)
+        a = time.perf_counter()
+        ew.ewald(box.x.astype(np.float64), mp, box.box, tol=1e-11, grad=True, nthreads=nthreads)
+        return time.perf_counter() - a, f"FP64 Ewald oracle, full energy + gradient of the {box.n}-atom box"
+    rows, kstride = (500, 400) if nthreads != 1 else (100, 2000)   # bounded: seconds of host time
+    r = oracle_sample(box, nthreads=nthreads, rows=rows, kstride=kstride)
+    return r["seconds_full_eval"], r["sample"]
+
+
+def time_device(fn, steps, flush, stream):
+    """Mean device time of one call: CUDA events on the launch stream around
+    each call, L2 flushed before each, after three warm-up calls."""
+    import torch
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    tot = 0.0
+    for k in range(steps):
+        flush.fill_(float(k))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        tot += e0.elapsed_time(e1) / 1e3
+    return tot / steps
+
+
+def golden_errors(box, E, dEdx=None):
+    """Relative energy error and sampled relative RMS force error against the
+    FP64 Ewald reference of the box (tests/golden), or None without one."""
+    gpath = os.path.join(ROOT, "tests", "golden", f"ewald_{box.name}.json")
+    if not os.path.exists(gpath):
+        return None
+    gd = json.load(open(gpath))
+    acc = {"rel_energy_error": abs(E - gd["E"]) / abs(gd["E"]), "reference": "FP64 Ewald oracle (tests/golden)"}
+    if dEdx is not None:
+        idx = np.array(gd["sample_idx"])
+        ref = np.array(gd["sample_grad"])
+        gx = dEdx.cpu().numpy().astype(np.float64)[idx]
+        acc["rel_rms_force_error_sample"] = float(np.sqrt(np.mean((gx - ref[:, :3]) ** 2)) / gd["rms_all"]["dEdx"])
+    return acc
+
+
+def config_legs(args, dev, api, synth, flush, stream, steps):
+    """The smaller water workloads at the library's default parameters (leaf
+    count and order from its accuracy table): 648 atoms charges only (energy),
+    24,000 atoms q/mu/Theta (energy), 96,000 atoms q/mu/Theta (energy, forces
+    and torques); each with its error against the FP64 Ewald reference and the
+    same-run oracle time on the host cores (and on one core for the two
+    smallest)."""
+    import torch
+    legs = []
+    for c in (1, 2, 3):
+        box = synth.config_box(c)
+        f32 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
+        x, q, mu, th = f32(box.x), f32(box.q), f32(box.mu), f32(box.theta)
+        order = 0 if c == 1 else 2
+        m = api.Ankh(box.box, box.n, n_cells=0, Lu=0, max_order=order)
+        info = m.info
+        forces = c == 3
+        out = {"dEdx": torch.empty((box.n, 3), device=dev), "dEdq": torch.empty(box.n, device=dev),
+               "dEdmu": torch.empty((box.n, 3), device=dev), "dEdtheta": torch.empty((box.n, 6), device=dev),
+               "torque": torch.empty((box.n, 3), device=dev)}
+        if forces:
+            fn = lambda: api.ankh_energy_forces(m.h, x, q, mu, th, sync=False, stream=stream, **out)
+        else:
+            fn = lambda: api.ankh_energy(m.h, x, q, mu, th, stream=stream)
+        t = time_device(fn, steps, flush, stream)
+        E = (api.ankh_energy_forces(m.h, x, q, mu, th, stream=stream, **out) if forces
+             else api.ankh_energy(m.h, x, q, mu, th, stream=stream))
+        m.close()
+        ot, osample = oracle_time(box)
+        rec = {"config": c, "workload": box.name + ("_energy_forces_torques" if forces else "_energy"),
+               "n_atoms": box.n, "box_A": round(box.box, 4), "n_cells": info["n_cells"], "Lu": info["Lu"],
+               "call": "ankh_energy_forces" if forces else "ankh_energy (returns the energy: includes its sync)",
+               "evals_per_s": 1.0 / t, "ms_per_eval": t * 1e3, "matoms_per_s": box.n / t / 1e6,
+               "accuracy": golden_errors(box, E, out["dEdx"] if forces else None),
+               "oracle": {"seconds_per_eval": ot, "cores": os.cpu_count() or 1, "sample": osample}}
+        if c <= 2:
+            ot1, _ = oracle_time(box, nthreads=1)
+            rec["oracle"]["seconds_per_eval_one_core"] = ot1
+        legs.append(rec)
+    return legs
+
+
 def run_reference(args, rank, world):
     """Reference arm: the CPU oracle as it stands, on the host cores."""
     from paper_2212_08284_gb300 import synth
@@ -313,20 +406,23 @@ def max_over_ranks(value, dist, device):
     return float(t.item())
 
 
-def run_replicas(args, rank, world, dev, api, synth, dist=None):
+def replicas_measure(args, rank, world, dev, api, synth, dist=None, steps=None, e2e_steps=None,
+                     cpu_baseline=True):
     """64 independent water boxes of uneven size (3,000-48,000 atoms), one
     batched call (one CUDA graph) per step.  With N ranks the same 64 boxes
     are split by cost (atoms) with LPT, each rank evaluating its share
-    (strong scaling, no data-path collective)."""
+    (strong scaling, no data-path collective).  Returns rank 0's line."""
     import torch
+    steps = steps or args.steps
+    e2e_steps = e2e_steps or args.e2e_steps
     all_boxes = synth.replica_boxes(64)
     mine = lpt_partition([b.n for b in all_boxes], world)[rank]
     boxes = [all_boxes[i] for i in mine]
     if not boxes:
         raise SystemExit("more ranks than boxes")
-    cat = lambda f: torch.from_numpy(np.ascontiguousarray(np.concatenate([f(b) for b in boxes]),
-                                                          dtype=np.float32)).to(dev)
-    x, q, mu, th = cat(lambda b: b.x), cat(lambda b: b.q), cat(lambda b: b.mu), cat(lambda b: b.theta)
+    cat = lambda f: np.ascontiguousarray(np.concatenate([f(b) for b in boxes]), dtype=np.float32)
+    hx, hq, hmu, hth = cat(lambda b: b.x), cat(lambda b: b.q), cat(lambda b: b.mu), cat(lambda b: b.theta)
+    x, q, mu, th = (torch.from_numpy(a).to(dev) for a in (hx, hq, hmu, hth))
     ntot = int(x.shape[0])
     bt = api.AnkhBatch([b.box for b in boxes], [b.n for b in boxes], Lu=args.Lu, mixed=not args.plain)
     out = {"dEdx": torch.empty((ntot, 3), device=dev), "dEdq": torch.empty(ntot, device=dev),
@@ -343,7 +439,7 @@ def run_replicas(args, rank, world, dev, api, synth, dist=None):
     torch.cuda.synchronize()
     clocks.mark("timed_start")
     tot = 0.0
-    for k in range(args.steps):
+    for k in range(steps):
         flush.fill_(float(k))
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -358,21 +454,79 @@ def run_replicas(args, rank, world, dev, api, synth, dist=None):
     if dist:
         dist.barrier()
     tot = max_over_ranks(tot, dist, dev)
-    value = 64 * args.steps / tot
+    value = 64 * steps / tot
     ntot_all = sum(b.n for b in all_boxes)
-    if rank == 0:
-        print(json.dumps({
-            "metric": METRIC, "value": value, "unit": "box-evals/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": tot / args.steps * 1e3, "higher_is_better": True,
-            "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "replicas64_water_3000_48000_qmuTheta_energy_forces", "n_boxes": 64,
-                       "n_atoms_total": ntot_all, "Lu": args.Lu, "l2": "flushed: 256 MiB write between timed steps",
-                       "execution": "one CUDA graph per rank, one branch per box",
-                       "parallelism": f"boxes split over {world} GPU(s) by LPT on atom counts"},
-            "matoms_per_s": value / 64 * ntot_all / 1e6, "clocks": clk, "roofline": None, "cpu_baseline": None,
-            "e2e": None, "gpu_launches": sum(launches_per_step(batch_box_cells(api, bt, i) ** 3, args.plain)
-                                             for i in range(len(boxes))) * args.steps}), flush=True)
+
+    # end to end: the host arrays copied in (pinned), the batch call, the
+    # gradients copied back, every step
+    pin = lambda a: torch.from_numpy(a).pin_memory()
+    px, pq, pmu, pth = pin(hx), pin(hq), pin(hmu), pin(hth)
+    ho = {k: torch.empty(tuple(v.shape), dtype=torch.float32).pin_memory() for k, v in out.items()}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for d_, h_ in ((x, px), (q, pq), (mu, pmu), (th, pth)):
+            d_.copy_(h_, non_blocking=True)
+        bt.energy_forces(x, q, mu, th, out=out)
+        for k_, v_ in out.items():
+            ho[k_].copy_(v_, non_blocking=True)
+        torch.cuda.synchronize()
+    t_e2e = max_over_ranks(time.perf_counter() - t0, dist, dev)
+
+    # near field over all boxes against the measured FP32 peak: a lower bound
+    # of the near kernel's rate (the whole step's time; the graph has no
+    # per-stage timing)
+    fp32_meas, _ = api.ankh_measure_fp32_peak(stream)
+    pairs = 0
+    for i in range(len(boxes)):
+        hb = api.ankh_batch_box(bt.h, i)
+        nb_ = int(api.ankh_get_info(hb)["n_cells"])
+        pairs += unordered_near_pairs(api.ankh_debug_copy(hb, api.BUF_START).cpu().numpy(), nb_)
+    near_lb = pairs * NEAR_FLOPS_PER_PAIR / 1e12 / (tot / steps)
+    roof = {"kernel": "near (all boxes, whole-step time: a lower bound)", "bound": "alu", "achieved": near_lb,
+            "peak": fp32_meas, "unit": "TFLOP/s", "frac": near_lb / fp32_meas, "traffic": None,
+            "peak_source": "FP32 FMA throughput measured on this GPU (ankh_measure_fp32_peak)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and cpu_baseline:
+        # the FP64 Ewald oracle on a bounded sample of four of the boxes
+        # (smallest, two middle, largest), a power law in N fitted to their
+        # extrapolated full-evaluation times, summed over all 64 boxes
+        order = sorted(range(len(all_boxes)), key=lambda i: all_boxes[i].n)
+        pick = [order[0], order[len(order) // 3], order[2 * len(order) // 3], order[-1]]
+        ts, ns = [], []
+        for i in pick:
+            r = oracle_sample(all_boxes[i], rows=150, kstride=400)
+            ts.append(r["seconds_full_eval"])
+            ns.append(all_boxes[i].n)
+        k_, c_ = np.polyfit(np.log(ns), np.log(ts), 1)
+        t_all = float(sum(math.exp(c_) * b.n ** k_ for b in all_boxes))
+        cpu = {"value": 64.0 / t_all, "unit": "box-evals/s", "cores": os.cpu_count() or 1, "kind": "oracle",
+               "sample": (f"FP64 Ewald oracle, energy + gradient: real-space rows of 150 and 300 atoms and "
+                          f"every 400-th / 200-th k-vector of boxes of {ns} atoms, each extrapolated to a full "
+                          f"evaluation, t = {math.exp(c_):.3g} N^{k_:.3f} s fitted and summed over the 64 boxes")}
+    line = {
+        "metric": METRIC, "value": value, "unit": "box-evals/s", "n_gpus": world, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": tot / steps * 1e3, "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "replicas64_water_3000_48000_qmuTheta_energy_forces", "n_boxes": 64,
+                   "n_atoms_total": ntot_all, "Lu": args.Lu, "l2": "flushed: 256 MiB write between timed steps",
+                   "execution": "one CUDA graph per rank, one branch per box",
+                   "parallelism": f"boxes split over {world} GPU(s) by LPT on atom counts"},
+        "matoms_per_s": value / 64 * ntot_all / 1e6, "clocks": clk, "roofline": roof, "cpu_baseline": cpu,
+        "e2e": {"value": 64 * e2e_steps / t_e2e, "unit": "box-evals/s",
+                "h2d_bytes_per_step": 4 * ntot * (3 + 1 + 3 + 6),
+                "d2h_bytes_per_step": 4 * ntot * (3 + 1 + 3 + 6 + 3)},
+        "gpu_launches": sum(launches_per_step(batch_box_cells(api, bt, i) ** 3, args.plain)
+                            for i in range(len(boxes))) * steps}
     bt.close()
+    return line
+
+
+def run_replicas(args, rank, world, dev, api, synth, dist=None):
+    line = replicas_measure(args, rank, world, dev, api, synth, dist, cpu_baseline=not args.no_cpu_baseline)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def run_fmm(args, rank, world, dev, api, synth, dist, cfg):
@@ -590,6 +744,8 @@ def main():
     ap.add_argument("--nonperiodic", action="store_true",
                     help="no periodic images (bare kernel, zero-padded far field, Sec. 5.2)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the plain-FP32 leg and the other workloads after the main line's timing")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--n-cells", type=int, default=0, help="leaves per axis (0 = autotuned)")
     ap.add_argument("--Lu", type=int, default=5, help="equispaced interpolation order")
@@ -787,6 +943,23 @@ def main():
     roof = roofline(dom) if dom in models else None
     roof_all = [roofline(k) for k in models if k in stage_ms and stage_ms[k] > 0]
 
+    # the plain FP32 form of the same evaluation on the same box and leaf count
+    plain_leg = None
+    legs = None
+    if rank == 0 and world == 1 and not args.no_extras and not args.plain and not args.nonperiodic:
+        mp_ = api.Ankh(box.box, N, n_cells=n_cells, Lu=info["Lu"], Lc=info["Lu"], mixed=False)
+        fn = lambda: api.ankh_energy_forces(mp_.h, x, q, mu, th, sync=False, stream=stream, **out)
+        tp = time_device(fn, max(10, min(args.steps, 30)), flush, stream)
+        Ep = api.ankh_energy_forces(mp_.h, x, q, mu, th, stream=stream, **out)
+        mp_.close()
+        plain_leg = {"precision": "plain_fp32 (FP32 CUDA-core correction)", "n_cells": n, "Lu": info["Lu"],
+                     "evals_per_s": 1.0 / tp, "ms_per_eval": tp * 1e3,
+                     "accuracy": golden_errors(box, Ep, out["dEdx"]),
+                     "mixed_over_plain": (1.0 / ms_step * 1e3) / (1.0 / tp)}
+        legs = config_legs(args, dev, api, synth, flush, stream, max(10, min(args.steps, 30)))
+        legs.append(replicas_measure(args, 0, 1, dev, api, synth, None, steps=max(5, min(args.steps, 10)),
+                                     e2e_steps=3, cpu_baseline=not args.no_cpu_baseline))
+
     cpu = None
     cpu_ankh = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -820,6 +993,8 @@ def main():
             "cpu_baseline_ankh": cpu_ankh,
             "e2e": {"value": world * args.e2e_steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
+            "plain_fp32": plain_leg,
+            "other_configs": legs,
             "gpu_launches": launches_per_step(ncell, args.plain) * args.steps,
         }
         print(json.dumps(line), flush=True)

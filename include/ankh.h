@@ -92,6 +92,7 @@ typedef struct {
     double box, h, xi;
     double precompute_ms;     /* wall time of ankh_create's table set-up */
     int64_t device_bytes;     /* device memory held by the handle */
+    int tables_from_cache;    /* 1: ankh_create_cached read the tables from its cache file */
 } ankh_info;
 
 typedef struct ankh_handle ankh_handle;
@@ -105,9 +106,30 @@ void ankh_default_params(ankh_params *p);
  * matrices, the spectrum of the periodic far-field kernel on the merged
  * equispaced grid, and the adjacent-leaf correction blocks.  Allocates all
  * device scratch on the current device.  params may be NULL (defaults).
+ * The merged grid of n (L_u - 1) points per axis (periodic) or its
+ * zero-padded size (non-periodic, chosen by the library) is transformed by
+ * the library's own FFT, which takes lengths with prime factors 2, 3, 5 and
+ * 7 only, at most 1024.
  * Errors: ANKH_EINVAL (N < 1, box not finite and > 0, n < 3, orders out of
- * range, xi <= 0), ANKH_ENOMEM, ANKH_ECUDA.  *out is NULL on error. */
+ * range, xi <= 0, a periodic grid n (L_u - 1) with a prime factor above 7
+ * or above 1024 points), ANKH_ENOMEM, ANKH_ECUDA.  *out is NULL on error. */
 int ankh_create(double box_edge, int64_t N, const ankh_params *params, ankh_handle **out);
+
+/* Same as ankh_create, with the per-box tables that do not depend on the
+ * atoms cached in the directory cache_dir (the paper's precomputation is its
+ * slow step, done once per box: Sec. 4.3 and 5.6).  The tables are the
+ * spectrum of the far-field kernel on the merged grid with its FP64 k = 0
+ * value, and the adjacent-leaf correction blocks C_d; they depend on the box
+ * edge, n, L_u, L_c, xi (as FP32), the grid size, ANKH_NONPERIODIC and
+ * ANKH_INCLUDE_REC, which key the file (cache_dir/ankh_tables_<hash>.bin,
+ * the key stored and compared in full).  A matching file is read instead of
+ * computing the tables; otherwise they are computed and the file is written
+ * (to a temporary name, then renamed).  Results are bit-identical to
+ * ankh_create's.  ANKH-FMM handles compute their own tables (not cached).
+ * Errors: as ankh_create; ANKH_EINVAL if cache_dir is NULL or empty or the
+ * file cannot be written.  ankh_get_info reports tables_from_cache. */
+int ankh_create_cached(double box_edge, int64_t N, const ankh_params *params, const char *cache_dir,
+                       ankh_handle **out);
 
 /* Energy of Eq. 1 by Alg. 5: near field over adjacent leaves (step 3), far
  * field by the diagonalised circulant (step 2), self term (step 4).
@@ -246,6 +268,21 @@ int ankh_bin_sort_noalloc(const float *x, int64_t N, double box_edge, int n_cell
  * NULL) receives the time of one launch.  It is the denominator of the near
  * field's roofline.  Synchronises the stream. */
 int ankh_measure_fp32_peak(double *tflops, double *ms, void *cuda_stream);
+
+/* Test access to the far-field transform step alone (no counterpart in the
+ * paper's interface; the tests use it to check the hand-written FFT against a
+ * library transform).  rho: nf^3 device floats (the merged grid, z fastest);
+ * D: nf * nf * (nf/2 + 1) device floats in the spectrum layout [x][y][kz]
+ * (NULL: the handle's kernel spectrum).  mode 0: out receives the forward
+ * unnormalised 3-D real transform of rho, nf * nf * (nf/2 + 1) complex
+ * (float2) values in the same layout.  mode 1: the far-field step of an
+ * evaluation: *E_glob = (1/2M) sum over the full spectrum of D |rho^|^2
+ * (M = nf^3), and out receives phi = the unnormalised inverse transform of
+ * D rho^ (nf^3 floats).  Overwrites the handle's grid buffers; synchronises
+ * the stream.  Errors: ANKH_EINVAL (NULL arguments, bad mode, ANKH-FMM
+ * handle), ANKH_ECUDA. */
+int ankh_debug_fft(ankh_handle *h, const float *rho, const float *D, int mode, double *E_glob, void *out,
+                   void *cuda_stream);
 
 /* Free everything the handle owns.  NULL is ignored. */
 void ankh_destroy(ankh_handle *h);

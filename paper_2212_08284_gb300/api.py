@@ -27,11 +27,11 @@ ANKH_FMM = 8
 # buffer ids of ankh_debug_copy
 BUF_PERM, BUF_START, BUF_M, BUF_RHO, BUF_PSI, BUF_SCELL = range(6)
 
-EXPORTED = ["ankh_default_params", "ankh_create", "ankh_energy", "ankh_energy_forces",
+EXPORTED = ["ankh_default_params", "ankh_create", "ankh_create_cached", "ankh_energy", "ankh_energy_forces",
             "ankh_energy_forces_host", "ankh_last_terms", "ankh_get_info", "ankh_debug_copy",
             "ankh_ldm", "ankh_set_timing", "ankh_stage_times", "ankh_bin_sort_noalloc", "ankh_destroy",
             "ankh_last_error", "ankh_version", "ankh_create_batch", "ankh_energy_forces_batch",
-            "ankh_batch_box", "ankh_destroy_batch", "ankh_induce", "ankh_measure_fp32_peak"]
+            "ankh_batch_box", "ankh_destroy_batch", "ankh_induce", "ankh_measure_fp32_peak", "ankh_debug_fft"]
 STAGES = ["sort", "self", "p2m", "merge", "fft_fwd", "spectral", "corr", "near", "fft_inv", "l2p",
           "unused", "reduce"]
 
@@ -51,7 +51,7 @@ class ankh_info(ctypes.Structure):
     _fields_ = [("n_cells", ctypes.c_int), ("Lu", ctypes.c_int), ("Lc", ctypes.c_int),
                 ("nf", ctypes.c_int), ("n_atoms", ctypes.c_int64), ("box", ctypes.c_double),
                 ("h", ctypes.c_double), ("xi", ctypes.c_double), ("precompute_ms", ctypes.c_double),
-                ("device_bytes", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("tables_from_cache", ctypes.c_int)]
 
 
 _lib = None
@@ -74,6 +74,9 @@ def load_library(path: str = LIB_PATH):
         lib.ankh_create.argtypes = [ctypes.c_double, ctypes.c_int64, ctypes.POINTER(ankh_params),
                                     ctypes.POINTER(vp)]
         lib.ankh_create.restype = ctypes.c_int
+        lib.ankh_create_cached.argtypes = [ctypes.c_double, ctypes.c_int64, ctypes.POINTER(ankh_params),
+                                           ctypes.c_char_p, ctypes.POINTER(vp)]
+        lib.ankh_create_cached.restype = ctypes.c_int
         lib.ankh_energy.argtypes = [vp, vp, vp, vp, vp, dp, vp]
         lib.ankh_energy.restype = ctypes.c_int
         lib.ankh_energy_forces.argtypes = [vp, vp, vp, vp, vp, dp, vp, vp, vp, vp, vp, vp]
@@ -111,6 +114,8 @@ def load_library(path: str = LIB_PATH):
         lib.ankh_destroy.restype = None
         lib.ankh_last_error.argtypes = []
         lib.ankh_last_error.restype = ctypes.c_char_p
+        lib.ankh_debug_fft.argtypes = [vp, vp, vp, ctypes.c_int, dp, vp, vp]
+        lib.ankh_debug_fft.restype = ctypes.c_int
         lib.ankh_measure_fp32_peak.argtypes = [dp, dp, vp]
         lib.ankh_measure_fp32_peak.restype = ctypes.c_int
         lib.ankh_version.argtypes = []
@@ -146,6 +151,14 @@ def ankh_create(box_edge: float, n_atoms: int, params: ankh_params | None = None
     h = ctypes.c_void_p()
     _check(lib.ankh_create(float(box_edge), int(n_atoms),
                            ctypes.byref(params) if params is not None else None, ctypes.byref(h)))
+    return h
+
+
+def ankh_create_cached(box_edge: float, n_atoms: int, params: ankh_params | None, cache_dir: str) -> ctypes.c_void_p:
+    lib = load_library()
+    h = ctypes.c_void_p()
+    _check(lib.ankh_create_cached(float(box_edge), int(n_atoms), ctypes.byref(params) if params is not None else None,
+                                  os.fsencode(cache_dir), ctypes.byref(h)))
     return h
 
 
@@ -239,6 +252,15 @@ def ankh_stage_times(h) -> dict:
     return dict(zip(STAGES, list(t)))
 
 
+def ankh_debug_fft(h, rho, D, mode: int, out, stream=None) -> float:
+    """The far-field transform step alone (tests): mode 0 forward transform of
+    rho into out (complex64), mode 1 energy term (returned) and phi into out."""
+    E = ctypes.c_double(0.0)
+    _check(load_library().ankh_debug_fft(h, _ptr(rho), _ptr(D), int(mode), ctypes.byref(E), _ptr(out),
+                                         _stream_ptr(stream)))
+    return E.value
+
+
 def ankh_measure_fp32_peak(stream=None) -> tuple[float, float]:
     """FP32 FMA throughput of the current device: (TFLOP/s, ms per launch)."""
     t, ms = ctypes.c_double(), ctypes.c_double()
@@ -281,7 +303,7 @@ class Ankh:
 
     def __init__(self, box_edge: float, n_atoms: int, xi: float = 0.01, n_cells: int = 0, Lu: int = 5,
                  Lc: int = 0, max_order: int = 2, include_rec: bool = True, mixed: bool = True,
-                 nonperiodic: bool = False, fmm: bool = False):
+                 nonperiodic: bool = False, fmm: bool = False, cache_dir: str | None = None):
         p = ankh_default_params()
         p.xi = xi
         p.n_cells = n_cells
@@ -292,7 +314,7 @@ class Ankh:
                    | (ANKH_NONPERIODIC if nonperiodic else 0) | (ANKH_FMM if fmm else 0))
         self.n_atoms = int(n_atoms)
         self.box = float(box_edge)
-        self.h = ankh_create(box_edge, n_atoms, p)
+        self.h = ankh_create_cached(box_edge, n_atoms, p, cache_dir) if cache_dir else ankh_create(box_edge, n_atoms, p)
 
     def close(self):
         if self.h:

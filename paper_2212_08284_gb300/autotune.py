@@ -19,9 +19,17 @@ from . import api
 _cache: dict = {}
 
 
-def candidates(box: float, spread: int = 4, h0: float = 4.0) -> list[int]:
+def smooth(m: int) -> bool:
+    """True when m has no prime factor above 7 (the lengths the FFT takes)."""
+    for p in (2, 3, 5, 7):
+        while m % p == 0:
+            m //= p
+    return m == 1
+
+
+def candidates(box: float, spread: int = 4, h0: float = 4.0, Lu: int = 5) -> list[int]:
     n0 = max(3, int(round(box / h0)))
-    return sorted({max(3, n0 + d) for d in range(-spread, spread + 1)})
+    return sorted({max(3, n0 + d) for d in range(-spread, spread + 1) if smooth(max(3, n0 + d) * (Lu - 1))})
 
 
 def autotune_n(box: float, x, q, mu=None, theta=None, Lu: int = 5, Lc: int = 0, mixed: bool = True,

@@ -169,6 +169,84 @@ static int choose_n_fmm(double box)
     return 1 << std::min(7, std::max(2, E));
 }
 
+// ---------------------------------------------------------------------------
+// Table cache (ANKH-FFT): the per-box tables that do not depend on the atoms
+// -- the far-field kernel spectrum D (FP32, k = 0 removed) with its FP64
+// k = 0 value D0, and the adjacent-leaf correction blocks C_d (FP32) -- in a
+// binary file keyed by everything they depend on.  File layout: the TableKey
+// below, then D0 (double), D (nf * nf * (nf/2 + 1) floats), C (27 ldm^2
+// floats).  The tensor-core operands are derived from C exactly as when it
+// is computed, so a handle made from the file gives bit-identical results.
+struct TableKey {
+    char magic[8];          // "ANKHTAB1"
+    double box, xi;         // xi as the FP32 value the tables were computed with
+    int32_t n, Lu, Lc, nf, ldm, nonperiodic, include_rec, pad;
+    int64_t nspec, nC;
+};
+
+static TableKey table_key(const Geo &g, unsigned flags)
+{
+    TableKey k;
+    std::memset(&k, 0, sizeof(k));
+    std::memcpy(k.magic, "ANKHTAB1", 8);
+    k.box = g.box;
+    k.xi = (double)g.xi;
+    k.n = g.n;
+    k.Lu = g.Lu;
+    k.Lc = g.Lc;
+    k.nf = g.nf;
+    k.ldm = g.ldm;
+    k.nonperiodic = g.nonperiodic;
+    k.include_rec = (flags & ANKH_INCLUDE_REC) ? 1 : 0;
+    k.nspec = (int64_t)g.nf * g.nf * g.nfh;
+    k.nC = (int64_t)27 * g.ldm * g.ldm;
+    return k;
+}
+
+static std::string table_path(const char *dir, const TableKey &k)
+{
+    // FNV-1a of the key bytes names the file; the key itself is checked on load
+    uint64_t hsh = 1469598103934665603ull;
+    const unsigned char *b = reinterpret_cast<const unsigned char *>(&k);
+    for (size_t i = 0; i < sizeof(k); ++i) hsh = (hsh ^ b[i]) * 1099511628211ull;
+    char name[64];
+    std::snprintf(name, sizeof(name), "/ankh_tables_%016llx.bin", (unsigned long long)hsh);
+    return std::string(dir) + name;
+}
+
+static bool table_load(const std::string &path, const TableKey &want, double *D0, std::vector<float> &D,
+                       std::vector<float> &C)
+{
+    FILE *f = std::fopen(path.c_str(), "rb");
+    if (!f) return false;
+    TableKey k;
+    bool ok = std::fread(&k, sizeof(k), 1, f) == 1 && std::memcmp(&k, &want, sizeof(k)) == 0;
+    if (ok) {
+        D.resize((size_t)k.nspec);
+        C.resize((size_t)k.nC);
+        ok = std::fread(D0, sizeof(double), 1, f) == 1 && std::fread(D.data(), sizeof(float), D.size(), f) == D.size() &&
+             std::fread(C.data(), sizeof(float), C.size(), f) == C.size() && std::fgetc(f) == EOF;
+    }
+    std::fclose(f);
+    return ok;
+}
+
+static bool table_save(const std::string &path, const TableKey &k, double D0, const std::vector<float> &D,
+                       const std::vector<float> &C)
+{
+    const std::string tmp = path + ".tmp" + std::to_string((long long)std::chrono::steady_clock::now()
+                                                           .time_since_epoch().count());
+    FILE *f = std::fopen(tmp.c_str(), "wb");
+    if (!f) return false;
+    bool ok = std::fwrite(&k, sizeof(k), 1, f) == 1 && std::fwrite(&D0, sizeof(double), 1, f) == 1 &&
+              std::fwrite(D.data(), sizeof(float), D.size(), f) == D.size() &&
+              std::fwrite(C.data(), sizeof(float), C.size(), f) == C.size();
+    ok = (std::fclose(f) == 0) && ok;
+    if (ok) ok = std::rename(tmp.c_str(), path.c_str()) == 0;
+    if (!ok) std::remove(tmp.c_str());
+    return ok;
+}
+
 static void free_device(Handle *H)
 {
     if (!H) return;
@@ -184,11 +262,8 @@ static void free_device(Handle *H)
     if (H->have_events)
         for (int k = 0; k <= kNumStages; ++k) cudaEventDestroy(H->ev[k]);
     H->have_events = 0;
-    if (H->have_plans) {
-        cufftDestroy(H->plan_r2c);
-        cufftDestroy(H->plan_c2r);
-    }
-    H->have_plans = 0;
+    if (H->d_tw) cudaFree(H->d_tw);
+    H->d_tw = nullptr;
 }
 
 template <typename T>
@@ -228,8 +303,7 @@ int run_sequence(Handle &H, const float *x, const float *q, const float *mu, con
     mark_stage(H, kStP2M, s);
     ANKH_CU(launch_fine_gather(H, s), "merge");
     mark_stage(H, kStMerge, s);
-    if (cufftSetStream(H.plan_r2c, s) != CUFFT_SUCCESS) return fail(ANKH_ECUDA, "cufftSetStream");
-    if (cufftExecR2C(H.plan_r2c, H.d_rho, H.d_rhohat) != CUFFT_SUCCESS) return fail(ANKH_ECUDA, "cufftExecR2C");
+    ANKH_CU(launch_fft_forward(H, s), "forward FFT");
     mark_stage(H, kStFFTf, s);
     ANKH_CU(launch_spectral(H, forces, s), "spectral");
     mark_stage(H, kStSpectral, s);
@@ -241,9 +315,7 @@ int run_sequence(Handle &H, const float *x, const float *q, const float *mu, con
     ANKH_CU(launch_near(H, forces, s), "near");
     mark_stage(H, kStNear, s);
     if (forces) {
-        if (cufftSetStream(H.plan_c2r, s) != CUFFT_SUCCESS) return fail(ANKH_ECUDA, "cufftSetStream");
-        if (cufftExecC2R(H.plan_c2r, H.d_rhohat, H.d_phi) != CUFFT_SUCCESS)
-            return fail(ANKH_ECUDA, "cufftExecC2R");
+        ANKH_CU(launch_fft_inverse(H, s), "inverse FFT");
         mark_stage(H, kStFFTi, s);
         ANKH_CU(launch_l2p(H, dEdx, dEdq, dEdmu, dEdtheta, torque, s), "l2p");
         mark_stage(H, kStL2P, s);
@@ -271,9 +343,6 @@ int fetch_terms(Handle &H, double *E_host, cudaStream_t s)
 
 using namespace ankh;
 
-struct ankh_handle {
-    Handle h;
-};
 
 extern "C" {
 
@@ -292,7 +361,25 @@ void ankh_default_params(ankh_params *p)
     p->flags = ANKH_INCLUDE_REC | ANKH_MIXED;
 }
 
+static int create_handle(double box_edge, int64_t N, const ankh_params *params, const char *cache_dir,
+                         ankh_handle **out);
+
 int ankh_create(double box_edge, int64_t N, const ankh_params *params, ankh_handle **out)
+{
+    return create_handle(box_edge, N, params, nullptr, out);
+}
+
+int ankh_create_cached(double box_edge, int64_t N, const ankh_params *params, const char *cache_dir,
+                       ankh_handle **out)
+{
+    if (!cache_dir || !*cache_dir) return fail(ANKH_EINVAL, "cache_dir is required");
+    return create_handle(box_edge, N, params, cache_dir, out);
+}
+
+}  // extern "C"
+
+static int create_handle(double box_edge, int64_t N, const ankh_params *params, const char *cache_dir,
+                         ankh_handle **out)
 {
     if (!out) return fail(ANKH_EINVAL, "out is NULL");
     *out = nullptr;
@@ -318,6 +405,9 @@ int ankh_create(double box_edge, int64_t N, const ankh_params *params, ankh_hand
     // least twice that minus one, so the circular convolution is the linear one
     const int ngrid = fmm ? 0 : (nonper ? next_fft_size(2 * (n * (p.Lu - 1) + 1) - 1) : n * (p.Lu - 1));
     if (ngrid > 1024) return fail(ANKH_EINVAL, "FFT grid larger than 1024 points per axis");
+    if (!fmm && !good_fft_size(ngrid))
+        return fail(ANKH_EINVAL, "the merged grid of n (L_u - 1) = " + std::to_string(ngrid) +
+                                     " points per axis must have no prime factor above 7 (choose another n)");
 
     auto t0 = std::chrono::steady_clock::now();
     ankh_handle *hh = new (std::nothrow) ankh_handle();
@@ -461,12 +551,19 @@ int ankh_create(double box_edge, int64_t N, const ankh_params *params, ankh_hand
         set_error("");
         return ANKH_OK;
     }
-    {
+    // per-box tables: from the cache file when one matches, else computed
+    const TableKey tkey = table_key(g, p.flags);
+    const std::string tpath = cache_dir ? table_path(cache_dir, tkey) : std::string();
+    std::vector<float> Cf, Dcache;
+    double D0cache = 0.0;
+    const bool from_cache = cache_dir && table_load(tpath, tkey, &D0cache, Dcache, Cf);
+    if (!from_cache) {
         std::vector<double> C = make_C(g.Lu, g.ldm, g.h / (g.Lu - 1), p.xi);
-        std::vector<float> Cf(C.begin(), C.end());
-        if (cudaMemcpy(H.d_C, Cf.data(), Cf.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
-            return bail(ANKH_ECUDA, "upload C");
+        Cf.assign(C.begin(), C.end());
     }
+    H.tables_from_cache = from_cache ? 1 : 0;
+    if (cudaMemcpy(H.d_C, Cf.data(), Cf.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(ANKH_ECUDA, "upload C");
     if ((p.flags & ANKH_MIXED) && g.ldm % 32 == 0 && g.ldm <= 512 && n <= 128) {
         int S, R;
         tc_tile_shape(n, S, R);
@@ -485,16 +582,15 @@ int ankh_create(double box_edge, int64_t N, const ankh_params *params, ankh_hand
         cudaMemset(H.d_Mlo, 0, sizeof(__half) * rows * ldk);
         // A = 2^eC [C_0 | ... | C_26] as [halves*128 rows][27*ldk], split into fp16 hi + lo
         // (round to nearest), eC from max |C| so that the largest entry is <= 2^14
-        std::vector<double> C = make_C(g.Lu, g.ldm, g.h / (g.Lu - 1), p.xi);
-        double cmax = 0.0;
-        for (double v : C) cmax = std::max(cmax, std::fabs(v));
-        H.tc.eC = split_exponent((float)cmax);
+        float cmax = 0.f;
+        for (float v : Cf) cmax = std::max(cmax, std::fabs(v));
+        H.tc.eC = split_exponent(cmax);
         const float cs = std::ldexp(1.f, H.tc.eC);
         std::vector<__half> Ah((size_t)(arows * acols), __float2half_rn(0.f)), Al(Ah);
         for (int d = 0; d < 27; ++d)
             for (int m = 0; m < g.ldm; ++m)
                 for (int l = 0; l < g.ldm; ++l) {
-                    const float v = (float)C[((size_t)d * g.ldm + m) * g.ldm + l] * cs;
+                    const float v = Cf[((size_t)d * g.ldm + m) * g.ldm + l] * cs;
                     const __half hi = __float2half_rn(v);
                     Ah[(size_t)m * acols + (size_t)d * ldk + l] = hi;
                     Al[(size_t)m * acols + (size_t)d * ldk + l] = __float2half_rn(v - __half2float(hi));
@@ -505,15 +601,25 @@ int ankh_create(double box_edge, int64_t N, const ankh_params *params, ankh_hand
         std::string terr;
         if (!tc_prepare(H, terr)) return bail(ANKH_ECUDA, terr);
     }
-    std::string perr;
-    if (precompute_kernel_spectrum(H, &H.D0, perr) != cudaSuccess) return bail(ANKH_ECUDA, perr);
-    if (cufftPlan3d(&H.plan_r2c, g.nf, g.nf, g.nf, CUFFT_R2C) != CUFFT_SUCCESS)
-        return bail(ANKH_ECUDA, "cufftPlan3d R2C");
-    if (cufftPlan3d(&H.plan_c2r, g.nf, g.nf, g.nf, CUFFT_C2R) != CUFFT_SUCCESS) {
-        cufftDestroy(H.plan_r2c);
-        return bail(ANKH_ECUDA, "cufftPlan3d C2R");
+    if (from_cache) {
+        H.D0 = D0cache;
+        if (cudaMemcpy(H.d_D, Dcache.data(), Dcache.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(ANKH_ECUDA, "upload cached spectrum");
+    } else {
+        std::string perr;
+        if (precompute_kernel_spectrum(H, &H.D0, perr) != cudaSuccess) return bail(ANKH_ECUDA, perr);
+        if (cache_dir) {
+            Dcache.resize((size_t)tkey.nspec);
+            if (cudaMemcpy(Dcache.data(), H.d_D, Dcache.size() * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
+                return bail(ANKH_ECUDA, "read back spectrum");
+            if (!table_save(tpath, tkey, H.D0, Dcache, Cf))
+                return bail(ANKH_EINVAL, "cannot write the table cache file " + tpath);
+        }
     }
-    H.have_plans = 1;
+    {
+        std::string ferr;
+        if (!fft_prepare(H, ferr)) return bail(ANKH_ECUDA, ferr);
+    }
     if (cudaDeviceSynchronize() != cudaSuccess) return bail(ANKH_ECUDA, "precompute synchronize");
     auto t1 = std::chrono::steady_clock::now();
     H.precompute_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
@@ -522,6 +628,8 @@ int ankh_create(double box_edge, int64_t N, const ankh_params *params, ankh_hand
     set_error("");
     return ANKH_OK;
 }
+
+extern "C" {
 
 void ankh_destroy(ankh_handle *h)
 {
@@ -636,6 +744,7 @@ int ankh_get_info(const ankh_handle *h, ankh_info *info)
     info->xi = H.g.xi;
     info->precompute_ms = H.precompute_ms;
     info->device_bytes = H.device_bytes;
+    info->tables_from_cache = H.tables_from_cache;
     return ANKH_OK;
 }
 

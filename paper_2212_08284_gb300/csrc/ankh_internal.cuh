@@ -54,6 +54,18 @@ struct RadixBufs {
 };
 RadixPlan radix_plan(int64_t N, int ncell);
 
+// Hand-written 3-D real FFT of the merged grid (fft.cu): one mixed-radix
+// Stockham plan for the L = nf points of every axis.
+constexpr int kFftMaxStages = 12;
+struct FftPlan {
+    int L, Lh;                  // points per axis, L / 2 + 1
+    int nst;                    // stages
+    int radix[kFftMaxStages];   // radix of each stage (2 .. 8)
+    int p[kFftMaxStages];       // product of the radices before each stage
+    int tk;                     // lines per block of the passes along y and x
+    int zl;                     // complex lines (row pairs) per block of the passes along z
+};
+
 // Pipeline stages (for the optional per-stage timing)
 enum Stage { kStSort = 0, kStSelf, kStP2M, kStMerge, kStFFTf, kStSpectral, kStCorr, kStNear, kStFFTi,
              kStL2P, kStUnused, kStReduce, kNumStages };
@@ -126,6 +138,7 @@ struct Handle {
     int sm_count;           // multiprocessors of the device (grid sizing)
     double D0;              // k = 0 value of the far-field kernel spectrum (FP64)
     double precompute_ms;
+    int tables_from_cache;  // 1: the per-box tables were read from a cache file
     int64_t device_bytes;
 
     // atoms (sorted by leaf)
@@ -161,8 +174,8 @@ struct Handle {
     float *d_hostbuf;       // staging for the host-buffer entry point
     int64_t hostbuf_bytes;
     double last_terms[6];
-    cufftHandle plan_r2c, plan_c2r;
-    int have_plans;
+    FftPlan fft;
+    float2 *d_tw;           // [L] FFT twiddles e^{-2 pi i e / L} (FP32 from FP64)
     // optional per-stage timing (events on the caller's stream)
     int timing;
     int have_events;
@@ -188,7 +201,10 @@ cudaError_t launch_bin_sort_raw(int N, const float *x, const Geo &g, int *cellid
                                 const RadixPlan &rp, const RadixBufs &b, int *start, int *perm, cudaStream_t s);
 cudaError_t launch_p2m(Handle &H, cudaStream_t s);
 cudaError_t launch_fine_gather(Handle &H, cudaStream_t s);
-cudaError_t launch_spectral(Handle &H, bool forces, cudaStream_t s);
+bool fft_prepare(Handle &H, std::string &err);
+cudaError_t launch_fft_forward(Handle &H, cudaStream_t s);   // passes along z and y
+cudaError_t launch_spectral(Handle &H, bool forces, cudaStream_t s);   // along x: energy [, D rho^, inverse along x]
+cudaError_t launch_fft_inverse(Handle &H, cudaStream_t s);   // inverse passes along y and z
 cudaError_t launch_corr(Handle &H, bool forces, cudaStream_t s);
 cudaError_t launch_near(Handle &H, bool forces, cudaStream_t s);
 cudaError_t launch_l2p(Handle &H, float *dEdx, float *dEdq, float *dEdmu, float *dEdtheta, float *torque,
@@ -229,3 +245,8 @@ int corr_blocks(const Handle &H);
 int self_blocks(const Handle &H);
 
 }  // namespace ankh
+
+// The opaque handle of the C ABI.
+struct ankh_handle {
+    ankh::Handle h;
+};

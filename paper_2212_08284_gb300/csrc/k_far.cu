@@ -4,7 +4,8 @@
 // adjacent leaves, periodic images folded in, Sec. 4.3) is applied here as
 //   F = 1/2 rho^T G rho  +  (adjacent-leaf correction, k_corr.cu)
 // where rho is the grid charge with the duplicated face nodes summed and G is
-// one circulant on the n (L_u - 1) grid:
+// one circulant on the n (L_u - 1) grid (its transforms and the spectral
+// product are in fft.cu):
 //   G(z) = Phi(z) - [ |z|_inf < h ] H(z),  Phi(z) = sum_m H(z + L m),
 // i.e. the interactions closer than one leaf width are taken out of the
 // global kernel and every adjacent-leaf node pair at |z|_inf >= h is removed
@@ -28,61 +29,6 @@
 #include <cmath>
 
 namespace ankh {
-
-__device__ __forceinline__ double block_sum_d(double v, double *sh)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) sh[wid] = v;
-    __syncthreads();
-    double t = 0.0;
-    if (threadIdx.x < 32) {
-        t = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-    }
-    return t;  // valid in thread 0
-}
-
-// E_glob partials and (optionally) phi^ = D rho^ in place.
-__global__ void __launch_bounds__(256)
-k_spectral(Geo g, cufftComplex *__restrict__ rh, const float *__restrict__ D, int write_phi,
-           double *__restrict__ part)
-{
-    __shared__ double sh[32];
-    const int64_t total = (int64_t)g.nf * g.nf * g.nfh;
-    const int nfh = g.nfh;
-    const bool even = (g.nf % 2) == 0;
-    double e = 0.0;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int kz = (int)(idx % nfh);
-        const float w = (kz == 0 || (even && kz == nfh - 1)) ? 1.f : 2.f;
-        const float d = D[idx];
-        cufftComplex c = rh[idx];
-        e += (double)(w * d * (c.x * c.x + c.y * c.y));
-        if (write_phi) {
-            c.x *= d;
-            c.y *= d;
-            rh[idx] = c;
-        }
-    }
-    const double t = block_sum_d(e, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = t;
-}
-
-int spectral_blocks(const Handle &H)
-{
-    return H.sm_count * 4;
-}
-
-cudaError_t launch_spectral(Handle &H, bool forces, cudaStream_t s)
-{
-    k_spectral<<<spectral_blocks(H), 256, 0, s>>>(H.g, H.d_rhohat, H.d_D, forces ? 1 : 0,
-                                                  H.d_part + H.part_off[kPartGlob]);
-    return cudaGetLastError();
-}
 
 // ----------------------------------------------------------------------------
 // Precomputation kernels (FP64)

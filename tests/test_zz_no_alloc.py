@@ -33,7 +33,7 @@ def test_no_alloc_bin_sort_matches_allocating_path(gpu):
     ptr = lambda t: ctypes.c_void_p(t.data_ptr())
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
-    boxes = [(synth.small_box(4000, 77, box=49.4), 11), (synth.small_box(1500, 78, box=35.6), 7),
+    boxes = [(synth.small_box(4000, 77, box=49.4), 12), (synth.small_box(1500, 78, box=35.6), 7),
              face_box(False), clustered_one_leaf(), clustered_half_in_eight()]
     for b, n in boxes:
         f32 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
