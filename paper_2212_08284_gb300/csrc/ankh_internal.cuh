@@ -62,8 +62,11 @@ struct FftPlan {
     int nst;                    // stages
     int radix[kFftMaxStages];   // radix of each stage (2 .. 8)
     int p[kFftMaxStages];       // product of the radices before each stage
+    unsigned mag[kFftMaxStages];  // ceil(2^20 / p): i / p = (i mag) >> 20 for i < L
+    unsigned magL, magLh;       // floor(2^32 / d) + 1 for d = L and L / 2 + 1
     int tk;                     // lines per block of the passes along y and x
     int zl;                     // complex lines (row pairs) per block of the passes along z
+    int ty, tz;                 // threads per block of those passes
 };
 
 // Pipeline stages (for the optional per-stage timing)

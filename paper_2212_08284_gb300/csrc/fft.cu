@@ -30,8 +30,10 @@
 // so consecutive threads touch consecutive words.
 #include "ankh_internal.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <functional>
+#include <numeric>
 #include <vector>
 
 namespace ankh {
@@ -186,28 +188,36 @@ struct Dft<8, SIGN> {
 };
 
 // One Stockham stage of radix R over the NL lines of a block (line stride
-// ls in the point index).  tw: e^{-2 pi i e / L}, e = 0 .. L - 1.
-template <int R, int SIGN>
-__device__ __forceinline__ void fft_stage(const float2 *__restrict__ a, float2 *__restrict__ b, int L, int p, int NL,
-                                          int ls, const float2 *__restrict__ tw)
+// ls in the point index).  Butterfly f covers line f mod NL and index
+// i = f / NL of the stage; k = i mod p with the division by p done as a
+// multiplication by mag = ceil(2^20 / p) (exact for i, p < 1024, checked on
+// the host).  The twiddles W^(r k L/(p R)), r = 1 .. R-1, are powers of the
+// one read from the table.  tw: e^{-2 pi i e / L}, e = 0 .. L - 1.
+template <int R, int SIGN, int NL>
+__device__ __forceinline__ void fft_stage(const float2 *__restrict__ a, float2 *__restrict__ b, int L, int p,
+                                          unsigned mag, int ls, const float2 *__restrict__ tw)
 {
+    constexpr int LG = NL == 16 ? 4 : (NL == 8 ? 3 : (NL == 4 ? 2 : 1));
     const int LR = L / R, tws = L / (p * R), nb = LR * NL;
-    for (int idx = threadIdx.x; idx < nb; idx += blockDim.x) {
-        const int i = idx / NL, l = idx - i * NL;
-        const int k = i % p;
+    for (int f = threadIdx.x; f < nb; f += blockDim.x) {
+        const int l = f & (NL - 1), i = f >> LG;
+        const int g = (int)(((unsigned)i * mag) >> 20);
+        const int k = i - g * p;
         float2 u[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) u[r] = a[(i + r * LR) * ls + l];
         if (k != 0) {
+            float2 w1 = tw[k * tws];
+            if (SIGN > 0) w1.y = -w1.y;
+            float2 w = w1;
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                float2 w = tw[r * k * tws];          // r k tws < L
-                if (SIGN > 0) w.y = -w.y;
                 u[r] = cmul(u[r], w);
+                if (r + 1 < R) w = cmul(w, w1);
             }
         }
         Dft<R, SIGN>::run(u);
-        const int j = (i - k) * R + k;
+        const int j = g * p * R + k;
 #pragma unroll
         for (int r = 0; r < R; ++r) b[(j + r * p) * ls + l] = u[r];
     }
@@ -215,19 +225,20 @@ __device__ __forceinline__ void fft_stage(const float2 *__restrict__ a, float2 *
 
 // Transform the NL lines held in a (point-major, line stride ls); returns
 // the buffer that holds the result (a or b).  Ends with a barrier.
-template <int SIGN>
-__device__ float2 *fft_lines(float2 *a, float2 *b, int NL, int ls, const FftPlan &pl, const float2 *tw)
+template <int SIGN, int NL>
+__device__ float2 *fft_lines(float2 *a, float2 *b, int ls, const FftPlan &pl, const float2 *tw)
 {
     for (int s = 0; s < pl.nst; ++s) {
         const int R = pl.radix[s], p = pl.p[s];
+        const unsigned mag = pl.mag[s];
         switch (R) {
-        case 2: fft_stage<2, SIGN>(a, b, pl.L, p, NL, ls, tw); break;
-        case 3: fft_stage<3, SIGN>(a, b, pl.L, p, NL, ls, tw); break;
-        case 4: fft_stage<4, SIGN>(a, b, pl.L, p, NL, ls, tw); break;
-        case 5: fft_stage<5, SIGN>(a, b, pl.L, p, NL, ls, tw); break;
-        case 6: fft_stage<6, SIGN>(a, b, pl.L, p, NL, ls, tw); break;
-        case 7: fft_stage<7, SIGN>(a, b, pl.L, p, NL, ls, tw); break;
-        default: fft_stage<8, SIGN>(a, b, pl.L, p, NL, ls, tw); break;
+        case 2: fft_stage<2, SIGN, NL>(a, b, pl.L, p, mag, ls, tw); break;
+        case 3: fft_stage<3, SIGN, NL>(a, b, pl.L, p, mag, ls, tw); break;
+        case 4: fft_stage<4, SIGN, NL>(a, b, pl.L, p, mag, ls, tw); break;
+        case 5: fft_stage<5, SIGN, NL>(a, b, pl.L, p, mag, ls, tw); break;
+        case 6: fft_stage<6, SIGN, NL>(a, b, pl.L, p, mag, ls, tw); break;
+        case 7: fft_stage<7, SIGN, NL>(a, b, pl.L, p, mag, ls, tw); break;
+        default: fft_stage<8, SIGN, NL>(a, b, pl.L, p, mag, ls, tw); break;
         }
         __syncthreads();
         float2 *t = a;
@@ -237,33 +248,53 @@ __device__ float2 *fft_lines(float2 *a, float2 *b, int NL, int ls, const FftPlan
     return a;
 }
 
+// q / d for the d of a plan: (q m) >> 32 with m = floor(2^32 / d) + 1
+// (exact for the q, d of the plans, checked on the host)
+__device__ __forceinline__ int udiv(int q, unsigned m) { return (int)__umulhi((unsigned)q, m); }
+
 __device__ __forceinline__ void load_twiddles(float2 *stw, const float2 *__restrict__ tw, int L)
 {
     for (int e = threadIdx.x; e < L; e += blockDim.x) stw[e] = tw[e];
 }
 
 // ---------------------------------------------------------------------------
-// Pass Z: r2c along z.  Block: 2 * ZL consecutive rows (x, y) of L reals, as
+// Pass Z: r2c along z.  Block: 2 ZL consecutive rows (x, y) of L reals, as
 // ZL complex lines; out: [rows][Lh] complex.
-__global__ void __launch_bounds__(256) k_fft_z_r2c(FftPlan pl, int nrows, const float *__restrict__ in,
+template <int ZL>
+__global__ void __launch_bounds__(512) k_fft_z_r2c(FftPlan pl, int nrows, const float *__restrict__ in,
                                                    float2 *__restrict__ out, const float2 *__restrict__ tw)
 {
     extern __shared__ float2 sm[];
-    const int L = pl.L, Lh = pl.Lh, ZL = pl.zl, ls = ZL + 1;
+    const int L = pl.L, Lh = pl.Lh;
+    constexpr int ls = ZL + 1;
     float2 *stw = sm, *a = sm + L, *b = a + L * ls;
     load_twiddles(stw, tw, L);
     const int row0 = blockIdx.x * 2 * ZL;
-    for (int e = threadIdx.x; e < 2 * ZL * L; e += blockDim.x) {
-        const int rr = e / L, n = e - rr * L;
-        const int row = row0 + rr;
-        const float v = row < nrows ? in[(int64_t)row * L + n] : 0.f;
-        float *dst = reinterpret_cast<float *>(&a[n * ls + (rr >> 1)]);
-        dst[rr & 1] = v;
+    const int tot = 2 * ZL * L;
+    const float *src = in + (int64_t)row0 * L;              // the block's rows are contiguous
+    const int64_t avail = ((int64_t)nrows - row0) * L;      // values left in the input
+    float *af = reinterpret_cast<float *>(a);
+    for (int f0 = threadIdx.x; f0 < tot; f0 += 8 * blockDim.x) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int f = f0 + u * blockDim.x;
+            v[u] = (f < tot && f < avail) ? src[f] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int f = f0 + u * blockDim.x;
+            if (f < tot) {
+                const int rr = udiv(f, pl.magL), n = f - rr * L;
+                af[2 * (n * ls + (rr >> 1)) + (rr & 1)] = v[u];
+            }
+        }
     }
     __syncthreads();
-    const float2 *z = fft_lines<-1>(a, b, ZL, ls, pl, stw);
-    for (int e = threadIdx.x; e < 2 * ZL * Lh; e += blockDim.x) {
-        const int rr = e / Lh, k = e - rr * Lh;
+    const float2 *z = fft_lines<-1, ZL>(a, b, ls, pl, stw);
+    const int toto = 2 * ZL * Lh;
+    for (int f = threadIdx.x; f < toto; f += blockDim.x) {
+        const int rr = udiv(f, pl.magLh), k = f - rr * Lh;
         const int row = row0 + rr;
         if (row >= nrows) continue;
         const int q = rr >> 1;
@@ -271,68 +302,108 @@ __global__ void __launch_bounds__(256) k_fft_z_r2c(FftPlan pl, int nrows, const 
         // X = (Z_k + conj Z_{L-k}) / 2,  Y = (Z_k - conj Z_{L-k}) / 2i
         const float2 v = (rr & 1) ? make_float2(0.5f * (zk.y + zm.y), 0.5f * (zm.x - zk.x))
                                   : make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
-        out[(int64_t)row * Lh + k] = v;
+        out[(int64_t)row0 * Lh + f] = v;                    // rows of Lh values, contiguous
     }
 }
 
 // Pass Z': c2r along z.  in: [rows][Lh] half spectra; out: [rows][L] reals.
-__global__ void __launch_bounds__(256) k_fft_z_c2r(FftPlan pl, int nrows, const float2 *__restrict__ in,
+template <int ZL>
+__global__ void __launch_bounds__(512) k_fft_z_c2r(FftPlan pl, int nrows, const float2 *__restrict__ in,
                                                    float *__restrict__ out, const float2 *__restrict__ tw)
 {
     extern __shared__ float2 sm[];
-    const int L = pl.L, Lh = pl.Lh, ZL = pl.zl, ls = ZL + 1;
+    const int L = pl.L, Lh = pl.Lh;
+    constexpr int ls = ZL + 1;
     float2 *stw = sm, *a = sm + L, *b = a + L * ls;
     load_twiddles(stw, tw, L);
     const int row0 = blockIdx.x * 2 * ZL;
     // Z_k = X_k + i Y_k over k = 0 .. L-1, X_{L-k} = conj X_k (Hermitian rows)
-    for (int e = threadIdx.x; e < ZL * L; e += blockDim.x) {
-        const int q = e / L, k = e - q * L;
-        const int r0 = row0 + 2 * q, r1 = r0 + 1;
-        const bool lowh = k < Lh;
-        const int kk = lowh ? k : L - k;
-        float2 X = r0 < nrows ? in[(int64_t)r0 * Lh + kk] : make_float2(0.f, 0.f);
-        float2 Y = r1 < nrows ? in[(int64_t)r1 * Lh + kk] : make_float2(0.f, 0.f);
-        if (kk == 0 || 2 * kk == L) {
-            X.y = 0.f;
-            Y.y = 0.f;
+    const int tot = ZL * L;
+    for (int f0 = threadIdx.x; f0 < tot; f0 += 4 * blockDim.x) {
+        float2 X[4], Y[4];
+        int kk4[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int f = f0 + u * blockDim.x;
+            const int q = udiv(f, pl.magL), k = f - q * L;
+            const int r0 = row0 + 2 * q, r1 = r0 + 1;
+            const int kk = k < Lh ? k : L - k;
+            kk4[u] = kk;
+            X[u] = (f < tot && r0 < nrows) ? in[(int64_t)r0 * Lh + kk] : make_float2(0.f, 0.f);
+            Y[u] = (f < tot && r1 < nrows) ? in[(int64_t)r1 * Lh + kk] : make_float2(0.f, 0.f);
         }
-        if (!lowh) {
-            X.y = -X.y;
-            Y.y = -Y.y;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int f = f0 + u * blockDim.x;
+            if (f >= tot) continue;
+            const int q = udiv(f, pl.magL), k = f - q * L;
+            float2 x = X[u], y = Y[u];
+            if (kk4[u] == 0 || 2 * kk4[u] == L) {
+                x.y = 0.f;
+                y.y = 0.f;
+            }
+            if (k >= Lh) {
+                x.y = -x.y;
+                y.y = -y.y;
+            }
+            a[k * ls + q] = make_float2(x.x - y.y, x.y + y.x);
         }
-        a[k * ls + q] = make_float2(X.x - Y.y, X.y + Y.x);
     }
     __syncthreads();
-    const float2 *z = fft_lines<1>(a, b, ZL, ls, pl, stw);
-    for (int e = threadIdx.x; e < 2 * ZL * L; e += blockDim.x) {
-        const int rr = e / L, n = e - rr * L;
-        const int row = row0 + rr;
-        if (row >= nrows) continue;
-        const float2 v = z[n * ls + (rr >> 1)];
-        out[(int64_t)row * L + n] = (rr & 1) ? v.y : v.x;
+    const float2 *z = fft_lines<1, ZL>(a, b, ls, pl, stw);
+    const float *zf = reinterpret_cast<const float *>(z);
+    const int toto = 2 * ZL * L;
+    for (int f = threadIdx.x; f < toto; f += blockDim.x) {
+        const int rr = udiv(f, pl.magL), n = f - rr * L;
+        if (row0 + rr >= nrows) continue;
+        out[(int64_t)row0 * L + f] = zf[2 * (n * ls + (rr >> 1)) + (rr & 1)];
+    }
+}
+
+// Load a tile of L points x TK lines (line l of point pos at
+// base[pos * stride + l], lines beyond nvalid read as 0) into shared memory,
+// point-major, with eight loads in flight per thread.
+template <int TK>
+__device__ __forceinline__ void tile_load(float2 *a, const float2 *__restrict__ base, int64_t stride, int L,
+                                          bool full, int nvalid)
+{
+    constexpr int LG = TK == 16 ? 4 : 3;
+    const int tot = L * TK;
+    for (int f0 = threadIdx.x; f0 < tot; f0 += 8 * blockDim.x) {
+        float2 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int f = f0 + u * blockDim.x;
+            const int l = f & (TK - 1), pos = f >> LG;
+            v[u] = (f < tot && (full || l < nvalid)) ? base[pos * stride + l] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int f = f0 + u * blockDim.x;
+            if (f < tot) a[f] = v[u];
+        }
     }
 }
 
 // Pass Y / Y': complex FFT along y, in place.  Block (kz tile, x): the TK
 // columns kz0 .. kz0 + TK - 1 of the plane x, all L values of y.
-template <int SIGN>
-__global__ void __launch_bounds__(256) k_fft_y(FftPlan pl, float2 *__restrict__ s, const float2 *__restrict__ tw)
+template <int SIGN, int TK>
+__global__ void __launch_bounds__(512) k_fft_y(FftPlan pl, float2 *__restrict__ s, const float2 *__restrict__ tw)
 {
     extern __shared__ float2 sm[];
-    const int L = pl.L, Lh = pl.Lh, TK = pl.tk;
+    constexpr int LG = TK == 16 ? 4 : 3;
+    const int L = pl.L, Lh = pl.Lh;
     float2 *stw = sm, *a = sm + L, *b = a + L * TK;
     load_twiddles(stw, tw, L);
     const int kz0 = blockIdx.x * TK, x = blockIdx.y;
     float2 *base = s + (int64_t)x * L * Lh + kz0;
-    for (int e = threadIdx.x; e < L * TK; e += blockDim.x) {
-        const int y = e / TK, l = e - y * TK;
-        a[y * TK + l] = kz0 + l < Lh ? base[(int64_t)y * Lh + l] : make_float2(0.f, 0.f);
-    }
+    const bool full = kz0 + TK <= Lh;
+    tile_load<TK>(a, base, Lh, L, full, Lh - kz0);
     __syncthreads();
-    const float2 *z = fft_lines<SIGN>(a, b, TK, TK, pl, stw);
-    for (int e = threadIdx.x; e < L * TK; e += blockDim.x) {
-        const int y = e / TK, l = e - y * TK;
-        if (kz0 + l < Lh) base[(int64_t)y * Lh + l] = z[y * TK + l];
+    const float2 *z = fft_lines<SIGN, TK>(a, b, TK, pl, stw);
+    for (int f = threadIdx.x; f < L * TK; f += blockDim.x) {
+        const int l = f & (TK - 1), y = f >> LG;
+        if (full || kz0 + l < Lh) base[(int64_t)y * Lh + l] = z[f];
     }
 }
 
@@ -340,29 +411,47 @@ __global__ void __launch_bounds__(256) k_fft_y(FftPlan pl, float2 *__restrict__ 
 // with D and the inverse FFT along x, in place.  Block (kz tile, y).
 // mode 0: energy only; 1: energy, D rho^ and the inverse along x written
 // back (forces); 2: the forward transform written back (no energy; tests).
-__global__ void __launch_bounds__(256) k_fft_x_spectral(FftPlan pl, float2 *__restrict__ s,
+template <int TK>
+__global__ void __launch_bounds__(512) k_fft_x_spectral(FftPlan pl, float2 *__restrict__ s,
                                                         const float *__restrict__ D, const float2 *__restrict__ tw,
                                                         int mode, double *__restrict__ part)
 {
     extern __shared__ float2 sm[];
-    __shared__ double sred[8];
-    const int L = pl.L, Lh = pl.Lh, TK = pl.tk;
+    __shared__ double sred[16];
+    constexpr int LG = TK == 16 ? 4 : 3;
+    const int L = pl.L, Lh = pl.Lh;
     float2 *stw = sm, *a = sm + L, *b = a + L * TK;
     load_twiddles(stw, tw, L);
     const int kz0 = blockIdx.x * TK, y = blockIdx.y;
     const int64_t pstride = (int64_t)L * Lh;          // between x planes
     float2 *base = s + (int64_t)y * Lh + kz0;
     const float *Db = D + (int64_t)y * Lh + kz0;
-    for (int e = threadIdx.x; e < L * TK; e += blockDim.x) {
-        const int x = e / TK, l = e - x * TK;
-        a[x * TK + l] = kz0 + l < Lh ? base[x * pstride + l] : make_float2(0.f, 0.f);
+    const bool full = kz0 + TK <= Lh;
+    float *sD = reinterpret_cast<float *>(b + L * TK);      // the D tile, loaded with the spectrum tile
+    tile_load<TK>(a, base, pstride, L, full, Lh - kz0);
+    if (mode != 2) {
+        const int tot = L * TK;
+        for (int f0 = threadIdx.x; f0 < tot; f0 += 8 * blockDim.x) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int f = f0 + u * blockDim.x;
+                const int l = f & (TK - 1), x = f >> LG;
+                v[u] = (f < tot && (full || kz0 + l < Lh)) ? Db[x * pstride + l] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int f = f0 + u * blockDim.x;
+                if (f < tot) sD[f] = v[u];
+            }
+        }
     }
     __syncthreads();
-    float2 *z = fft_lines<-1>(a, b, TK, TK, pl, stw);
+    float2 *z = fft_lines<-1, TK>(a, b, TK, pl, stw);
     if (mode == 2) {
-        for (int e = threadIdx.x; e < L * TK; e += blockDim.x) {
-            const int x = e / TK, l = e - x * TK;
-            if (kz0 + l < Lh) base[x * pstride + l] = z[x * TK + l];
+        for (int f = threadIdx.x; f < L * TK; f += blockDim.x) {
+            const int l = f & (TK - 1), x = f >> LG;
+            if (full || kz0 + l < Lh) base[x * pstride + l] = z[f];
         }
         return;
     }
@@ -370,15 +459,15 @@ __global__ void __launch_bounds__(256) k_fft_x_spectral(FftPlan pl, float2 *__re
     float2 *o = z == a ? b : a;
     const bool even = (L & 1) == 0;
     double en = 0.0;
-    for (int e = threadIdx.x; e < L * TK; e += blockDim.x) {
-        const int x = e / TK, l = e - x * TK;
+    for (int f = threadIdx.x; f < L * TK; f += blockDim.x) {
+        const int l = f & (TK - 1), x = f >> LG;
         const int kz = kz0 + l;
         if (kz >= Lh) continue;
-        const float d = Db[x * pstride + l];
-        float2 c = z[x * TK + l];
+        const float d = sD[f];
+        const float2 c = z[f];
         const float w = (kz == 0 || (even && kz == Lh - 1)) ? 1.f : 2.f;
         en += (double)(w * d * (c.x * c.x + c.y * c.y));
-        if (forces) z[x * TK + l] = cscale(c, d);
+        if (forces) z[f] = cscale(c, d);
     }
     // fixed-order block sum of the energy partials
 #pragma unroll
@@ -391,10 +480,10 @@ __global__ void __launch_bounds__(256) k_fft_x_spectral(FftPlan pl, float2 *__re
         part[blockIdx.y * gridDim.x + blockIdx.x] = t;
     }
     if (!forces) return;
-    z = fft_lines<1>(z, o, TK, TK, pl, stw);
-    for (int e = threadIdx.x; e < L * TK; e += blockDim.x) {
-        const int x = e / TK, l = e - x * TK;
-        if (kz0 + l < Lh) base[x * pstride + l] = z[x * TK + l];
+    z = fft_lines<1, TK>(z, o, TK, pl, stw);
+    for (int f = threadIdx.x; f < L * TK; f += blockDim.x) {
+        const int l = f & (TK - 1), x = f >> LG;
+        if (full || kz0 + l < Lh) base[x * pstride + l] = z[f];
     }
 }
 
@@ -436,6 +525,40 @@ bool fft_prepare(Handle &H, std::string &err)
     }
     pl.tk = L <= 512 ? 16 : 8;
     pl.zl = L <= 512 ? 8 : 4;
+    // division by p as (i mag) >> 20, checked for every index of the stage
+    for (int st = 0; st < pl.nst; ++st) {
+        const unsigned pp = (unsigned)pl.p[st];
+        pl.mag[st] = (unsigned)(((1u << 20) + pp - 1) / pp);
+        for (unsigned i = 0; i < (unsigned)L; ++i)
+            if (((i * pl.mag[st]) >> 20) != i / pp) {
+                err = "FFT index division check failed";
+                return false;
+            }
+    }
+    // threads per block: a multiple of 32 that divides the butterfly count of
+    // every stage (every thread busy in every stage) when one of 128 .. 512
+    // exists, else 256
+    auto pick = [&](int NL) {
+        int gg = 0;
+        for (int st = 0; st < pl.nst; ++st) gg = std::gcd(gg, NL * (L / pl.radix[st]));
+        for (int t = 512; t >= 128; t -= 32)
+            if (gg % t == 0) return t;
+        return 256;
+    };
+    pl.ty = pick(pl.tk);
+    pl.tz = pick(pl.zl);
+    // q / L and q / (L/2 + 1) as __umulhi(q, m), checked over the ranges used
+    auto magic = [&](unsigned d, unsigned qmax, unsigned &m) {
+        m = (unsigned)((1ull << 32) / d + 1);
+        for (unsigned q = 0; q < qmax; ++q)
+            if ((unsigned)(((unsigned long long)q * m) >> 32) != q / d) return false;
+        return true;
+    };
+    if (!magic((unsigned)L, (unsigned)(2 * pl.zl * L), pl.magL) ||
+        !magic((unsigned)pl.Lh, (unsigned)(2 * pl.zl * pl.Lh), pl.magLh)) {
+        err = "FFT index division check failed";
+        return false;
+    }
     std::vector<float2> tw(L);
     for (int e = 0; e < L; ++e) {
         const double ang = -2.0 * M_PI * (double)e / (double)L;
@@ -447,13 +570,26 @@ bool fft_prepare(Handle &H, std::string &err)
         return false;
     }
     H.device_bytes += (int64_t)sizeof(float2) * L;
-    const int sz = (int)(sizeof(float2) * (L + 2 * L * (pl.zl + 1)));
-    const int sy = (int)(sizeof(float2) * (L + 2 * L * pl.tk));
-    if (cudaFuncSetAttribute(k_fft_z_r2c, cudaFuncAttributeMaxDynamicSharedMemorySize, sz) != cudaSuccess ||
-        cudaFuncSetAttribute(k_fft_z_c2r, cudaFuncAttributeMaxDynamicSharedMemorySize, sz) != cudaSuccess ||
-        cudaFuncSetAttribute(k_fft_y<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sy) != cudaSuccess ||
-        cudaFuncSetAttribute(k_fft_y<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sy) != cudaSuccess ||
-        cudaFuncSetAttribute(k_fft_x_spectral, cudaFuncAttributeMaxDynamicSharedMemorySize, sy) != cudaSuccess) {
+    // the attribute belongs to the kernel, not to the handle: set the need of
+    // the largest grid of each tile regime (L = 512 and 1024), so that handles
+    // of other grid sizes keep launching
+    auto need_z = [](int Lx) { return (int)(sizeof(float2) * (Lx + 2 * Lx * ((Lx <= 512 ? 8 : 4) + 1))); };
+    auto need_y = [](int Lx) { return (int)(sizeof(float2) * (Lx + 2 * Lx * (Lx <= 512 ? 16 : 8))); };
+    auto need_x = [&](int Lx) { return need_y(Lx) + (int)(sizeof(float) * Lx * (Lx <= 512 ? 16 : 8)); };
+    const int sz = std::max(need_z(512), need_z(1024));
+    const int sy = std::max(need_y(512), need_y(1024));
+    const int sx = std::max(need_x(512), need_x(1024));
+    const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    if (cudaFuncSetAttribute(k_fft_z_r2c<8>, A, sz) != cudaSuccess ||
+        cudaFuncSetAttribute(k_fft_z_r2c<4>, A, sz) != cudaSuccess ||
+        cudaFuncSetAttribute(k_fft_z_c2r<8>, A, sz) != cudaSuccess ||
+        cudaFuncSetAttribute(k_fft_z_c2r<4>, A, sz) != cudaSuccess ||
+        cudaFuncSetAttribute(k_fft_y<-1, 16>, A, sy) != cudaSuccess ||
+        cudaFuncSetAttribute(k_fft_y<-1, 8>, A, sy) != cudaSuccess ||
+        cudaFuncSetAttribute(k_fft_y<1, 16>, A, sy) != cudaSuccess ||
+        cudaFuncSetAttribute(k_fft_y<1, 8>, A, sy) != cudaSuccess ||
+        cudaFuncSetAttribute(k_fft_x_spectral<16>, A, sx) != cudaSuccess ||
+        cudaFuncSetAttribute(k_fft_x_spectral<8>, A, sx) != cudaSuccess) {
         err = "cudaFuncSetAttribute (FFT shared memory)";
         return false;
     }
@@ -468,44 +604,64 @@ int spectral_blocks(const Handle &H)
 
 static size_t smem_z(const FftPlan &pl) { return sizeof(float2) * (pl.L + 2 * pl.L * (pl.zl + 1)); }
 static size_t smem_y(const FftPlan &pl) { return sizeof(float2) * (pl.L + 2 * pl.L * pl.tk); }
+static size_t smem_x(const FftPlan &pl) { return smem_y(pl) + sizeof(float) * pl.L * pl.tk; }
+
+static void launch_z(const FftPlan &pl, bool inverse, float *rho, float2 *spec, const float2 *tw, cudaStream_t s)
+{
+    const int nrows = pl.L * pl.L;
+    const unsigned nb = (unsigned)((nrows + 2 * pl.zl - 1) / (2 * pl.zl));
+    if (!inverse) {
+        if (pl.zl == 8) k_fft_z_r2c<8><<<nb, pl.tz, smem_z(pl), s>>>(pl, nrows, rho, spec, tw);
+        else k_fft_z_r2c<4><<<nb, pl.tz, smem_z(pl), s>>>(pl, nrows, rho, spec, tw);
+    } else {
+        if (pl.zl == 8) k_fft_z_c2r<8><<<nb, pl.tz, smem_z(pl), s>>>(pl, nrows, spec, rho, tw);
+        else k_fft_z_c2r<4><<<nb, pl.tz, smem_z(pl), s>>>(pl, nrows, spec, rho, tw);
+    }
+}
+
+template <int SIGN>
+static void launch_y(const FftPlan &pl, float2 *spec, const float2 *tw, cudaStream_t s)
+{
+    const dim3 g((pl.Lh + pl.tk - 1) / pl.tk, pl.L);
+    if (pl.tk == 16) k_fft_y<SIGN, 16><<<g, pl.ty, smem_y(pl), s>>>(pl, spec, tw);
+    else k_fft_y<SIGN, 8><<<g, pl.ty, smem_y(pl), s>>>(pl, spec, tw);
+}
+
+static void launch_x(const Handle &H, int mode, cudaStream_t s)
+{
+    const FftPlan &pl = H.fft;
+    const dim3 g((pl.Lh + pl.tk - 1) / pl.tk, pl.L);
+    float2 *spec = reinterpret_cast<float2 *>(H.d_rhohat);
+    double *part = H.d_part + H.part_off[kPartGlob];
+    if (pl.tk == 16) k_fft_x_spectral<16><<<g, pl.ty, smem_x(pl), s>>>(pl, spec, H.d_D, H.d_tw, mode, part);
+    else k_fft_x_spectral<8><<<g, pl.ty, smem_x(pl), s>>>(pl, spec, H.d_D, H.d_tw, mode, part);
+}
 
 cudaError_t launch_fft_forward(Handle &H, cudaStream_t s)
 {
-    const FftPlan &pl = H.fft;
-    const int nrows = pl.L * pl.L;
     float2 *spec = reinterpret_cast<float2 *>(H.d_rhohat);
-    k_fft_z_r2c<<<(nrows + 2 * pl.zl - 1) / (2 * pl.zl), 256, smem_z(pl), s>>>(pl, nrows, H.d_rho, spec, H.d_tw);
-    const dim3 g((pl.Lh + pl.tk - 1) / pl.tk, pl.L);
-    k_fft_y<-1><<<g, 256, smem_y(pl), s>>>(pl, spec, H.d_tw);
+    launch_z(H.fft, false, H.d_rho, spec, H.d_tw, s);
+    launch_y<-1>(H.fft, spec, H.d_tw, s);
     return cudaGetLastError();
 }
 
 cudaError_t launch_spectral(Handle &H, bool forces, cudaStream_t s)
 {
-    const FftPlan &pl = H.fft;
-    const dim3 g((pl.Lh + pl.tk - 1) / pl.tk, pl.L);
-    k_fft_x_spectral<<<g, 256, smem_y(pl), s>>>(pl, reinterpret_cast<float2 *>(H.d_rhohat), H.d_D, H.d_tw,
-                                                forces ? 1 : 0, H.d_part + H.part_off[kPartGlob]);
+    launch_x(H, forces ? 1 : 0, s);
     return cudaGetLastError();
 }
 
 static cudaError_t launch_forward_x_only(Handle &H, cudaStream_t s)
 {
-    const FftPlan &pl = H.fft;
-    const dim3 g((pl.Lh + pl.tk - 1) / pl.tk, pl.L);
-    k_fft_x_spectral<<<g, 256, smem_y(pl), s>>>(pl, reinterpret_cast<float2 *>(H.d_rhohat), H.d_D, H.d_tw, 2,
-                                                H.d_part + H.part_off[kPartGlob]);
+    launch_x(H, 2, s);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fft_inverse(Handle &H, cudaStream_t s)
 {
-    const FftPlan &pl = H.fft;
-    const int nrows = pl.L * pl.L;
     float2 *spec = reinterpret_cast<float2 *>(H.d_rhohat);
-    const dim3 g((pl.Lh + pl.tk - 1) / pl.tk, pl.L);
-    k_fft_y<1><<<g, 256, smem_y(pl), s>>>(pl, spec, H.d_tw);
-    k_fft_z_c2r<<<(nrows + 2 * pl.zl - 1) / (2 * pl.zl), 256, smem_z(pl), s>>>(pl, nrows, spec, H.d_phi, H.d_tw);
+    launch_y<1>(H.fft, spec, H.d_tw, s);
+    launch_z(H.fft, true, H.d_phi, spec, H.d_tw, s);
     return cudaGetLastError();
 }
 

@@ -525,7 +525,9 @@ bool tc_prepare(Handle &H, std::string &err)
         return false;
     }
     H.tc.grid = std::min(H.tc.tiles * H.tc.halves, sms);   // persistent: one CTA per SM
-    const int smem = (int)tc_smem_bytes(H.tc.N);
+    // the attribute belongs to the kernel, not to the handle: set the largest
+    // tile's need, so that handles of other tile widths keep launching
+    const int smem = (int)tc_smem_bytes(tcg::kMaxN);
     if (cudaFuncSetAttribute(k_corr_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
         cudaFuncSetAttribute(k_corr_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
         err = "cudaFuncSetAttribute (shared memory) failed";

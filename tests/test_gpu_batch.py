@@ -54,3 +54,23 @@ def test_batch_matches_single_boxes_and_reference(api):
             assert np.sqrt(np.mean((gx - ref) ** 2)) / rms < 3e-5
             assert np.max(np.abs(gx - ref)) / rms < 20 * 3e-5
     bt.close()
+
+
+def test_handles_of_different_sizes_coexist(api):
+    """Kernel launch attributes (dynamic shared memory) are per kernel, not per
+    handle: a handle whose FFT passes (192^3 grid) and tensor-core tiles (128
+    leaves) need more than the default shared memory keeps evaluating, bit for
+    bit, after handles with a small grid (12^3) and with narrower tiles (96
+    leaves) are created."""
+    import torch
+    f = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+    big = synth.config_box(2)
+    m1 = api.Ankh(big.box, big.n, n_cells=48, Lu=5)
+    E1 = m1.energy(f(big.x), f(big.q), f(big.mu), f(big.theta))
+    small = synth.small_box(200, 3, box=18.0)
+    others = [api.Ankh(small.box, small.n, n_cells=4, Lu=4), api.Ankh(small.box, small.n, n_cells=70, Lu=4)]
+    for m in others:
+        m.energy(f(small.x), f(small.q), f(small.mu), f(small.theta))
+    assert m1.energy(f(big.x), f(big.q), f(big.mu), f(big.theta)) == E1
+    for m in [m1] + others:
+        m.close()
