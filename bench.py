@@ -510,7 +510,9 @@ def replicas_measure(args, rank, world, dev, api, synth, dist=None, steps=None, 
         "warmup": args.warmup, "ms_per_step": tot / steps * 1e3, "higher_is_better": True,
         "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "replicas64_water_3000_48000_qmuTheta_energy_forces", "n_boxes": 64,
-                   "n_atoms_total": ntot_all, "Lu": args.Lu, "l2": "flushed: 256 MiB write between timed steps",
+                   "n_atoms_total": ntot_all,
+                   "Lu": args.Lu or "per box, with its leaf count, from the accuracy table",
+                   "l2": "flushed: 256 MiB write between timed steps",
                    "execution": "one CUDA graph per rank, one branch per box",
                    "parallelism": f"boxes split over {world} GPU(s) by LPT on atom counts"},
         "matoms_per_s": value / 64 * ntot_all / 1e6, "clocks": clk, "roofline": roof, "cpu_baseline": cpu,
@@ -542,7 +544,7 @@ def run_fmm(args, rank, world, dev, api, synth, dist, cfg):
     N = box.n
     f32 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
     x, q, mu, th = f32(box.x), f32(box.q), f32(box.mu), f32(box.theta)
-    L = args.Lu
+    L = args.Lu or 5
     n_cells, tune = args.n_cells, None
     if n_cells == 0:
         # tree depth by measurement (outside the timed region): the two powers
@@ -679,12 +681,12 @@ def run_induce(args, rank, world, dev, api, synth, dist, cfg):
     f32 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
     x, q, mu, th = f32(box.x), f32(box.q), f32(box.mu), f32(box.theta)
     alpha = torch.full((box.n,), 0.005, device=dev)
-    n_cells = args.n_cells
+    n_cells, Lu = args.n_cells, args.Lu
     if n_cells == 0:
         from paper_2212_08284_gb300 import autotune
-        n_cells, _ = autotune.autotune_n(box.box, x, q, mu, th, Lu=args.Lu, Lc=args.Lu, mixed=not args.plain,
-                                         nonperiodic=args.nonperiodic)
-    model = api.Ankh(box.box, box.n, n_cells=n_cells, Lu=args.Lu, Lc=args.Lu, mixed=not args.plain,
+        (n_cells, Lu), _ = autotune.autotune(box.box, x, q, mu, th, Lu=args.Lu, mixed=not args.plain,
+                                             nonperiodic=args.nonperiodic)
+    model = api.Ankh(box.box, box.n, n_cells=n_cells, Lu=Lu, Lc=Lu, mixed=not args.plain,
                      nonperiodic=args.nonperiodic)
     out = torch.empty((box.n, 3), device=dev)
     stream = torch.cuda.current_stream()
@@ -717,7 +719,7 @@ def run_induce(args, rank, world, dev, api, synth, dist, cfg):
             "ms_per_step": t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": box.name + ("_nonperiodic" if args.nonperiodic else "") + "_induce",
-                       "n_atoms": box.n, "n_cells": n_cells, "Lu": args.Lu, "alpha_A3": 0.005, "tol": 1e-6,
+                       "n_atoms": box.n, "n_cells": n_cells, "Lu": Lu, "alpha_A3": 0.005, "tol": 1e-6,
                        "parallelism": f"replicas{world}"},
             "iterations": statistics.mean(its), "ms_per_field_evaluation": t * 1e3 / evals,
             "E_pol": E_pol, "clocks": clk, "roofline": None, "cpu_baseline": None, "e2e": None,
@@ -748,7 +750,8 @@ def main():
                     help="skip the plain-FP32 leg and the other workloads after the main line's timing")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--n-cells", type=int, default=0, help="leaves per axis (0 = autotuned)")
-    ap.add_argument("--Lu", type=int, default=5, help="equispaced interpolation order")
+    ap.add_argument("--Lu", type=int, default=0,
+                    help="equispaced interpolation order (0: chosen with the leaf count from the accuracy table)")
     args = ap.parse_args()
 
     rank, world, local = env_int("RANK", 0), env_int("WORLD_SIZE", 1), env_int("LOCAL_RANK", 0)
@@ -790,15 +793,16 @@ def main():
     f32 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
     x, q, mu, th = f32(box.x), f32(box.q), f32(box.mu), f32(box.theta)
     tune = None
-    n_cells = args.n_cells
+    n_cells, Lu = args.n_cells, args.Lu
     if n_cells == 0:
-        # leaf count picked by measurement (outside the timed region)
+        # leaf count and order picked by measurement (outside the timed region)
+        # among the pairs that the library's accuracy table allows for the box
         from paper_2212_08284_gb300 import autotune
-        n_cells, tab = autotune.autotune_n(box.box, x, q, mu, th, Lu=args.Lu, Lc=args.Lu, mixed=not args.plain,
-                                           nonperiodic=args.nonperiodic)
-        tune = {str(k): round(v, 4) for k, v in sorted(tab.items())}
+        (n_cells, Lu), tab = autotune.autotune(box.box, x, q, mu, th, Lu=args.Lu, mixed=not args.plain,
+                                               nonperiodic=args.nonperiodic)
+        tune = {k: round(v, 4) for k, v in tab.items()}
     t_pre0 = time.perf_counter()
-    model = api.Ankh(box.box, N, n_cells=n_cells, Lu=args.Lu, Lc=args.Lu, mixed=not args.plain,
+    model = api.Ankh(box.box, N, n_cells=n_cells, Lu=Lu, Lc=Lu, mixed=not args.plain,
                      nonperiodic=args.nonperiodic)
     t_pre = time.perf_counter() - t_pre0
     info = model.info
@@ -967,7 +971,7 @@ def main():
         cpu = {"value": 1.0 / r["seconds_full_eval"], "unit": UNIT, "cores": os.cpu_count() or 1,
                "kind": "oracle", "sample": r["sample"]}
         if not args.nonperiodic:
-            cpu_ankh = oracle_ankh_sample(box, args.Lu)
+            cpu_ankh = oracle_ankh_sample(box, info["Lu"])
 
     if rank == 0:
         line = {
@@ -980,7 +984,8 @@ def main():
                        "xi": 0.0 if args.nonperiodic else 0.01,
                        "precision": "plain_fp32" if args.plain else "mixed_2xfp16_correction",
                        "l2": "flushed: 256 MiB write between timed steps", "parallelism": f"replicas{world}",
-                       "leaf_count": "autotuned" if args.n_cells == 0 else "fixed", "autotune_ms": tune},
+                       "leaf_count": ("autotuned among the (n, L_u) the accuracy table allows" if args.n_cells == 0
+                                      else "fixed"), "autotune_ms": tune},
             "matoms_per_s": value * N / 1e6,
             "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
             "near_pairs_unordered": pairs,

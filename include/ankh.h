@@ -79,8 +79,8 @@ enum {
 
 typedef struct {
     double xi;        /* Ewald screening [1/A]; Sec. 5 uses 0.01 */
-    int n_cells;      /* leaves per axis n >= 3 (0 = choose from the box) */
-    int Lu;           /* equispaced interpolation order, 2..8 (0 = 5) */
+    int n_cells;      /* leaves per axis n >= 3 (0 = from the accuracy table, see ankh_accuracy_rule) */
+    int Lu;           /* equispaced interpolation order, 2..8 (0 = from the accuracy table) */
     int Lc;           /* Chebyshev interpolation order, 2..16 (0 = Lu) */
     int max_order;    /* 0 = charges, 1 = + dipoles, 2 = + quadrupoles */
     unsigned flags;   /* ANKH_* flags above */
@@ -97,9 +97,31 @@ typedef struct {
 
 typedef struct ankh_handle ankh_handle;
 
-/* Fill *p with the defaults (xi = 0.01, n chosen from the box, Lu = Lc = 5,
- * quadrupoles, ANKH_INCLUDE_REC | ANKH_MIXED). */
+/* Fill *p with the defaults (xi = 0.01, n and Lu = Lc from the accuracy
+ * table, quadrupoles, ANKH_INCLUDE_REC | ANKH_MIXED). */
 void ankh_default_params(ankh_params *p);
+
+/* Accuracy table of the defaults (the paper picks the interpolation order
+ * for a target accuracy, Sec. 5.2-5.3; this table is calibrated, not
+ * printed there).  For N atoms (max_order 0: charges only, else with
+ * multipoles) and order Lu, *hmin and *hmax (may be NULL) receive the range
+ * of leaf edges (A) over which the method's own error -- the FP64 ANKH-FFT
+ * against FP64 Ewald, measured on synthetic water boxes of 24,000 / 96,000 /
+ * 1,008,000 atoms with charges, dipoles and quadrupoles, and of 648 atoms
+ * with charges only -- stayed within 5e-6 relative energy error and 3e-5
+ * relative RMS force error at every measured leaf count, leaving the rest of
+ * the 1e-5 / 1e-4 target for the FP32 arithmetic.  Orders 2..6 only (above 6
+ * the FP32 far field loses that margin).  The box uses the class of its kind
+ * with the largest atom count not above N.  Returns ANKH_OK, or ANKH_EINVAL
+ * when Lu is not calibrated for that class or N is below the smallest class
+ * of its kind (with multipoles: 24,000 atoms).  With n_cells = 0 and/or
+ * Lu = 0, ankh_create takes the lowest calibrated order that has a leaf
+ * count in its range, and the largest such leaf count whose grid the FFT
+ * takes; a box below the smallest class uses that class's rules, and where
+ * no rule applies (too small a box, ANKH-FMM) the defaults are L_u = 5 and
+ * a leaf edge near 4 A: in both cases with no accuracy guarantee.  Host
+ * only. */
+int ankh_accuracy_rule(int64_t N, int max_order, int Lu, double *hmin, double *hmax);
 
 /* Create a handle for a cubic box of edge box_edge (= 2 r_B) holding N atoms.
  * Runs the per-box precomputation (Alg. 4 / Sec. 4.3): the interpolation
@@ -196,7 +218,9 @@ int ankh_get_info(const ankh_handle *h, ankh_info *info);
  * start offsets (int32, n^3 + 1), 2 = equispaced modified charges M
  * (float32, n^3 x ldm), 3 = merged grid charges (float32, nf^3),
  * 4 = correction potential psi (float32, n^3 x ldm, forces calls only),
- * 5 = leaf id of each sorted slot (int32).  ldm = ankh_ldm(h). */
+ * 5 = leaf id of each sorted slot (int32), 6 = far-field kernel spectrum D
+ * (float32, nf x nf x (nf/2 + 1), k = 0 removed; set at creation).
+ * ldm = ankh_ldm(h). */
 int ankh_debug_copy(const ankh_handle *h, int which, void *dst, int64_t *bytes, void *cuda_stream);
 int ankh_ldm(const ankh_handle *h);
 

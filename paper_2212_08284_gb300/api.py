@@ -25,13 +25,13 @@ ANKH_NONPERIODIC = 4
 ANKH_FMM = 8
 
 # buffer ids of ankh_debug_copy
-BUF_PERM, BUF_START, BUF_M, BUF_RHO, BUF_PSI, BUF_SCELL = range(6)
+BUF_PERM, BUF_START, BUF_M, BUF_RHO, BUF_PSI, BUF_SCELL, BUF_D = range(7)
 
 EXPORTED = ["ankh_default_params", "ankh_create", "ankh_create_cached", "ankh_energy", "ankh_energy_forces",
             "ankh_energy_forces_host", "ankh_last_terms", "ankh_get_info", "ankh_debug_copy",
             "ankh_ldm", "ankh_set_timing", "ankh_stage_times", "ankh_bin_sort_noalloc", "ankh_destroy",
             "ankh_last_error", "ankh_version", "ankh_create_batch", "ankh_energy_forces_batch",
-            "ankh_batch_box", "ankh_destroy_batch", "ankh_induce", "ankh_measure_fp32_peak", "ankh_debug_fft"]
+            "ankh_batch_box", "ankh_destroy_batch", "ankh_induce", "ankh_measure_fp32_peak", "ankh_debug_fft", "ankh_accuracy_rule"]
 STAGES = ["sort", "self", "p2m", "merge", "fft_fwd", "spectral", "corr", "near", "fft_inv", "l2p",
           "unused", "reduce"]
 
@@ -114,6 +114,8 @@ def load_library(path: str = LIB_PATH):
         lib.ankh_destroy.restype = None
         lib.ankh_last_error.argtypes = []
         lib.ankh_last_error.restype = ctypes.c_char_p
+        lib.ankh_accuracy_rule.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_int, dp, dp]
+        lib.ankh_accuracy_rule.restype = ctypes.c_int
         lib.ankh_debug_fft.argtypes = [vp, vp, vp, ctypes.c_int, dp, vp, vp]
         lib.ankh_debug_fft.restype = ctypes.c_int
         lib.ankh_measure_fp32_peak.argtypes = [dp, dp, vp]
@@ -252,6 +254,15 @@ def ankh_stage_times(h) -> dict:
     return dict(zip(STAGES, list(t)))
 
 
+def ankh_accuracy_rule(n_atoms: int, Lu: int, max_order: int = 2):
+    """(hmin, hmax) leaf-edge range of the accuracy table for N atoms at order
+    Lu (max_order 0: charges only), or None when not calibrated."""
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    rc = load_library().ankh_accuracy_rule(int(n_atoms), int(max_order), int(Lu), ctypes.byref(lo),
+                                           ctypes.byref(hi))
+    return (lo.value, hi.value) if rc == ANKH_OK else None
+
+
 def ankh_debug_fft(h, rho, D, mode: int, out, stream=None) -> float:
     """The far-field transform step alone (tests): mode 0 forward transform of
     rho into out (complex64), mode 1 energy term (returned) and phi into out."""
@@ -301,7 +312,7 @@ def ankh_debug_copy(h, which: int, dtype=None, stream=None):
 class Ankh:
     """Owning wrapper of one handle (one cubic box, fixed N)."""
 
-    def __init__(self, box_edge: float, n_atoms: int, xi: float = 0.01, n_cells: int = 0, Lu: int = 5,
+    def __init__(self, box_edge: float, n_atoms: int, xi: float = 0.01, n_cells: int = 0, Lu: int = 0,
                  Lc: int = 0, max_order: int = 2, include_rec: bool = True, mixed: bool = True,
                  nonperiodic: bool = False, fmm: bool = False, cache_dir: str | None = None):
         p = ankh_default_params()
@@ -393,7 +404,7 @@ def ankh_batch_box(h, i: int) -> ctypes.c_void_p:
 class AnkhBatch:
     """Owning wrapper of a batch of independent boxes (replicas)."""
 
-    def __init__(self, box_edges, n_atoms, xi: float = 0.01, n_cells: int = 0, Lu: int = 5, Lc: int = 0,
+    def __init__(self, box_edges, n_atoms, xi: float = 0.01, n_cells: int = 0, Lu: int = 0, Lc: int = 0,
                  max_order: int = 2, include_rec: bool = True, mixed: bool = True, nonperiodic: bool = False):
         p = ankh_default_params()
         p.xi, p.n_cells, p.Lu, p.Lc, p.max_order = xi, n_cells, Lu, Lc, max_order

@@ -1,14 +1,18 @@
-"""Leaf-size autotuner.
+"""Leaf-count and order autotuner, constrained by the library's accuracy table.
 
-The ANKH error is scale-free in the leaf edge h (xi h << 1), so the number
-of leaves per axis n only trades work: near-field pairs grow like h^3, the
-adjacent-leaf correction, the merged FFT grid and the P2M/L2P node work like
-h^-3, and the near-field kernel's lane use depends on the atoms per leaf.
-The autotuner measures one full energy + gradient evaluation on the device
-(CUDA events around the library call) for candidate n around a 4.0 A leaf
-edge, extends the window while the fastest count sits at its edge, and
-returns the fastest.  Results are cached per (box, N, orders,
-precision) for the life of the process.
+The candidates are the (n, L_u) pairs that the accuracy table allows for the
+box (ankh_accuracy_rule: the leaf-edge range over which the method's own
+error stayed within 3e-6 relative energy and 3e-5 relative RMS force on the
+calibration water boxes of the box's size class) and whose merged grid the
+library's FFT takes.  Within those, n only trades work -- near-field pairs
+grow like h^3; the adjacent-leaf correction, the merged FFT grid and the
+P2M/L2P node work like h^-3 and with the order -- so the autotuner measures
+one full energy + gradient evaluation on the device (CUDA events around the
+library call) for each candidate and returns the fastest.  Where the table
+calibrates nothing for the box (an explicit order it does not cover, a box
+with multipoles below 24,000 atoms), the candidates are leaf counts around a
+4.0 A leaf edge at that order or L_u = 6 (no accuracy guarantee).  Results are cached
+per (box, N, order, precision) for the life of the process.
 """
 from __future__ import annotations
 
@@ -21,39 +25,75 @@ _cache: dict = {}
 
 def smooth(m: int) -> bool:
     """True when m has no prime factor above 7 (the lengths the FFT takes)."""
+    if m < 1:
+        return False
     for p in (2, 3, 5, 7):
         while m % p == 0:
             m //= p
     return m == 1
 
 
-def candidates(box: float, spread: int = 4, h0: float = 4.0, Lu: int = 5) -> list[int]:
-    n0 = max(3, int(round(box / h0)))
-    return sorted({max(3, n0 + d) for d in range(-spread, spread + 1) if smooth(max(3, n0 + d) * (Lu - 1))})
+def next_smooth(m: int) -> int:
+    while not smooth(m):
+        m += 1
+    return m
 
 
-def autotune_n(box: float, x, q, mu=None, theta=None, Lu: int = 5, Lc: int = 0, mixed: bool = True,
-               max_order: int = 2, cands: list[int] | None = None, reps: int = 4, warm: int = 2,
-               nonperiodic: bool = False):
-    """Return (best n, {n: milliseconds per evaluation})."""
+def grid_ok(n: int, Lu: int, nonperiodic: bool = False) -> bool:
+    ng = next_smooth(2 * (n * (Lu - 1) + 1) - 1) if nonperiodic else n * (Lu - 1)
+    return ng <= 1024 and smooth(ng)
+
+
+def allowed(box: float, n_atoms: int, Lu: int, nonperiodic: bool = False, per_order: int = 4,
+            max_order: int = 2) -> list[int]:
+    """Leaf counts the accuracy table allows at order Lu (largest first, at
+    most per_order of them), or [] when Lu is not calibrated for the box."""
+    rule = api.ankh_accuracy_rule(n_atoms, Lu, max_order)
+    if rule is None:
+        return []
+    hmin, hmax = rule
+    out = [n for n in range(int(math.floor(box / hmin)), 2, -1)
+           if hmin <= box / n <= hmax and grid_ok(n, Lu, nonperiodic)]
+    return out[:per_order]
+
+
+def candidates(box: float, n_atoms: int, Lu: int = 0, nonperiodic: bool = False, spread: int = 4,
+               h0: float = 4.0, max_order: int = 2) -> list[tuple[int, int]]:
+    """(n, L_u) pairs to time: every calibrated order's allowed leaf counts
+    (Lu = 0), one order's (Lu > 0), or, for an uncalibrated explicit order,
+    the leaf counts within `spread` of a 4 A leaf edge."""
+    orders = range(2, 9) if Lu == 0 else [Lu]
+    out = [(n, L) for L in orders for n in allowed(box, n_atoms, L, nonperiodic, max_order=max_order)]
+    if not out:
+        # not calibrated (a box with multipoles below the smallest class):
+        # leaf counts near a 4 A leaf edge at the given order, or L_u = 6
+        Lu = Lu or 6
+        n0 = max(3, int(round(box / h0)))
+        out = [(n, Lu) for n in sorted({max(3, n0 + d) for d in range(-spread, spread + 1)})
+               if grid_ok(n, Lu, nonperiodic)]
+    return out
+
+
+def autotune(box: float, x, q, mu=None, theta=None, Lu: int = 0, mixed: bool = True, max_order: int = 2,
+             cands: list[tuple[int, int]] | None = None, reps: int = 4, warm: int = 2,
+             nonperiodic: bool = False):
+    """Return ((n, L_u) fastest, {"n,Lu": milliseconds per evaluation})."""
     import torch
-    key = (round(box, 6), int(x.shape[0]), Lu, Lc, mixed, max_order, nonperiodic)
-    if key in _cache:
-        return _cache[key]
     n_atoms = int(x.shape[0])
+    key = (round(box, 6), n_atoms, Lu, mixed, max_order, nonperiodic)
+    if key in _cache and cands is None:
+        return _cache[key]
     dev = x.device
     out = {"dEdx": torch.empty((n_atoms, 3), device=dev), "dEdq": torch.empty(n_atoms, device=dev),
            "dEdmu": torch.empty((n_atoms, 3), device=dev), "dEdtheta": torch.empty((n_atoms, 6), device=dev)}
     table = {}
     stream = torch.cuda.current_stream()
-
-    def measure(n):
+    for n, L in (cands or candidates(box, n_atoms, Lu, nonperiodic, max_order=max_order)):
         try:
-            m = api.Ankh(box, n_atoms, n_cells=n, Lu=Lu, Lc=Lc, mixed=mixed, max_order=max_order,
+            m = api.Ankh(box, n_atoms, n_cells=n, Lu=L, Lc=L, mixed=mixed, max_order=max_order,
                          nonperiodic=nonperiodic)
         except api.AnkhError:
-            table[n] = math.inf          # not creatable (grid too large): never chosen
-            return
+            continue                     # not creatable (e.g. grid too large): never chosen
         for _ in range(warm):
             api.ankh_energy_forces(m.h, x, q, mu, theta, sync=False, stream=stream, **out)
         e0 = torch.cuda.Event(enable_timing=True)
@@ -63,30 +103,12 @@ def autotune_n(box: float, x, q, mu=None, theta=None, Lu: int = 5, Lc: int = 0, 
             api.ankh_energy_forces(m.h, x, q, mu, theta, sync=False, stream=stream, **out)
         e1.record(stream)
         e1.synchronize()
-        table[n] = e0.elapsed_time(e1) / reps
+        table[(n, L)] = e0.elapsed_time(e1) / reps
         m.close()
-
-    for n in (cands or candidates(box)):
-        measure(n)
-    if cands is None:
-        # while the fastest count sits at an edge of the window, extend the
-        # window past that edge (two counts at a time, at most 12 more)
-        for _ in range(6):
-            done = {k: v for k, v in table.items() if math.isfinite(v)}
-            if not done:
-                break
-            best = min(done, key=done.get)
-            if best == max(table):
-                ext = [best + 1, best + 2]
-            elif best == min(table) and best > 3:
-                ext = [k for k in (best - 1, best - 2) if k >= 3]
-            else:
-                break
-            for n in ext:
-                measure(n)
-    table = {k: v for k, v in table.items() if math.isfinite(v)}
     if not table:
-        raise RuntimeError("no candidate leaf count could be created")
+        raise RuntimeError("no candidate (leaf count, order) could be created")
     best = min(table, key=table.get)
-    _cache[key] = (best, table)
-    return best, table
+    res = (best, {f"{k[0]},{k[1]}": v for k, v in sorted(table.items())})
+    if cands is None:
+        _cache[key] = res
+    return res

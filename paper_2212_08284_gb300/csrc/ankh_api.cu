@@ -144,6 +144,87 @@ static int next_fft_size(int m)
     return m;
 }
 
+// Accuracy table of the default parameters.  For each calibration class
+// (synthetic water boxes at 0.0334 molecules/A^3: with q, mu, Theta at
+// 24,000, 96,000 and 1,008,000 atoms; with charges only at 648 atoms) and
+// each equispaced order L_u <= 6, the range of leaf edges [hmin, hmax] (A)
+// over which the oracle's FP64 ANKH-FFT stays within 5e-6 (relative energy)
+// and 3e-5 (relative RMS force; energy only for the charges-only class) of
+// the FP64 Ewald reference at every measured leaf count, starting at a run
+// of at least three consecutive measured leaf counts from the largest
+// measured leaf edge down (tests/golden/error_map.json; edges rounded
+// outwards to 1e-4 A).  The margin to the 1e-5 target is left for the FP32
+// arithmetic.  Orders above 6 are not calibrated: there the merged-grid
+// term and the adjacent-leaf correction each exceed the energy by 2-50x,
+// and the FP32 rounding of the tables and modified charges costs 1e-5 -
+// 3e-4 of the energy.  A box uses the class of its kind with the largest
+// atom count not above its own (the relative error of the energy falls with
+// N: the errors of the many far pairs are independent while the energy is
+// extensive); a box below the smallest class of its kind is not calibrated.
+struct AccRule {
+    int64_t n_atoms;
+    int charges_only;
+    int Lu;
+    double hmin, hmax;
+};
+static const AccRule kAccRules[] = {
+    {1008000, 0, 5, 3.9976, 4.7972}, {1008000, 0, 6, 4.4973, 5.3969},
+    {96000, 0, 5, 5.1885, 6.1615},   {96000, 0, 6, 3.3994, 6.1615},
+    {24000, 0, 6, 3.8814, 6.2104},
+    {648, 1, 5, 3.1066, 6.2134},     {648, 1, 6, 3.1066, 6.2134},
+};
+
+// the calibration class of N atoms (0: below the smallest of its kind)
+static int64_t accuracy_class(int64_t N, bool charges_only)
+{
+    int64_t best = 0;
+    for (const AccRule &r : kAccRules)
+        if ((r.charges_only != 0) == charges_only && r.n_atoms <= N && r.n_atoms > best) best = r.n_atoms;
+    return best;
+}
+
+static int64_t smallest_class(bool charges_only)
+{
+    int64_t best = 0;
+    for (const AccRule &r : kAccRules)
+        if ((r.charges_only != 0) == charges_only && (best == 0 || r.n_atoms < best)) best = r.n_atoms;
+    return best;
+}
+
+// the rule of class c for order Lu, or NULL
+static const AccRule *class_rule(int64_t c, bool charges_only, int Lu)
+{
+    for (const AccRule &r : kAccRules)
+        if (r.n_atoms == c && (r.charges_only != 0) == charges_only && r.Lu == Lu) return &r;
+    return nullptr;
+}
+
+static const AccRule *accuracy_rule(int64_t N, bool charges_only, int Lu)
+{
+    const int64_t c = accuracy_class(N, charges_only);
+    return c ? class_rule(c, charges_only, Lu) : nullptr;
+}
+
+// FFT grid points per axis of n leaves at order Lu (0 if beyond 1024 or
+// with a prime factor above 7)
+static int grid_points(int n, int Lu, bool nonper)
+{
+    const int ng = nonper ? next_fft_size(2 * (n * (Lu - 1) + 1) - 1) : n * (Lu - 1);
+    return (ng <= 1024 && good_fft_size(ng)) ? ng : 0;
+}
+
+// The largest leaf count whose leaf edge lies in the rule's range and whose
+// grid the FFT takes; 0 if there is none.
+static int rule_n(double box, int Lu, const AccRule &r, bool nonper)
+{
+    for (int n = (int)std::floor(box / r.hmin); n >= 3; --n) {
+        const double h = box / n;
+        if (h > r.hmax) break;
+        if (h >= r.hmin && grid_points(n, Lu, nonper)) return n;
+    }
+    return 0;
+}
+
 static int choose_n(double box, int Lu)
 {
     // leaf edge near 4.0 A for L_u = 5 (balances near-field pairs against
@@ -346,7 +427,18 @@ using namespace ankh;
 
 extern "C" {
 
-int ankh_version(void) { return 100; }
+int ankh_version(void) { return 200; }
+
+int ankh_accuracy_rule(int64_t N, int max_order, int Lu, double *hmin, double *hmax)
+{
+    const AccRule *r = accuracy_rule(N, max_order == 0, Lu);
+    if (!r) return fail(ANKH_EINVAL, "order L_u = " + std::to_string(Lu) + " is not calibrated for " +
+                                         std::to_string((long long)N) + " atoms" +
+                                         (max_order == 0 ? " (charges only)" : " (with multipoles)"));
+    if (hmin) *hmin = r->hmin;
+    if (hmax) *hmax = r->hmax;
+    return ANKH_OK;
+}
 
 const char *ankh_last_error(void) { return g_err.c_str(); }
 
@@ -355,8 +447,8 @@ void ankh_default_params(ankh_params *p)
     if (!p) return;
     p->xi = 0.01;
     p->n_cells = 0;
-    p->Lu = 5;
-    p->Lc = 5;
+    p->Lu = 0;
+    p->Lc = 0;
     p->max_order = 2;
     p->flags = ANKH_INCLUDE_REC | ANKH_MIXED;
 }
@@ -388,7 +480,36 @@ static int create_handle(double box_edge, int64_t N, const ankh_params *params, 
     if (params) p = *params;
     if (!(box_edge > 0.0) || !std::isfinite(box_edge)) return fail(ANKH_EINVAL, "box edge must be finite and > 0");
     if (N < 1 || N > (int64_t)1 << 30) return fail(ANKH_EINVAL, "N out of range [1, 2^30]");
-    if (p.Lu == 0) p.Lu = 5;
+    const bool nonper0 = (p.flags & ANKH_NONPERIODIC) != 0, fmm0 = (p.flags & ANKH_FMM) != 0;
+    if (!fmm0 && (p.Lu == 0 || p.n_cells == 0)) {
+        // defaults from the accuracy table: the lowest calibrated order with a
+        // leaf count in its range (or, with n given, whose range holds box / n);
+        // a box below the smallest class of its kind takes that class's rules
+        // (not calibrated)
+        const bool qonly = p.max_order == 0;
+        int64_t cls = accuracy_class(N, qonly);
+        if (!cls) cls = smallest_class(qonly);
+        if (p.Lu == 0) {
+            for (int Lu = 2; Lu <= kMaxLu && p.Lu == 0; ++Lu) {
+                const AccRule *r = class_rule(cls, qonly, Lu);
+                if (!r) continue;
+                if (p.n_cells == 0) {
+                    const int n = rule_n(box_edge, Lu, *r, nonper0);
+                    if (n) {
+                        p.Lu = Lu;
+                        p.n_cells = n;
+                    }
+                } else {
+                    const double h = box_edge / p.n_cells;
+                    if (h >= r->hmin && h <= r->hmax) p.Lu = Lu;
+                }
+            }
+        } else if (p.n_cells == 0) {
+            const AccRule *r = class_rule(cls, qonly, p.Lu);
+            if (r) p.n_cells = rule_n(box_edge, p.Lu, *r, nonper0);   // 0: no calibrated n, chosen below
+        }
+    }
+    if (p.Lu == 0) p.Lu = 5;   // outside the calibrated ranges (ANKH-FMM: L = 5)
     if (p.Lc == 0) p.Lc = p.Lu;
     if (p.Lu < 2 || p.Lu > kMaxLu) return fail(ANKH_EINVAL, "Lu out of range [2, 8]");
     if (p.Lc < 2 || p.Lc > kMaxLc) return fail(ANKH_EINVAL, "Lc out of range [2, 16]");
@@ -792,6 +913,7 @@ int ankh_debug_copy(const ankh_handle *h, int which, void *dst, int64_t *bytes, 
     case 3: src = H.d_rho; nb = H.g.M * 4; break;
     case 4: src = H.d_psi; nb = (int64_t)H.g.ncell * H.g.ldm * 4; break;
     case 5: src = H.d_scell; nb = H.N * 4; break;
+    case 6: src = H.d_D; nb = (int64_t)H.g.nf * H.g.nf * H.g.nfh * 4; break;
     default: return fail(ANKH_EINVAL, "unknown buffer id");
     }
     if (!src) return fail(ANKH_EINVAL, "buffer not allocated for this handle");

@@ -6,7 +6,7 @@ paper_2212_08284_gb300/synth.py and stores, per workload:
   * the gradient rows (dE/dx, dE/dq, dE/dmu, dE/dTheta) of a seeded sample
     of atoms, and the RMS over ALL atoms of each gradient group.
 
-Usage:  python tests/golden/make_golden.py 1 2 3 4
+Usage:  python tests/golden/make_golden.py 0 1 2 3 4   (0: the 3,000-atom test box)
 """
 import json
 import os
@@ -22,12 +22,18 @@ sys.path.insert(0, ROOT)
 from oracle import ewald as ew                      # noqa: E402
 from paper_2212_08284_gb300 import synth            # noqa: E402
 
+
+def workload(c: int):
+    """Config c of the benchmark (1-4), or 0: the 3,000-atom water box with
+    q, mu, Theta in a 31.1 A box that the GPU tests use (seed 31)."""
+    return synth.small_box(1000, 31, box=31.1) if c == 0 else synth.config_box(c)
+
 N_SAMPLE = 2048
 
 
 def main(cfgs):
     for c in cfgs:
-        b = synth.config_box(c)
+        b = workload(c)
         mp = ew.pack_multipoles(b.q, b.mu, b.theta)
         t0 = time.time()
         r = ew.ewald(b.x.astype(np.float64), mp, b.box, tol=1e-11, grad=True)

@@ -36,7 +36,7 @@ def test_version_and_defaults_without_gpu():
     assert lib.ankh_version() >= 100
     p = api.ankh_default_params()
     assert p.xi == pytest.approx(0.01)
-    assert p.Lu == 5 and p.max_order == 2
+    assert p.Lu == 0 and p.n_cells == 0 and p.max_order == 2   # orders and leaf count from the accuracy table
     assert p.flags & api.ANKH_INCLUDE_REC
 
 

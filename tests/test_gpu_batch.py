@@ -18,14 +18,15 @@ def api(gpu):
     return A
 
 
-def test_batch_matches_single_boxes_and_reference(api):
+@pytest.mark.parametrize("Lu", [5, 0], ids=["Lu5", "defaults"])
+def test_batch_matches_single_boxes_and_reference(api, Lu):
     import torch
     sizes = [1000, 2200, 1500, 3600, 1200, 2700, 1800, 3000]        # waters per box
     boxes = [synth.water_box(w, 9000 + i, multipoles=True, name=f"b{i}") for i, w in enumerate(sizes)]
     cat = lambda f: torch.from_numpy(np.ascontiguousarray(np.concatenate([f(b) for b in boxes]),
                                                           dtype=np.float32)).cuda()
     x, q, mu, th = cat(lambda b: b.x), cat(lambda b: b.q), cat(lambda b: b.mu), cat(lambda b: b.theta)
-    bt = api.AnkhBatch([b.box for b in boxes], [b.n for b in boxes], Lu=5)
+    bt = api.AnkhBatch([b.box for b in boxes], [b.n for b in boxes], Lu=Lu)
     E1, g1 = bt.energy_forces(x, q, mu, th, torques=True)
     # new output buffers (new capture), then the same buffers again (graph replay)
     g2 = {k: torch.empty_like(v) for k, v in g1.items()}
@@ -38,15 +39,19 @@ def test_batch_matches_single_boxes_and_reference(api):
     off = np.concatenate([[0], np.cumsum([b.n for b in boxes])])
     for i, b in enumerate(boxes):
         info = api.ankh_get_info(api.ankh_batch_box(bt.h, i))
-        m = api.Ankh(b.box, b.n, n_cells=info["n_cells"], Lu=5)
+        m = api.Ankh(b.box, b.n, n_cells=info["n_cells"], Lu=info["Lu"])
         f = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
         Es, gs = m.energy_forces(f(b.x), f(b.q), f(b.mu), f(b.theta), torques=True)
         assert Es == E1[i]
         for k in gs:
             assert torch.equal(gs[k], g1[k][off[i]:off[i + 1]])
         m.close()
-        if i in (0, 3):
-            o = ar.ankh_energy(b.x, b.q, b.mu, b.theta, ar.Params(b.box, info["n_cells"], 5, 5), grad=True)
+        # parity with the FP64 reference at matched parameters: at L_u = 5 (the
+        # default orders of these 3,000-10,800-atom boxes are outside the
+        # calibrated range, where the FP32 correction can lose the 2e-6 bar)
+        if Lu == 5 and i in (0, 3):
+            o = ar.ankh_energy(b.x, b.q, b.mu, b.theta, ar.Params(b.box, info["n_cells"], info["Lu"], info["Lu"]),
+                               grad=True)
             assert E1[i] == pytest.approx(o["E"], rel=2e-6)
             gx = g1["dEdx"][off[i]:off[i + 1]].cpu().numpy().astype(np.float64)
             ref = o["grad"][:, :3]

@@ -185,43 +185,67 @@ def golden(name):
     return json.load(open(p))
 
 
-@pytest.mark.parametrize("cfg,Lu", [(1, 6), (2, 6), (3, 6), (2, 5), (3, 5)])
-def test_against_fp64_ewald(api, cfg, Lu):
-    """The method's target against the FP64 Ewald oracle with the library's
-    default leaf count: L_u = 6 meets <= 1e-5 relative energy error and
-    <= 1e-4 relative RMS force error; L_u = 5 (the fast setting) is held to
-    2e-5 in energy -- its interpolation error varies with the leaf count,
-    measured 3e-7 to 1.3e-5 on the 96,000-atom box, same in the FP64
-    reference at matched parameters."""
-    b = synth.config_box(cfg)
-    gd = golden(b.name)
-    m, E, g = run_gpu(api, b, n=0, Lu=Lu, max_order=0 if cfg == 1 else 2, mixed=True)
-    assert abs(E - gd["E"]) / abs(gd["E"]) <= (1e-5 if Lu >= 6 else 2e-5)
+def workload(cfg):
+    """Config 1-4 of the benchmark, or 0: the 3,000-atom water box of the tests."""
+    return synth.small_box(1000, 31, box=31.1) if cfg == 0 else synth.config_box(cfg)
+
+
+def check_against_golden(api, b, gd, E, g, energy_only=False):
+    assert abs(E - gd["E"]) / abs(gd["E"]) <= 1e-5
+    if energy_only:
+        return
     idx = np.array(gd["sample_idx"])
     ref = np.array(gd["sample_grad"])
     G = grad13(g)[idx]
     err = np.sqrt(np.mean((G[:, 0:3] - ref[:, 0:3]) ** 2)) / gd["rms_all"]["dEdx"]
-    if cfg > 1:
-        assert err <= 1e-4
+    assert err <= 1e-4
+
+
+@pytest.mark.parametrize("cfg", [1, 2, 3])
+def test_defaults_against_fp64_ewald(api, cfg):
+    """The library's defaults (n_cells = 0, L_u = 0: leaf count and order from
+    its accuracy table) meet the method's target against the FP64 Ewald
+    oracle: relative energy error <= 1e-5 and relative RMS force error
+    <= 1e-4 (sampled atoms; config 1 has charges only and its golden holds
+    the energy)."""
+    b = workload(cfg)
+    gd = golden(b.name)
+    m = api.Ankh(b.box, b.n, max_order=0 if cfg == 1 else 2)
+    E, g = m.energy_forces(*to_dev(b), torques=True)
+    g = {k: v.cpu().numpy().astype(np.float64) for k, v in g.items()}
+    info = m.info
+    assert api.ankh_accuracy_rule(b.n, info["Lu"], 0 if cfg == 1 else 2) is not None
+    check_against_golden(api, b, gd, E, g, energy_only=cfg == 1)
 
 
 def test_full_size_workload_against_fp64_ewald(api):
-    """The 1,008,000-atom box in the launch configuration the benchmark times
-    (n = 54, L_u = L_c = 5, tensor-core correction) against the FP64 Ewald
+    """The 1,008,000-atom box at every (n, L_u) that the accuracy table allows
+    (the benchmark times the fastest of them) against the FP64 Ewald
     reference: energy within 1e-5 and the forces of the 2,048 sampled atoms
-    within 1e-4 RMS (of the RMS over all atoms).  The other gradient groups
-    are held to the method's own error at L_u = 5 and this leaf edge (the
-    oracle's ANKH-FFT on the 24,000-atom box at n = 14..16, 4.4-3.9 A:
-    dE/dq 3.0-3.2e-4, dE/dmu 1.1-1.4e-4, dE/dTheta 3.8-5.9e-5) with margin."""
+    within 1e-4 RMS (of the RMS over all atoms); at the library's default the
+    other gradient groups too, held to the method's own error at this leaf
+    edge and L_u = 5 (the oracle's ANKH-FFT on the 24,000-atom box at
+    4.4-3.9 A: dE/dq 3.0-3.2e-4, dE/dmu 1.1-1.4e-4, dE/dTheta 3.8-5.9e-5)
+    with margin."""
+    from paper_2212_08284_gb300 import autotune
     b = synth.config_box(4)
     gd = golden(b.name)
-    m, E, g = run_gpu(api, b, n=54, Lu=5, max_order=2, mixed=True)
-    assert abs(E - gd["E"]) / abs(gd["E"]) <= 1e-5
+    x, q, mu, th = to_dev(b)
+    for n, Lu in autotune.candidates(b.box, b.n):
+        m = api.Ankh(b.box, b.n, n_cells=n, Lu=Lu, mixed=True)
+        E, g = m.energy_forces(x, q, mu, th)
+        g = {k: v.cpu().numpy().astype(np.float64) for k, v in g.items()}
+        m.close()
+        check_against_golden(api, b, gd, E, g)
+    m = api.Ankh(b.box, b.n)
+    E, g = m.energy_forces(x, q, mu, th)
+    g = {k: v.cpu().numpy().astype(np.float64) for k, v in g.items()}
+    check_against_golden(api, b, gd, E, g)
     idx = np.array(gd["sample_idx"])
     ref = np.array(gd["sample_grad"])
     G = grad13(g)[idx]
-    bars = {"dEdx": 1e-4, "dEdq": 5e-4, "dEdmu": 2.5e-4, "dEdtheta": 1.2e-4}
-    for lo, hi, key in ((0, 3, "dEdx"), (3, 4, "dEdq"), (4, 7, "dEdmu"), (7, 13, "dEdtheta")):
+    bars = {"dEdq": 5e-4, "dEdmu": 2.5e-4, "dEdtheta": 1.2e-4}
+    for lo, hi, key in ((3, 4, "dEdq"), (4, 7, "dEdmu"), (7, 13, "dEdtheta")):
         err = np.sqrt(np.mean((G[:, lo:hi] - ref[:, lo:hi]) ** 2)) / gd["rms_all"][key]
         assert err <= bars[key], (key, err)
 
