@@ -104,6 +104,10 @@ def autotune(box: float, x, q, mu=None, theta=None, Lu: int = 0, mixed: bool = T
         e1.record(stream)
         e1.synchronize()
         table[(n, L)] = e0.elapsed_time(e1) / reps
+        # one call that reads the energy and the error flag: a kernel that ran
+        # into a bounded wait (ANKH_ETIMEOUT) or a numeric error stops the
+        # search here instead of after every candidate
+        api.ankh_energy_forces(m.h, x, q, mu, theta, stream=stream, **out)
         m.close()
     if not table:
         raise RuntimeError("no candidate (leaf count, order) could be created")
