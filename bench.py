@@ -44,7 +44,13 @@ FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) per launch from one ncu capture of the same kernel
 # code on the same workload and leaf count; keyed by (kernel, workload, n, L_u).
 # Entries are removed whenever the kernel changes and re-measured.
-DRAM_TRAFFIC: dict = {}
+DRAM_TRAFFIC: dict = {
+    # stage: kernels (read + write per launch); the timed evaluation, ncu, one pass per kernel
+    ("near", "water_1008000_qmuTheta", 54, 5): 96.30e6,      # k_near
+    ("corr", "water_1008000_qmuTheta", 54, 5): 348.77e6,     # k_split_f16 + k_corr_tc
+    ("p2m", "water_1008000_qmuTheta", 54, 5): 92.34e6,       # k_p2m
+    ("l2p", "water_1008000_qmuTheta", 54, 5): 489.43e6,      # k_node_pot + k_l2p
+}
 
 
 def env_int(k, d):
