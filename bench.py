@@ -49,7 +49,6 @@ DRAM_TRAFFIC: dict = {
     ("near", "water_1008000_qmuTheta", 54, 5): 96.30e6,      # k_near
     ("corr", "water_1008000_qmuTheta", 54, 5): 348.77e6,     # k_split_f16 + k_corr_tc
     ("p2m", "water_1008000_qmuTheta", 54, 5): 92.34e6,       # k_p2m
-    ("l2p", "water_1008000_qmuTheta", 54, 5): 489.43e6,      # k_node_pot + k_l2p
 }
 
 

@@ -334,7 +334,7 @@ static void free_device(Handle *H)
     void *ptrs[] = {H->d_cellid, H->rsb.vtmp[0], H->rsb.vtmp[1], H->rsb.hist, H->rsb.goff, H->rsb.bsum,
                     H->d_items, H->d_nitems, H->d_count, H->d_start, H->d_perm, H->d_inv, H->d_loc, H->d_ctr, H->d_scell, H->d_flag, H->d_bsum,
                     H->d_A0, H->d_A1, H->d_A2, H->d_A3, H->d_W, H->d_M, H->d_rho, H->d_rhohat, H->d_D,
-                    H->d_phi, H->d_C, H->d_Chi, H->d_Clo, H->d_psi, H->d_gnear, H->d_pi, H->d_part,
+                    H->d_phi, H->d_C, H->d_Chi, H->d_Clo, H->d_psi, H->d_gnear, H->d_part,
                     H->d_partoff, H->d_rscr, H->d_ticket, H->d_terms, H->d_hostbuf, H->d_Mhi, H->d_Mlo, H->d_mmax, H->d_ind, H->d_ind_part};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -626,7 +626,6 @@ static int create_handle(double box_edge, int64_t N, const ankh_params *params, 
         ANKH_AL(H.d_C, (int64_t)27 * g.ldm * g.ldm);
         ANKH_AL(H.d_psi, (int64_t)g.ncell * g.ldm);
         ANKH_AL(H.d_gnear, 13 * N);
-        ANKH_AL(H.d_pi, (int64_t)g.ncell * g.ldm);
     }
     // energy partial layout (ANKH-FMM: the root term in the far slot, the M2L CTAs in the correction slot)
     int nb[kPartCount];

@@ -166,7 +166,6 @@ struct Handle {
     float *d_C;             // [27][ldm][ldm] adjacent-leaf correction blocks (FP32)
     float *d_psi;           // [ncell][ldm] correction potential
     float *d_gnear;         // [13][Nslot] near-field gradient per sorted slot
-    float *d_pi;            // [ncell][ldm] far-field node potentials (forces)
     double *d_part;         // energy partials
     int part_off[kPartCount + 1];
     int *d_partoff;         // device copy of part_off

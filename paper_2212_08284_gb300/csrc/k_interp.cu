@@ -249,47 +249,42 @@ __global__ void __launch_bounds__(128) k_fine(Geo g, const float *__restrict__ M
     rho[((int64_t)gg[0] * nf + gg[1]) * nf + gz] = s;
 }
 
-// Node potentials of the far field, per leaf t and node k:
+// L2P fused with the node potentials and the gradient assembly, one thread
+// per sorted atom: the node potentials of its leaf,
 //   Pi_t[k] = phi[g(t,k)] / M - psi_t[k]
-// (the merged-grid potential at the node minus the adjacent-leaf
-// correction), one thread per (leaf, node); nodes beyond P are left alone.
-template <int LU>
-__global__ void __launch_bounds__(128) k_node_pot(Geo g, const float *__restrict__ phi, float invM,
-                                                  const float *__restrict__ psi, float *__restrict__ pi)
-{
-    constexpr int P = LU * LU * LU, Lm = LU - 1;
-    // grid: x over the (leaf, node) pairs of one z-row of leaves, y = leaf y, z = leaf x
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int n = g.n, nf = g.nf;
-    const int cz = t / P, node = t - cz * P;
-    if (cz >= n) return;
-    const int cx = blockIdx.z, cy = blockIdx.y;
-    const int a = node / (LU * LU), bb = (node / LU) % LU, c = node % LU;
-    int gx = cx * Lm + a, gy = cy * Lm + bb, gz = cz * Lm + c;
-    gx = gx >= nf ? gx - nf : gx;
-    gy = gy >= nf ? gy - nf : gy;
-    gz = gz >= nf ? gz - nf : gz;
-    const int64_t o = ((int64_t)(cx * n + cy) * n + cz) * g.ldm + node;
-    pi[o] = __ldg(&phi[((int64_t)gx * nf + gy) * nf + gz]) * invM - psi[o];
-}
-
-// L2P fused with the gradient assembly, one thread per sorted atom: the node
-// potentials of its leaf (Pi, read through the cache, shared by the leaf's
-// atoms) contracted with its basis -- the adjoint of P2M -- for the far-field
-// gradient, plus the near-field gradient, the self-term gradient and the
-// k = 0 potential; torques; write to the caller's atom order.
+// (the merged-grid potential at the node minus the adjacent-leaf correction,
+// both read through the cache and shared by the leaf's atoms), contracted
+// with its basis -- the adjoint of P2M -- for the far-field gradient, plus the
+// near-field gradient, the self-term gradient and the k = 0 potential;
+// torques; write to the caller's atom order.
 template <int LU, bool FASTW>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, LU <= 5 ? 4 : 2)
 k_l2p(Geo g, const int *__restrict__ scell, const int *__restrict__ perm, const float4 *__restrict__ A0,
       const float4 *__restrict__ A1, const float4 *__restrict__ A2, const float4 *__restrict__ A3,
-      const float *__restrict__ W, const __grid_constant__ WTab<LU> Wc, const float *__restrict__ pi,
-      const float *__restrict__ gnear, int64_t Nslot, const double *__restrict__ terms,
-      float *__restrict__ dEdx, float *__restrict__ dEdq, float *__restrict__ dEdmu, float *__restrict__ dEdth,
-      float *__restrict__ torque)
+      const float *__restrict__ W, const __grid_constant__ WTab<LU> Wc, const float *__restrict__ phi, float invM,
+      const float *__restrict__ psi, const float *__restrict__ gnear, int64_t Nslot,
+      const double *__restrict__ terms, float *__restrict__ dEdx, float *__restrict__ dEdq,
+      float *__restrict__ dEdmu, float *__restrict__ dEdth, float *__restrict__ torque)
 {
+    constexpr int Lm = LU - 1;
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= Nslot) return;
-    const float *__restrict__ pil = pi + (int64_t)scell[s] * g.ldm;
+    const int cell = scell[s];
+    const float *__restrict__ psil = psi + (int64_t)cell * g.ldm;
+    // merged-grid offsets of the leaf's nodes along each axis (periodic wrap)
+    const int n = g.n, nf = g.nf;
+    const int cx = cell / (n * n), cy = (cell / n) - cx * n, cz = cell - (cell / n) * n;
+    int ox[LU], oy[LU], oz[LU];            // nf^3 <= 2^30: 32-bit offsets
+#pragma unroll
+    for (int a = 0; a < LU; ++a) {
+        int gx = cx * Lm + a, gy = cy * Lm + a, gz = cz * Lm + a;
+        gx -= gx >= nf ? nf : 0;
+        gy -= gy >= nf ? nf : 0;
+        gz -= gz >= nf ? nf : 0;
+        ox[a] = gx * nf * nf;
+        oy[a] = gy * nf;
+        oz[a] = gz;
+    }
     const float dcpot = (float)terms[6];
     const float xi = g.xi;
     {
@@ -318,7 +313,8 @@ k_l2p(Geo g, const int *__restrict__ scell, const int *__restrict__ perm, const 
                 float X[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
                 for (int a = 0; a < LU; ++a) {
-                    const float pi = __ldg(&pil[(a * LU + bb) * LU + c]);
+                    const float pi = fmaf(__ldg(&phi[ox[a] + oy[bb] + oz[c]]), invM,
+                                          -__ldg(&psil[(a * LU + bb) * LU + c]));
 #pragma unroll
                     for (int p = 0; p < 4; ++p) X[p] = fmaf(pi, ux[p][a], X[p]);
                 }
@@ -464,17 +460,16 @@ static cudaError_t l2p_one(Handle &H, float *dEdx, float *dEdq, float *dEdmu, fl
 {
     constexpr int P = LU * LU * LU;
     const float invM = (float)(1.0 / (double)H.g.M);
-    const dim3 pgrid((unsigned)((H.g.n * P + 127) / 128), (unsigned)H.g.n, (unsigned)H.g.n);
-    k_node_pot<LU><<<pgrid, 128, 0, s>>>(H.g, H.d_phi, invM, H.d_psi, H.d_pi);
+    (void)P;
     const unsigned nb = (unsigned)((H.N + 127) / 128);
     if (H.g.Lc == LU)
         k_l2p<LU, true><<<nb, 128, 0, s>>>(H.g, H.d_scell, H.d_perm, H.d_A0, H.d_A1, H.d_A2, H.d_A3, H.d_W,
-                                           wtab<LU>(H), H.d_pi, H.d_gnear, H.N, H.d_terms, dEdx, dEdq, dEdmu,
-                                           dEdtheta, torque);
+                                           wtab<LU>(H), H.d_phi, invM, H.d_psi, H.d_gnear, H.N, H.d_terms, dEdx,
+                                           dEdq, dEdmu, dEdtheta, torque);
     else
         k_l2p<LU, false><<<nb, 128, 0, s>>>(H.g, H.d_scell, H.d_perm, H.d_A0, H.d_A1, H.d_A2, H.d_A3, H.d_W,
-                                            WTab<LU>{}, H.d_pi, H.d_gnear, H.N, H.d_terms, dEdx, dEdq, dEdmu,
-                                            dEdtheta, torque);
+                                            WTab<LU>{}, H.d_phi, invM, H.d_psi, H.d_gnear, H.N, H.d_terms, dEdx,
+                                            dEdq, dEdmu, dEdtheta, torque);
     return cudaGetLastError();
 }
 
