@@ -334,7 +334,7 @@ static void free_device(Handle *H)
     void *ptrs[] = {H->d_cellid, H->rsb.vtmp[0], H->rsb.vtmp[1], H->rsb.hist, H->rsb.goff, H->rsb.bsum,
                     H->d_items, H->d_nitems, H->d_count, H->d_start, H->d_perm, H->d_inv, H->d_loc, H->d_ctr, H->d_scell, H->d_flag, H->d_bsum,
                     H->d_A0, H->d_A1, H->d_A2, H->d_A3, H->d_W, H->d_M, H->d_rho, H->d_rhohat, H->d_D,
-                    H->d_phi, H->d_C, H->d_Chi, H->d_Clo, H->d_psi, H->d_gnear, H->d_part,
+                    H->d_phi, H->d_C, H->d_Chi, H->d_Clo, H->d_ChiE, H->d_CloE, H->d_psi, H->d_gnear, H->d_part,
                     H->d_partoff, H->d_rscr, H->d_ticket, H->d_terms, H->d_hostbuf, H->d_Mhi, H->d_Mlo, H->d_mmax, H->d_ind, H->d_ind_part};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -718,6 +718,25 @@ static int create_handle(double box_edge, int64_t N, const ankh_params *params, 
         if (cudaMemcpy(H.d_Chi, Ah.data(), Ah.size() * sizeof(__half), cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(H.d_Clo, Al.data(), Al.size() * sizeof(__half), cudaMemcpyHostToDevice) != cudaSuccess)
             return bail(ANKH_ECUDA, "upload tensor-core blocks");
+        // energy alone: [C_13 | 2 C_14 | ... | 2 C_26] (d = 0 and the 13 positive
+        // offsets; doubling an fp16 value is exact)
+        const int64_t acolsE = (int64_t)14 * ldk;
+        ANKH_AL(H.d_ChiE, arows * acolsE);
+        ANKH_AL(H.d_CloE, arows * acolsE);
+        std::vector<__half> AhE((size_t)(arows * acolsE)), AlE(AhE.size());
+        for (int64_t m = 0; m < arows; ++m)
+            for (int jd = 0; jd < 14; ++jd) {
+                const float w = jd == 0 ? 1.f : 2.f;
+                for (int l = 0; l < ldk; ++l) {
+                    const size_t src = (size_t)m * acols + (size_t)(13 + jd) * ldk + l;
+                    const size_t dst = (size_t)m * acolsE + (size_t)jd * ldk + l;
+                    AhE[dst] = __float2half_rn(w * __half2float(Ah[src]));
+                    AlE[dst] = __float2half_rn(w * __half2float(Al[src]));
+                }
+            }
+        if (cudaMemcpy(H.d_ChiE, AhE.data(), AhE.size() * sizeof(__half), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(H.d_CloE, AlE.data(), AlE.size() * sizeof(__half), cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(ANKH_ECUDA, "upload tensor-core blocks (energy)");
         std::string terr;
         if (!tc_prepare(H, terr)) return bail(ANKH_ECUDA, terr);
     }

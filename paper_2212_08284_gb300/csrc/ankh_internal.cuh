@@ -86,6 +86,7 @@ struct TcPlan {
     int eC;                 // C_d scaled by 2^eC before the fp16 split
     uint32_t tmem_cols;
     CUtensorMap mAhi, mAlo, mBhi, mBlo;
+    CUtensorMap mAhiE, mAloE;   // energy-only operator [C_0 | 2 C_d, d > 0] (14 blocks)
 };
 
 // ANKH-FMM (fmm.cu): perfect octree of depth E, L Chebyshev nodes per axis per cell.
@@ -131,6 +132,7 @@ struct Handle {
     FmmPlan fmm;
     __half *d_Mhi, *d_Mlo;  // [n*n*rowstride][ldk] fp16 split of 2^eM M, z-halo rows (tensor-core path)
     __half *d_Chi, *d_Clo;  // [halves*128][27*ldk] fp16 split of 2^eC [C_0 | ... | C_26]
+    __half *d_ChiE, *d_CloE;  // [halves*128][14*ldk] the same of [C_13 | 2 C_14 | ... | 2 C_26] (energy alone)
     unsigned *d_mmax;       // max |M| of the call (FP32 bits), sets eM (ANKH-FMM: one per level)
     float *d_ind;           // induced-dipole workspace (allocated on first use)
     double *d_ind_part;

@@ -112,8 +112,8 @@ __global__ void __launch_bounds__(kCorrThreads, 1)
 k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
           const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo, Geo g, int S,
           int R, int rowstride, int ldk, int eC, const unsigned *__restrict__ mmax, int ntiles, int nwork,
-          uint32_t tmem_cols, const float *__restrict__ M, float *__restrict__ psi, double *__restrict__ part,
-          int *__restrict__ errflag)
+          int d0, int noff, uint32_t tmem_cols, const float *__restrict__ M, float *__restrict__ psi,
+          double *__restrict__ part, int *__restrict__ errflag)
 {
     using namespace tcg;
     extern __shared__ unsigned char smem_raw[];
@@ -135,7 +135,7 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ldm = g.ldm;
     const int kch = ldk / kKc;            // K chunks per offset d
-    const int kIters = 27 * kch;          // stages per work item
+    const int kIters = noff * kch;        // stages per work item
     const int nmine = blockIdx.x < nwork ? (nwork - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -184,7 +184,9 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
                 cxr[r] = zrow / n;
                 cyr[r] = zrow - cxr[r] * n;
             }
-            for (int d = 0; d < 27 && !stop; ++d) {
+            for (int jd = 0; jd < noff && !stop; ++jd) {
+                // offset d = d0 + jd; its operator block is column block jd of A
+                const int d = d0 + jd;
                 const int dx = d / 9 - 1, dy = (d / 3) % 3 - 1, dz = d % 3 - 1;
                 int brow[8];
 #pragma unroll
@@ -211,8 +213,8 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
                     }
                     unsigned char *st = smem + (size_t)s * stage;
                     mbar_expect_tx(&full[s], stage);
-                    tma_2d(st, &tmAhi, &full[s], d * ldk + kc * kKc, row0);
-                    tma_2d(st + kABytes, &tmAlo, &full[s], d * ldk + kc * kKc, row0);
+                    tma_2d(st, &tmAhi, &full[s], jd * ldk + kc * kKc, row0);
+                    tma_2d(st + kABytes, &tmAlo, &full[s], jd * ldk + kc * kKc, row0);
 #pragma unroll
                     for (int r = 0; r < 8; ++r) {
                         if (r < R) {
@@ -517,6 +519,8 @@ bool tc_prepare(Handle &H, std::string &err)
     const int ldk = H.tc.ldk;
     if (!encode_2d(&H.tc.mAhi, H.d_Chi, 27 * (uint64_t)ldk, arows, tcg::kKc, 128, err)) return false;
     if (!encode_2d(&H.tc.mAlo, H.d_Clo, 27 * (uint64_t)ldk, arows, tcg::kKc, 128, err)) return false;
+    if (!encode_2d(&H.tc.mAhiE, H.d_ChiE, 14 * (uint64_t)ldk, arows, tcg::kKc, 128, err)) return false;
+    if (!encode_2d(&H.tc.mAloE, H.d_CloE, 14 * (uint64_t)ldk, arows, tcg::kKc, 128, err)) return false;
     if (!encode_2d(&H.tc.mBhi, H.d_Mhi, ldk, rows, tcg::kKc, (uint32_t)S, err)) return false;
     if (!encode_2d(&H.tc.mBlo, H.d_Mlo, ldk, rows, tcg::kKc, (uint32_t)S, err)) return false;
     int sms = 0;
@@ -556,14 +560,18 @@ cudaError_t launch_corr_tc(Handle &H, bool forces, cudaStream_t s)
     const size_t smem = tc_smem_bytes(H.tc.N);
     double *part = H.d_part + H.part_off[kPartCorr];
     const int nwork = H.tc.tiles * H.tc.halves;
-#define ANKH_CORR_LAUNCH(F)                                                                                     \
-    k_corr_tc<F><<<H.tc.grid, kCorrThreads, smem, s>>>(H.tc.mAhi, H.tc.mAlo, H.tc.mBhi, H.tc.mBlo, H.g, H.tc.S,  \
-                                                        H.tc.R, H.tc.rowstride, H.tc.ldk, H.tc.eC, H.d_mmax,      \
-                                                        H.tc.tiles, nwork, H.tc.tmem_cols, H.d_M, H.d_psi, part,  \
-                                                        H.d_flag)
-    if (forces) ANKH_CORR_LAUNCH(true);
-    else ANKH_CORR_LAUNCH(false);
-#undef ANKH_CORR_LAUNCH
+    // forces: all 27 offsets (psi at every leaf); energy alone: d = 0 and the 13
+    // positive offsets against [C_0 | 2 C_d], since C_(-d) = C_d^T
+    if (forces)
+        k_corr_tc<true><<<H.tc.grid, kCorrThreads, smem, s>>>(H.tc.mAhi, H.tc.mAlo, H.tc.mBhi, H.tc.mBlo, H.g,
+                                                               H.tc.S, H.tc.R, H.tc.rowstride, H.tc.ldk, H.tc.eC,
+                                                               H.d_mmax, H.tc.tiles, nwork, 0, 27, H.tc.tmem_cols,
+                                                               H.d_M, H.d_psi, part, H.d_flag);
+    else
+        k_corr_tc<false><<<H.tc.grid, kCorrThreads, smem, s>>>(H.tc.mAhiE, H.tc.mAloE, H.tc.mBhi, H.tc.mBlo, H.g,
+                                                                H.tc.S, H.tc.R, H.tc.rowstride, H.tc.ldk, H.tc.eC,
+                                                                H.d_mmax, H.tc.tiles, nwork, 13, 14, H.tc.tmem_cols,
+                                                                H.d_M, H.d_psi, part, H.d_flag);
     return cudaGetLastError();
 }
 

@@ -164,6 +164,10 @@ def test_energy_and_gradient_match_fp64_ankh(api, case, mixed):
     m, E, g = run_gpu(api, b, n=n, Lu=Lu, Lc=Lc, max_order=order, mixed=mixed, xi=xi)
     o = ar.ankh_energy(b.x, b.q, b.mu, b.theta, ar.Params(b.box, n, Lu, Lc, xi=xi))
     assert E == pytest.approx(o["E"], rel=2e-6)
+    # the energy-only call (correction over d = 0 and the 13 positive offsets)
+    E_only = m.energy(*to_dev(b))
+    assert E_only == pytest.approx(o["E"], rel=2e-6)
+    m.energy_forces(*to_dev(b))          # the terms below are those of the forces call
     t = m.terms()
     assert t["near"] == pytest.approx(o["E_near"], rel=2e-6)
     far_gpu = t["far"] + t["far_k0"] + t["correction"]
@@ -291,7 +295,9 @@ def test_wrapping_and_determinism(api):
     E1e = m.energy(x, q, mu, th)
     E3 = m.energy(torch.from_numpy(xs_np).cuda(), q, mu, th)
     assert E3 == E1e
-    assert E1e == pytest.approx(E1, rel=1e-7)
+    # the energy-only call sums the correction over d = 0 and the 13 positive
+    # offsets (C_(-d) = C_d^T), the forces call over all 27: equal to rounding
+    assert E1e == pytest.approx(E1, rel=1e-6)
 
 
 def test_nonfinite_input_reports_enumeric(api):
