@@ -129,19 +129,6 @@ def radix_passes(ncell: int) -> int:
     return (B + 9) // 10
 
 
-def launches_per_step(ncell: int, plain: bool) -> int:
-    """Kernels of one energy + gradient evaluation: bin, leaf scan (2), radix
-    sort (histogram, 2 scan kernels, scatter per pass), gather, k = 0 term,
-    P2M, merge, spectral product, [fp16 split,] correction, near field, node
-    potentials, L2P, energy reduction (cuFFT's two transforms not counted)."""
-    return 1 + 2 + 4 * radix_passes(ncell) + 1 + 1 + 1 + 1 + 1 + (0 if plain else 1) + 1 + 1 + 1 + 1 + 1
-
-
-def batch_box_cells(api, bt, i: int) -> int:
-    """Leaves per axis of box i of a batch."""
-    return int(api.ankh_get_info(api.ankh_batch_box(bt.h, i))["n_cells"])
-
-
 def preroll(clocks, step, seconds=0.4):
     """Start the clock sampler and run the untimed step for `seconds` so that
     the samples (and the clocks) are those of the loaded GPU; marks the start
@@ -524,8 +511,7 @@ def replicas_measure(args, rank, world, dev, api, synth, dist=None, steps=None, 
         "e2e": {"value": 64 * e2e_steps / t_e2e, "unit": "box-evals/s",
                 "h2d_bytes_per_step": 4 * ntot * (3 + 1 + 3 + 6),
                 "d2h_bytes_per_step": 4 * ntot * (3 + 1 + 3 + 6 + 3)},
-        "gpu_launches": sum(launches_per_step(batch_box_cells(api, bt, i) ** 3, args.plain)
-                            for i in range(len(boxes))) * steps}
+        "gpu_launches": api.ankh_batch_launch_count(bt.h) * steps}
     bt.close()
     return line
 
@@ -730,7 +716,7 @@ def run_induce(args, rank, world, dev, api, synth, dist, cfg):
             "E_pol": E_pol, "clocks": clk, "roofline": None, "cpu_baseline": None, "e2e": None,
             # per solve: one evaluation's kernels per field evaluation (iterations + 2
             # of them), 3 vector kernels per iteration, 3 outside the loop
-            "gpu_launches": int(round(args.steps * (launches_per_step(n_cells ** 3, args.plain)
+            "gpu_launches": int(round(args.steps * (api.ankh_launch_count(model.h, True)
                                                     * (statistics.mean(its) + 2) + 3 * statistics.mean(its) + 3)))}),
               flush=True)
     model.close()
@@ -1005,7 +991,7 @@ def main():
                     "d2h_bytes_per_step": d2h},
             "plain_fp32": plain_leg,
             "other_configs": legs,
-            "gpu_launches": launches_per_step(ncell, args.plain) * args.steps,
+            "gpu_launches": api.ankh_launch_count(model.h, True) * args.steps,
         }
         print(json.dumps(line), flush=True)
     model.close()

@@ -212,6 +212,13 @@ int ankh_last_terms(const ankh_handle *h, double terms[6]);
 
 int ankh_get_info(const ankh_handle *h, ankh_info *info);
 
+/* Kernels launched by one evaluation on h (forces != 0: ankh_energy_forces,
+ * else ankh_energy) into *count: the count the library's launch sequence
+ * issues, from its plan (digit passes of the leaf sort, the fp16 split of
+ * the tensor-core correction).  Errors: ANKH_EINVAL (NULL, or an ANKH_FMM
+ * handle). */
+int ankh_launch_count(const ankh_handle *h, int forces, int *count);
+
 /* Copy an internal device buffer of the last call into caller memory dst
  * (device pointer, at least *bytes long; with dst == NULL only *bytes is
  * set).  which: 0 = permutation (int32, sorted slot -> atom), 1 = leaf
@@ -239,6 +246,11 @@ int ankh_create_batch(int nbox, const double *box_edges, const int64_t *n_atoms,
 int ankh_energy_forces_batch(ankh_batch *b, const float *x, const float *q, const float *mu,
                              const float *theta, double *E_host, float *dEdx, float *dEdq, float *dEdmu,
                              float *dEdtheta, float *torque, void *cuda_stream);
+/* Kernels launched by one ankh_energy_forces_batch call into *count: every
+ * box's evaluation without its near field, plus one near-field launch over
+ * all boxes per group sharing xi and the near-field kernel variant.
+ * Errors: ANKH_EINVAL (NULL). */
+int ankh_batch_launch_count(const ankh_batch *b, int *count);
 /* Borrow the handle of box i (owned by the batch; do not destroy it). */
 int ankh_batch_box(const ankh_batch *b, int i, ankh_handle **h);
 void ankh_destroy_batch(ankh_batch *b);

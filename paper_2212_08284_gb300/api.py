@@ -31,7 +31,8 @@ EXPORTED = ["ankh_default_params", "ankh_create", "ankh_create_cached", "ankh_en
             "ankh_energy_forces_host", "ankh_last_terms", "ankh_get_info", "ankh_debug_copy",
             "ankh_ldm", "ankh_set_timing", "ankh_stage_times", "ankh_bin_sort_noalloc", "ankh_destroy",
             "ankh_last_error", "ankh_version", "ankh_create_batch", "ankh_energy_forces_batch",
-            "ankh_batch_box", "ankh_destroy_batch", "ankh_induce", "ankh_measure_fp32_peak", "ankh_debug_fft", "ankh_accuracy_rule"]
+            "ankh_batch_box", "ankh_destroy_batch", "ankh_induce", "ankh_measure_fp32_peak", "ankh_debug_fft", "ankh_accuracy_rule",
+            "ankh_launch_count", "ankh_batch_launch_count"]
 STAGES = ["sort", "self", "p2m", "merge", "fft_fwd", "spectral", "corr", "near", "fft_inv", "l2p",
           "unused", "reduce"]
 
@@ -108,6 +109,10 @@ def load_library(path: str = LIB_PATH):
         lib.ankh_energy_forces_batch.restype = ctypes.c_int
         lib.ankh_batch_box.argtypes = [vp, ctypes.c_int, ctypes.POINTER(vp)]
         lib.ankh_batch_box.restype = ctypes.c_int
+        lib.ankh_launch_count.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+        lib.ankh_launch_count.restype = ctypes.c_int
+        lib.ankh_batch_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+        lib.ankh_batch_launch_count.restype = ctypes.c_int
         lib.ankh_destroy_batch.argtypes = [vp]
         lib.ankh_destroy_batch.restype = None
         lib.ankh_destroy.argtypes = [vp]
@@ -393,6 +398,20 @@ def ankh_energy_forces_batch(h, nbox: int, x, q, mu=None, theta=None, dEdx=None,
                                                    _ptr(dEdq), _ptr(dEdmu), _ptr(dEdtheta), _ptr(torque),
                                                    _stream_ptr(stream)))
     return list(E)
+
+
+def ankh_launch_count(h, forces: bool) -> int:
+    """Kernels one evaluation on h launches (the library's own count)."""
+    out = ctypes.c_int()
+    _check(load_library().ankh_launch_count(h, 1 if forces else 0, ctypes.byref(out)))
+    return int(out.value)
+
+
+def ankh_batch_launch_count(b) -> int:
+    """Kernels one batched evaluation launches."""
+    out = ctypes.c_int()
+    _check(load_library().ankh_batch_launch_count(b, ctypes.byref(out)))
+    return int(out.value)
 
 
 def ankh_batch_box(h, i: int) -> ctypes.c_void_p:

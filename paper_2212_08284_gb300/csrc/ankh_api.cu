@@ -406,6 +406,42 @@ int run_sequence(Handle &H, const float *x, const float *q, const float *mu, con
     return ANKH_OK;
 }
 
+// The evaluation of run_sequence (energy + forces) in three parts, for the
+// batch: the sort and self terms; the far field up to the adjacent-leaf
+// correction; after the near field, the inverse transform, L2P and the energy
+// reduction.
+static int run_part_sort(Handle &H, const float *x, const float *q, const float *mu, const float *theta,
+                         cudaStream_t s)
+{
+    ANKH_CU(launch_bin(H, x, s), "bin");
+    ANKH_CU(launch_scan(H, s), "scan");
+    ANKH_CU(launch_scatter_sort_gather(H, x, q, mu, theta, s), "sort");
+    ANKH_CU(launch_self_dc(H, s), "self");
+    return ANKH_OK;
+}
+
+static int run_part_far(Handle &H, cudaStream_t s)
+{
+    ANKH_CU(launch_p2m(H, s), "p2m");
+    ANKH_CU(launch_fine_gather(H, s), "merge");
+    ANKH_CU(launch_fft_forward(H, s), "forward FFT");
+    ANKH_CU(launch_spectral(H, true, s), "spectral");
+    if (H.tc.enabled && (H.flags & ANKH_MIXED))
+        ANKH_CU(launch_corr_tc(H, true, s), "corr (tensor cores)");
+    else
+        ANKH_CU(launch_corr(H, true, s), "corr");
+    return ANKH_OK;
+}
+
+static int run_part_adjoint(Handle &H, float *dEdx, float *dEdq, float *dEdmu, float *dEdtheta, float *torque,
+                            cudaStream_t s)
+{
+    ANKH_CU(launch_fft_inverse(H, s), "inverse FFT");
+    ANKH_CU(launch_l2p(H, dEdx, dEdq, dEdmu, dEdtheta, torque, s), "l2p");
+    ANKH_CU(launch_reduce(H, s), "reduce");
+    return ANKH_OK;
+}
+
 int fetch_terms(Handle &H, double *E_host, cudaStream_t s)
 {
     ANKH_CU(cudaMemcpyAsync(H.h_terms, H.d_terms, 9 * sizeof(double), cudaMemcpyDeviceToHost, s), "copy E");
@@ -889,6 +925,22 @@ int ankh_get_info(const ankh_handle *h, ankh_info *info)
 
 int ankh_ldm(const ankh_handle *h) { return h ? h->h.g.ldm : 0; }
 
+// Kernels of one ANKH-FFT evaluation as run_sequence issues them: bin, leaf
+// scan (2), radix sort (histogram, 2 scan kernels, scatter per digit pass),
+// gather, k = 0 term, P2M, merge, forward FFT along z and y, the pass along x
+// with the spectral sum, [fp16 split,] correction, near field, and with
+// forces the inverse FFT along y and z and L2P; then the energy reduction.
+// The cudaMemsetAsync of the split exponent is not a kernel.
+static int launch_count(const Handle &H, bool forces, bool with_near)
+{
+    int k = 1 + 2 + 4 * H.rs.npass + 1 + 1 + 1 + 1 + 2 + 1;
+    if (H.tc.enabled && (H.flags & ANKH_MIXED)) k += 1;
+    k += 1;                    // correction
+    if (with_near) k += 1;
+    if (forces) k += 3;
+    return k + 1;              // reduction
+}
+
 int ankh_set_timing(ankh_handle *h, int enable)
 {
     if (!h) return fail(ANKH_EINVAL, "handle is NULL");
@@ -950,6 +1002,9 @@ int ankh_debug_copy(const ankh_handle *h, int which, void *dst, int64_t *bytes, 
 
 struct ankh_batch {
     std::vector<ankh_handle *> boxes;
+    std::vector<NearBatch> near_groups;  // one near-field launch per kernel variant (usually one)
+    cudaStream_t nearst = nullptr;       // stream of the batched near field
+    cudaEvent_t ev_near = nullptr;
     std::vector<int64_t> off;            // atom offsets, nbox + 1
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> joins;
@@ -965,6 +1020,9 @@ struct ankh_batch {
 static void batch_free(ankh_batch *b)
 {
     if (!b) return;
+    for (auto &g : b->near_groups) near_batch_free(g);
+    if (b->ev_near) cudaEventDestroy(b->ev_near);
+    if (b->nearst) cudaStreamDestroy(b->nearst);
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     for (auto e : b->joins) cudaEventDestroy(e);
@@ -1016,11 +1074,60 @@ int ankh_create_batch(int nbox, const double *box_edges, const int64_t *n_atoms,
         batch_free(b);
         return fail(ANKH_ENOMEM, "batch event / pinned buffer");
     }
+    for (auto h : b->boxes)
+        if (h->h.fmm.enabled) {
+            batch_free(b);
+            return fail(ANKH_EINVAL, "a batch computes forces; ANKH_FMM computes the energy only (Alg. 3)");
+        }
+    // the near field of all boxes in one launch per kernel variant
+    if (cudaStreamCreateWithFlags(&b->nearst, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_near, cudaEventDisableTiming) != cudaSuccess) {
+        batch_free(b);
+        return fail(ANKH_ECUDA, "batch near-field stream / event");
+    }
+    // boxes sharing xi and the B0 evaluation share a kernel variant
+    std::vector<bool> grouped(b->boxes.size(), false);
+    for (size_t i = 0; i < b->boxes.size(); ++i) {
+        if (grouped[i]) continue;
+        const Handle &Hi = b->boxes[i]->h;
+        std::vector<Handle *> hs;
+        for (size_t j = i; j < b->boxes.size(); ++j) {
+            Handle &Hj = b->boxes[j]->h;
+            if (!grouped[j] && Hj.g.xi == Hi.g.xi && near_mode(Hj) == near_mode(Hi)) {
+                hs.push_back(&Hj);
+                grouped[j] = true;
+            }
+        }
+        NearBatch nbt;
+        std::string err;
+        if (!near_batch_tables(hs.data(), (int)hs.size(), nbt, err)) {
+            batch_free(b);
+            return fail(ANKH_ENOMEM, err);
+        }
+        b->near_groups.push_back(nbt);
+    }
     *out = b;
     return ANKH_OK;
 }
 
 void ankh_destroy_batch(ankh_batch *b) { batch_free(b); }
+
+int ankh_launch_count(const ankh_handle *h, int forces, int *count)
+{
+    if (!h || !count) return fail(ANKH_EINVAL, "NULL argument");
+    if (h->h.fmm.enabled) return fail(ANKH_EINVAL, "ANKH_FMM handles are not counted");
+    *count = launch_count(h->h, forces != 0, true);
+    return ANKH_OK;
+}
+
+int ankh_batch_launch_count(const ankh_batch *b, int *count)
+{
+    if (!b || !count) return fail(ANKH_EINVAL, "NULL argument");
+    int k = (int)b->near_groups.size();
+    for (auto h : b->boxes) k += launch_count(h->h, true, false);
+    *count = k;
+    return ANKH_OK;
+}
 
 int ankh_batch_box(const ankh_batch *b, int i, ankh_handle **h)
 {
@@ -1050,14 +1157,35 @@ int ankh_energy_forces_batch(ankh_batch *b, const float *x, const float *q, cons
         const int ns = (int)b->streams.size();
         for (int k = 0; k < ns; ++k) cudaStreamWaitEvent(b->streams[k], b->fork, 0);
         int rc = ANKH_OK;
+        auto at = [](const float *p, int64_t o, int k) { return p ? p + k * o : nullptr; };
+        auto atw = [](float *p, int64_t o, int k) { return p ? p + k * o : nullptr; };
+        // (1) every box's sort and self terms on its stream
+        for (size_t i = 0; i < b->boxes.size() && rc == ANKH_OK; ++i) {
+            Handle &H = b->boxes[i]->h;
+            const int64_t o = b->off[i];
+            rc = run_part_sort(H, x + 3 * o, q + o, at(mu, o, 3), at(theta, o, 6), b->streams[i % ns]);
+        }
+        // (2) once every sort is done, the near field of all boxes in one
+        // launch per kernel variant, on its own stream, concurrent with (3)
+        for (int k = 0; k < ns; ++k) {
+            cudaEventRecord(b->joins[k], b->streams[k]);
+            cudaStreamWaitEvent(b->nearst, b->joins[k], 0);
+        }
+        for (auto &g : b->near_groups)
+            if (rc == ANKH_OK && launch_near_batch(g, true, b->nearst) != cudaSuccess)
+                rc = fail(ANKH_ECUDA, "batched near field");
+        cudaEventRecord(b->ev_near, b->nearst);
+        // (3) every box's far field up to the adjacent-leaf correction
+        for (size_t i = 0; i < b->boxes.size() && rc == ANKH_OK; ++i)
+            rc = run_part_far(b->boxes[i]->h, b->streams[i % ns]);
+        // (4) after the near field: inverse transform, L2P and energy per box
+        for (int k = 0; k < ns; ++k) cudaStreamWaitEvent(b->streams[k], b->ev_near, 0);
         for (size_t i = 0; i < b->boxes.size() && rc == ANKH_OK; ++i) {
             Handle &H = b->boxes[i]->h;
             const int64_t o = b->off[i];
             cudaStream_t st = b->streams[i % ns];
-            auto at = [o](const float *p, int k) { return p ? p + k * o : nullptr; };
-            auto atw = [o](float *p, int k) { return p ? p + k * o : nullptr; };
-            rc = run_sequence(H, x + 3 * o, q + o, at(mu, 3), at(theta, 6), true, atw(dEdx, 3), atw(dEdq, 1),
-                              atw(dEdmu, 3), atw(dEdtheta, 6), atw(torque, 3), st);
+            rc = run_part_adjoint(H, atw(dEdx, o, 3), atw(dEdq, o, 1), atw(dEdmu, o, 3), atw(dEdtheta, o, 6),
+                                  atw(torque, o, 3), st);
             if (rc == ANKH_OK) {
                 cudaMemcpyAsync(b->h_E + 2 * i, H.d_terms + 5, sizeof(double), cudaMemcpyDeviceToHost, st);
                 cudaMemcpyAsync(b->h_E + 2 * i + 1, H.d_terms + 8, sizeof(double), cudaMemcpyDeviceToHost, st);

@@ -244,6 +244,27 @@ int corr_tc_blocks(const Handle &H);
 cudaError_t launch_corr_tc(Handle &H, bool forces, cudaStream_t s);
 
 int near_blocks(const Handle &H);
+int near_mode(const Handle &H);   // B0 evaluation of the near field (series lengths or erfcf), from xi h
+
+// Screening coefficients of the near-field pair kernel (k_near.cu).
+struct BCoef {
+    float xi;
+    float kap;                  // xi^2 log2(e):  y = kap r^2,  exp(-xi^2 r^2) = 2^-y
+    float c1, c2, c3, c4, c5;   // (2 xi^2)^l / (xi sqrt(pi))
+    float a[8];                 // erf(xi r)/r = sum_k a_k y^k (Maclaurin series of erf)
+};
+
+// One launch of the near field over several boxes (k_near.cu).
+struct NearBox;
+struct NearBatch {
+    int nbox = 0, total_blocks = 0, mode = 0;
+    BCoef bc;
+    NearBox *d_boxes = nullptr;   // per box, in decreasing order of atom count
+    int *d_block0 = nullptr;      // [nbox + 1] first block of each box
+};
+bool near_batch_tables(Handle *const *hs, int nbox, NearBatch &nb, std::string &err);
+cudaError_t launch_near_batch(const NearBatch &nb, bool forces, cudaStream_t s);
+void near_batch_free(NearBatch &nb);
 int spectral_blocks(const Handle &H);
 int corr_blocks(const Handle &H);
 int self_blocks(const Handle &H);

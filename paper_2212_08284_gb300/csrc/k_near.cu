@@ -40,14 +40,11 @@
 // energy is infinite) sets bit 4 of the error flag.
 #include "ankh_internal.cuh"
 
+#include <algorithm>
+#include <vector>
+
 namespace ankh {
 
-struct BCoef {
-    float xi;
-    float kap;                  // xi^2 log2(e):  y = kap r^2,  exp(-xi^2 r^2) = 2^-y
-    float c1, c2, c3, c4, c5;   // (2 xi^2)^l / (xi sqrt(pi))
-    float a[8];                 // erf(xi r)/r = sum_k a_k y^k (Maclaurin series of erf)
-};
 
 // How B0 = erfc(xi r)/r is evaluated (chosen per launch from xi * r_max, r_max
 // the largest distance between atoms of adjacent leaves):
@@ -160,13 +157,36 @@ __device__ __forceinline__ void src_fields(float rx, float ry, float rz, const f
     }
 }
 
+// What the near field of one box needs (the single-box launch passes it by
+// value; the batched launch reads one per box from device memory).
+struct NearBox {
+    int n, nonperiodic;
+    float hf, hf_lo;                 // leaf edge as FP32 hi + lo
+    const int *start;
+    const int2 *items;
+    const int *nitems;
+    const float4 *A0, *A1, *A2, *A3;
+    float *gnear;
+    int64_t Nslot;
+    double *part;
+    int *flag;
+};
+
+// Block lb of nblocks working on box a (the item loop strides over the box's
+// blocks); the energy partial of the block goes to a.part[lb].
 template <bool FORCES, int MODE>
-__global__ void __launch_bounds__(kNearWarps * 32, 7)
-k_near(Geo g, const int *__restrict__ start, const int2 *__restrict__ items, const int *__restrict__ nitems,
-       const float4 *__restrict__ A0, const float4 *__restrict__ A1,
-       const float4 *__restrict__ A2, const float4 *__restrict__ A3, BCoef bc, float *__restrict__ gnear,
-       int64_t Nslot, double *__restrict__ part, int *__restrict__ flag)
+__device__ __forceinline__ void near_block(const NearBox &a, const BCoef &bc, int lb, int nblocks)
 {
+    const int *__restrict__ start = a.start;
+    const int2 *__restrict__ items = a.items;
+    const float4 *__restrict__ A0 = a.A0;
+    const float4 *__restrict__ A1 = a.A1;
+    const float4 *__restrict__ A2 = a.A2;
+    const float4 *__restrict__ A3 = a.A3;
+    float *__restrict__ gnear = a.gnear;
+    const int64_t Nslot = a.Nslot;
+    int *__restrict__ flag = a.flag;
+    const int nonperiodic = a.nonperiodic;
     constexpr int K = NAcc<FORCES>::K;
     __shared__ float4 sSrc[kNearWarps][kNearChunk][4];
     __shared__ int sBeg[kNearWarps][28], sPre[kNearWarps][28];
@@ -174,11 +194,11 @@ k_near(Geo g, const int *__restrict__ start, const int2 *__restrict__ items, con
     __shared__ int sZero[kNearWarps][32];
     __shared__ double sE[kNearWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n = g.n;
-    const float h = g.hf, hlo = g.hf_lo;
+    const int n = a.n;
+    const float h = a.hf, hlo = a.hf_lo;
     double ew = 0.0;
-    const int nit = *nitems;
-    for (int it = blockIdx.x * kNearWarps + warp; it < nit; it += gridDim.x * kNearWarps) {
+    const int nit = *a.nitems;
+    for (int it = lb * kNearWarps + warp; it < nit; it += nblocks * kNearWarps) {
         const int2 item = items[it];
         const int t = item.x, t0 = item.y;
         const int tb = start[t], nt_all = start[t + 1] - tb;
@@ -189,7 +209,7 @@ k_near(Geo g, const int *__restrict__ start, const int2 *__restrict__ items, con
             const int dx = lane / 9 - 1, dy = (lane / 3) % 3 - 1, dz = lane % 3 - 1;
             const int ax = cx + dx, ay = cy + dy, az = cz + dz;
             // non-periodic box: leaves beyond its faces do not exist
-            const bool inside = !g.nonperiodic || (ax >= 0 && ax < n && ay >= 0 && ay < n && az >= 0 && az < n);
+            const bool inside = !nonperiodic || (ax >= 0 && ax < n && ay >= 0 && ay < n && az >= 0 && az < n);
             if (inside) {
                 const int nc = (((ax + n) % n) * n + (ay + n) % n) * n + (az + n) % n;
                 beg = start[nc];
@@ -323,8 +343,38 @@ k_near(Geo g, const int *__restrict__ start, const int2 *__restrict__ items, con
     if (threadIdx.x == 0) {
         double u = 0.0;
         for (int w = 0; w < kNearWarps; ++w) u += sE[w];
-        part[blockIdx.x] = u;
+        a.part[lb] = u;
     }
+}
+
+template <bool FORCES, int MODE>
+__global__ void __launch_bounds__(kNearWarps * 32, 7) k_near(const __grid_constant__ NearBox a, BCoef bc)
+{
+    near_block<FORCES, MODE>(a, bc, blockIdx.x, gridDim.x);
+}
+
+// All the boxes of a batch in one launch: box b owns blocks
+// [block0[b], block0[b + 1]) (the boxes are laid out in order of decreasing
+// cost, so the largest start first); every box keeps its own items, energy
+// partials and gradients.  All boxes of one launch share xi (bc) and the
+// B0 evaluation.
+template <bool FORCES, int MODE>
+__global__ void __launch_bounds__(kNearWarps * 32, 7)
+k_near_batch(const NearBox *__restrict__ boxes, const int *__restrict__ block0, int nbox, BCoef bc)
+{
+    __shared__ int sbox;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = nbox;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (block0[mid] <= (int)blockIdx.x) lo = mid;
+            else hi = mid;
+        }
+        sbox = lo;
+    }
+    __syncthreads();
+    const int b = sbox;
+    near_block<FORCES, MODE>(boxes[b], bc, (int)blockIdx.x - block0[b], block0[b + 1] - block0[b]);
 }
 
 int near_blocks(const Handle &H)
@@ -334,10 +384,9 @@ int near_blocks(const Handle &H)
     return (H.max_items + per_block - 1) / per_block;
 }
 
-cudaError_t launch_near(Handle &H, bool forces, cudaStream_t s)
+static BCoef near_coef(double xi)
 {
     BCoef bc;
-    const double xi = H.g.xi;
     const double log2e = 1.4426950408889634;
     bc.xi = (float)xi;
     bc.kap = (float)(xi * xi * log2e);
@@ -360,26 +409,107 @@ cudaError_t launch_near(Handle &H, bool forces, cudaStream_t s)
         }
         bc.a[k] = (float)((k % 2 ? -1.0 : 1.0) * 2.0 * xi / sqrt(M_PI) / (fact * (2 * k + 1) * l2k));
     }
-    const double zmax = xi * 2.0 * sqrt(3.0) * H.g.h;   // xi times the farthest pair of adjacent leaves
-    const int mode = zmax <= 0.2 ? kSeriesShort : (zmax <= 0.5 ? kSeriesLong : kErfcLib);
-    double *part = H.d_part + H.part_off[kPartNear];
-    const int nb = near_blocks(H);
-    const int64_t S = H.N;
-    const dim3 grid(nb), block(kNearWarps * 32);
-#define ANKH_NEAR_LAUNCH(F, M) \
-    k_near<F, M><<<grid, block, 0, s>>>(H.g, H.d_start, H.d_items, H.d_nitems, H.d_A0, H.d_A1, H.d_A2, H.d_A3, bc, \
-                                        H.d_gnear, S, part, H.d_flag)
-    if (forces) {
-        if (mode == kSeriesShort) ANKH_NEAR_LAUNCH(true, kSeriesShort);
-        else if (mode == kSeriesLong) ANKH_NEAR_LAUNCH(true, kSeriesLong);
-        else ANKH_NEAR_LAUNCH(true, kErfcLib);
-    } else {
-        if (mode == kSeriesShort) ANKH_NEAR_LAUNCH(false, kSeriesShort);
-        else if (mode == kSeriesLong) ANKH_NEAR_LAUNCH(false, kSeriesLong);
-        else ANKH_NEAR_LAUNCH(false, kErfcLib);
-    }
-#undef ANKH_NEAR_LAUNCH
+    return bc;
+}
+
+int near_mode(const Handle &H)
+{
+    const double zmax = H.g.xi * 2.0 * sqrt(3.0) * H.g.h;   // xi times the farthest pair of adjacent leaves
+    return zmax <= 0.2 ? kSeriesShort : (zmax <= 0.5 ? kSeriesLong : kErfcLib);
+}
+
+static NearBox near_box(const Handle &H)
+{
+    NearBox a;
+    a.n = H.g.n;
+    a.nonperiodic = H.g.nonperiodic;
+    a.hf = H.g.hf;
+    a.hf_lo = H.g.hf_lo;
+    a.start = H.d_start;
+    a.items = H.d_items;
+    a.nitems = H.d_nitems;
+    a.A0 = H.d_A0;
+    a.A1 = H.d_A1;
+    a.A2 = H.d_A2;
+    a.A3 = H.d_A3;
+    a.gnear = H.d_gnear;
+    a.Nslot = H.N;
+    a.part = H.d_part + H.part_off[kPartNear];
+    a.flag = H.d_flag;
+    return a;
+}
+
+#define ANKH_NEAR_DISPATCH(forces, mode, LAUNCH)                         \
+    do {                                                                 \
+        if (forces) {                                                    \
+            if (mode == kSeriesShort) LAUNCH(true, kSeriesShort);        \
+            else if (mode == kSeriesLong) LAUNCH(true, kSeriesLong);     \
+            else LAUNCH(true, kErfcLib);                                 \
+        } else {                                                         \
+            if (mode == kSeriesShort) LAUNCH(false, kSeriesShort);       \
+            else if (mode == kSeriesLong) LAUNCH(false, kSeriesLong);    \
+            else LAUNCH(false, kErfcLib);                                \
+        }                                                                \
+    } while (0)
+
+cudaError_t launch_near(Handle &H, bool forces, cudaStream_t s)
+{
+    const BCoef bc = near_coef(H.g.xi);
+    const NearBox a = near_box(H);
+    const int mode = near_mode(H);
+    const dim3 grid(near_blocks(H)), block(kNearWarps * 32);
+#define ANKH_NEAR_ONE(F, M) k_near<F, M><<<grid, block, 0, s>>>(a, bc)
+    ANKH_NEAR_DISPATCH(forces, mode, ANKH_NEAR_ONE);
+#undef ANKH_NEAR_ONE
     return cudaGetLastError();
+}
+
+// The boxes of a batch that share xi and the B0 evaluation, in one launch.
+// d_boxes / d_block0 are device arrays made by near_batch_tables.
+cudaError_t launch_near_batch(const NearBatch &nb, bool forces, cudaStream_t s)
+{
+    if (nb.total_blocks == 0) return cudaSuccess;
+    const dim3 grid(nb.total_blocks), block(kNearWarps * 32);
+#define ANKH_NEAR_BATCH(F, M) k_near_batch<F, M><<<grid, block, 0, s>>>(nb.d_boxes, nb.d_block0, nb.nbox, nb.bc)
+    ANKH_NEAR_DISPATCH(forces, nb.mode, ANKH_NEAR_BATCH);
+#undef ANKH_NEAR_BATCH
+    return cudaGetLastError();
+}
+
+// Device tables of one batched launch over the handles hs[0..nbox) (all with
+// the same xi and B0 evaluation), in decreasing order of their atom counts.
+bool near_batch_tables(Handle *const *hs, int nbox, NearBatch &nb, std::string &err)
+{
+    std::vector<int> order(nbox);
+    for (int i = 0; i < nbox; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return hs[x]->N > hs[y]->N; });
+    std::vector<NearBox> boxes(nbox);
+    std::vector<int> block0(nbox + 1, 0);
+    for (int k = 0; k < nbox; ++k) {
+        boxes[k] = near_box(*hs[order[k]]);
+        block0[k + 1] = block0[k] + near_blocks(*hs[order[k]]);
+    }
+    nb.nbox = nbox;
+    nb.total_blocks = block0[nbox];
+    nb.mode = near_mode(*hs[0]);
+    nb.bc = near_coef(hs[0]->g.xi);
+    if (cudaMalloc(&nb.d_boxes, sizeof(NearBox) * nbox) != cudaSuccess ||
+        cudaMalloc(&nb.d_block0, sizeof(int) * (nbox + 1)) != cudaSuccess ||
+        cudaMemcpy(nb.d_boxes, boxes.data(), sizeof(NearBox) * nbox, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(nb.d_block0, block0.data(), sizeof(int) * (nbox + 1), cudaMemcpyHostToDevice) != cudaSuccess) {
+        err = "batched near-field tables";
+        near_batch_free(nb);
+        return false;
+    }
+    return true;
+}
+
+void near_batch_free(NearBatch &nb)
+{
+    if (nb.d_boxes) cudaFree(nb.d_boxes);
+    if (nb.d_block0) cudaFree(nb.d_block0);
+    nb.d_boxes = nullptr;
+    nb.d_block0 = nullptr;
 }
 
 }  // namespace ankh

@@ -18,15 +18,24 @@ def api(gpu):
     return A
 
 
-@pytest.mark.parametrize("Lu", [5, 0], ids=["Lu5", "defaults"])
-def test_batch_matches_single_boxes_and_reference(api, Lu):
+@pytest.mark.parametrize("Lu,n_cells", [(5, 0), (0, 0), (5, 6)], ids=["Lu5", "defaults", "n6_two_near_groups"])
+def test_batch_matches_single_boxes_and_reference(api, Lu, n_cells):
+    """The batch runs one near-field launch over all boxes that share xi and
+    the near-field kernel variant; with six leaves per axis the boxes of
+    31-48 A have leaf edges on both sides of the variant threshold (two
+    launches)."""
     import torch
     sizes = [1000, 2200, 1500, 3600, 1200, 2700, 1800, 3000]        # waters per box
     boxes = [synth.water_box(w, 9000 + i, multipoles=True, name=f"b{i}") for i, w in enumerate(sizes)]
     cat = lambda f: torch.from_numpy(np.ascontiguousarray(np.concatenate([f(b) for b in boxes]),
                                                           dtype=np.float32)).cuda()
     x, q, mu, th = cat(lambda b: b.x), cat(lambda b: b.q), cat(lambda b: b.mu), cat(lambda b: b.theta)
-    bt = api.AnkhBatch([b.box for b in boxes], [b.n for b in boxes], Lu=Lu)
+    bt = api.AnkhBatch([b.box for b in boxes], [b.n for b in boxes], Lu=Lu, n_cells=n_cells)
+    singles = sum(api.ankh_launch_count(api.ankh_batch_box(bt.h, i), True) for i in range(len(boxes)))
+    groups = api.ankh_batch_launch_count(bt.h) - (singles - len(boxes))
+    assert 1 <= groups <= 3
+    if n_cells == 6:
+        assert groups == 2
     E1, g1 = bt.energy_forces(x, q, mu, th, torques=True)
     # new output buffers (new capture), then the same buffers again (graph replay)
     g2 = {k: torch.empty_like(v) for k, v in g1.items()}
@@ -49,7 +58,7 @@ def test_batch_matches_single_boxes_and_reference(api, Lu):
         # parity with the FP64 reference at matched parameters: at L_u = 5 (the
         # default orders of these 3,000-10,800-atom boxes are outside the
         # calibrated range, where the FP32 correction can lose the 2e-6 bar)
-        if Lu == 5 and i in (0, 3):
+        if Lu == 5 and n_cells == 0 and i in (0, 3):
             o = ar.ankh_energy(b.x, b.q, b.mu, b.theta, ar.Params(b.box, info["n_cells"], info["Lu"], info["Lu"]),
                                grad=True)
             assert E1[i] == pytest.approx(o["E"], rel=2e-6)
