@@ -345,6 +345,13 @@ static void free_device(Handle *H)
     H->have_events = 0;
     if (H->d_tw) cudaFree(H->d_tw);
     H->d_tw = nullptr;
+    if (H->have_copy_stream) {
+        cudaEventDestroy(H->ev_call);
+        cudaEventDestroy(H->ev_x);
+        cudaEventDestroy(H->ev_inputs);
+        cudaStreamDestroy(H->copy_stream);
+    }
+    H->have_copy_stream = 0;
 }
 
 template <typename T>
@@ -863,14 +870,35 @@ int ankh_energy_forces_host(ankh_handle *h, const float *x, const float *q, cons
         ANKH_CU(cudaMalloc(&H.d_hostbuf, need), "cudaMalloc staging");
         H.hostbuf_bytes = need;
     }
+    if (!H.have_copy_stream) {
+        ANKH_CU(cudaStreamCreateWithFlags(&H.copy_stream, cudaStreamNonBlocking), "copy stream");
+        ANKH_CU(cudaEventCreateWithFlags(&H.ev_call, cudaEventDisableTiming), "copy event");
+        ANKH_CU(cudaEventCreateWithFlags(&H.ev_x, cudaEventDisableTiming), "copy event");
+        ANKH_CU(cudaEventCreateWithFlags(&H.ev_inputs, cudaEventDisableTiming), "copy event");
+        H.have_copy_stream = 1;
+    }
     float *dx = H.d_hostbuf, *dq = dx + 3 * N, *dmu = dq + N, *dth = dmu + 3 * N;
     float *ox = dth + 6 * N, *oq = ox + 3 * N, *omu = oq + N, *oth = omu + 3 * N, *otq = oth + 6 * N;
-    ANKH_CU(cudaMemcpyAsync(dx, x, 3 * N * sizeof(float), cudaMemcpyHostToDevice, s), "H2D x");
-    ANKH_CU(cudaMemcpyAsync(dq, q, N * sizeof(float), cudaMemcpyHostToDevice, s), "H2D q");
-    if (mu) ANKH_CU(cudaMemcpyAsync(dmu, mu, 3 * N * sizeof(float), cudaMemcpyHostToDevice, s), "H2D mu");
-    if (theta) ANKH_CU(cudaMemcpyAsync(dth, theta, 6 * N * sizeof(float), cudaMemcpyHostToDevice, s), "H2D theta");
+    // the copies start after the work already queued on s; x first (the leaf
+    // sort needs only x), then q, mu, theta while the sort runs
+    cudaStream_t c = H.copy_stream;
+    ANKH_CU(cudaEventRecord(H.ev_call, s), "record");
+    ANKH_CU(cudaStreamWaitEvent(c, H.ev_call, 0), "wait");
+    ANKH_CU(cudaMemcpyAsync(dx, x, 3 * N * sizeof(float), cudaMemcpyHostToDevice, c), "H2D x");
+    ANKH_CU(cudaEventRecord(H.ev_x, c), "record");
+    ANKH_CU(cudaMemcpyAsync(dq, q, N * sizeof(float), cudaMemcpyHostToDevice, c), "H2D q");
+    if (mu) ANKH_CU(cudaMemcpyAsync(dmu, mu, 3 * N * sizeof(float), cudaMemcpyHostToDevice, c), "H2D mu");
+    if (theta) ANKH_CU(cudaMemcpyAsync(dth, theta, 6 * N * sizeof(float), cudaMemcpyHostToDevice, c), "H2D theta");
+    ANKH_CU(cudaEventRecord(H.ev_inputs, c), "record");
+    ANKH_CU(cudaStreamWaitEvent(s, H.ev_x, 0), "wait");
+    H.gather_wait = H.ev_inputs;
     rc = run_sequence(H, dx, dq, mu ? dmu : nullptr, theta ? dth : nullptr, true, ox, oq, omu, oth, otq, s);
-    if (rc) return rc;
+    H.gather_wait = nullptr;
+    // s has waited for ev_inputs unless the sequence stopped before the gather
+    if (rc) {
+        cudaStreamWaitEvent(s, H.ev_inputs, 0);
+        return rc;
+    }
     if (dEdx) ANKH_CU(cudaMemcpyAsync(dEdx, ox, 3 * N * sizeof(float), cudaMemcpyDeviceToHost, s), "D2H dEdx");
     if (dEdq) ANKH_CU(cudaMemcpyAsync(dEdq, oq, N * sizeof(float), cudaMemcpyDeviceToHost, s), "D2H dEdq");
     if (dEdmu) ANKH_CU(cudaMemcpyAsync(dEdmu, omu, 3 * N * sizeof(float), cudaMemcpyDeviceToHost, s), "D2H dEdmu");

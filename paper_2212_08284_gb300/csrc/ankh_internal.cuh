@@ -177,6 +177,12 @@ struct Handle {
     double *h_terms;        // pinned host copy
     float *d_hostbuf;       // staging for the host-buffer entry point
     int64_t hostbuf_bytes;
+    // host-buffer entry point: inputs copied on copy_stream (x first) while
+    // the leaf sort runs; the gather waits for ev_inputs
+    cudaStream_t copy_stream;
+    cudaEvent_t ev_call, ev_x, ev_inputs;
+    int have_copy_stream;
+    cudaEvent_t gather_wait;  // set for one run_sequence call: event the gather waits for
     double last_terms[6];
     FftPlan fft;
     float2 *d_tw;           // [L] FFT twiddles e^{-2 pi i e / L} (FP32 from FP64)

@@ -494,8 +494,9 @@ cudaError_t launch_scatter_sort_gather(Handle &H, const float *x, const float *q
 {
     int N = (int)H.N;
     (void)x;
-    const cudaError_t e = launch_radix(N, H.d_cellid, H.rs, H.rsb, H.d_perm, H.d_inv, s);
+    cudaError_t e = launch_radix(N, H.d_cellid, H.rs, H.rsb, H.d_perm, H.d_inv, s);
     if (e != cudaSuccess) return e;
+    if (H.gather_wait && (e = cudaStreamWaitEvent(s, H.gather_wait, 0)) != cudaSuccess) return e;
     k_gather<<<(N + 255) / 256, 256, 0, s>>>(N, H.d_inv, H.d_cellid, H.d_loc, q, H.max_order >= 1 ? mu : nullptr,
                                               H.max_order >= 2 ? theta : nullptr, H.g, H.d_scell,
                                               H.d_A0, H.d_A1, H.d_A2, H.d_A3, H.d_part + H.part_off[kPartSelf],

@@ -329,15 +329,36 @@ def test_coincident_atoms_report_enumeric(api):
     assert m.energy(x, q, mu, th) == E0
 
 
-def test_host_entry_point_matches_device(api):
-    b = synth.small_box(600, 8, box=26.0)
-    m, E, g = run_gpu(api, b, n=6, Lu=5)
-    outs = {k: np.zeros(v.shape, np.float32) for k, v in g.items()}
-    Eh = api.ankh_energy_forces_host(m.h, b.x, b.q, b.mu, b.theta, outs["dEdx"], outs["dEdq"], outs["dEdmu"],
-                                     outs["dEdtheta"], outs["torque"])
-    assert Eh == E
-    for k in g:
-        assert np.array_equal(outs[k].astype(np.float64), g[k])
+@pytest.mark.parametrize("case", ["small_pageable", "w96000_pinned", "w96000_charges_pinned"])
+def test_host_entry_point_matches_device(api, case):
+    """The host-buffer call (inputs copied on the handle's copy stream while
+    the leaf sort runs, the gather waiting for them) gives the device call's
+    result bit for bit, twice in a row (the staging buffers reused), from
+    pageable and from pinned host memory."""
+    import torch
+    if case == "small_pageable":
+        b, n, mixed, mo = synth.small_box(600, 8, box=26.0), 6, False, 2
+    else:
+        b, n, mixed, mo = synth.config_box(3), 18, True, (0 if "charges" in case else 2)
+    m, E, g = run_gpu(api, b, n=n, Lu=5, mixed=mixed, max_order=mo)
+    if case == "small_pageable":
+        host = lambda a: np.ascontiguousarray(a, dtype=np.float32)
+        outs = {k: np.zeros(v.shape, np.float32) for k, v in g.items()}
+        view = lambda t: t
+    else:
+        host = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).pin_memory()
+        outs = {k: torch.zeros(v.shape, dtype=torch.float32).pin_memory() for k, v in g.items()}
+        view = lambda t: t.numpy()
+    mu, th = (host(b.mu), host(b.theta)) if mo == 2 else (None, None)
+    for _ in range(2):
+        for v in outs.values():
+            view(v)[...] = 0.0
+        Eh = api.ankh_energy_forces_host(m.h, host(b.x), host(b.q), mu, th, outs["dEdx"], outs["dEdq"],
+                                         outs["dEdmu"], outs["dEdtheta"], outs["torque"])
+        assert Eh == E
+        for k in g:
+            assert np.array_equal(view(outs[k]).astype(np.float64), g[k])
+    m.close()
 
 
 def test_autograd_backward_is_the_adjoint(api):
