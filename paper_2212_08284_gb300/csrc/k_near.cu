@@ -57,11 +57,15 @@ enum { kErfcLib = 0, kSeriesLong = 1, kSeriesShort = 2 };
 constexpr int kNearWarps = 4;
 constexpr int kNearChunk = 64;
 // Items per warp: the launch covers the largest possible item count with
-// max_items / (4 kNearWarps) blocks, which the hardware hands to the SMs as
+// max_items / (k kNearWarps) blocks, which the hardware hands to the SMs as
 // earlier blocks retire.  A persistent grid (a fixed share of leaves per
 // warp) left the SMs idle at the end, waiting for the warps that drew the
-// heaviest leaves.
-constexpr int kNearLeavesPerWarp = 4;
+// heaviest leaves.  k = 4 where that still gives at least kNearMinWaves
+// waves of resident blocks (fewer blocks, fewer energy partials), else 2 or
+// 1, so that a box of some ten thousand atoms still fills every SM.
+constexpr int kNearMaxItemsPerWarp = 4;
+constexpr int kNearBlocksPerSM = 7;   // resident blocks of 128 threads (<= 73 registers per thread)
+constexpr int kNearMinWaves = 8;
 
 template <bool FORCES>
 struct NAcc {
@@ -379,8 +383,10 @@ k_near_batch(const NearBox *__restrict__ boxes, const int *__restrict__ block0, 
 
 int near_blocks(const Handle &H)
 {
-    // 7 blocks of 128 threads are resident per SM (<= 73 registers per thread)
-    const int per_block = kNearWarps * kNearLeavesPerWarp;
+    const int64_t wave = (int64_t)kNearBlocksPerSM * H.sm_count;
+    int k = kNearMaxItemsPerWarp;
+    while (k > 1 && ((int64_t)H.max_items + kNearWarps * k - 1) / (kNearWarps * k) < kNearMinWaves * wave) k >>= 1;
+    const int per_block = kNearWarps * k;
     return (H.max_items + per_block - 1) / per_block;
 }
 
