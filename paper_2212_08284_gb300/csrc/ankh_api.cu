@@ -675,7 +675,7 @@ static int create_handle(double box_edge, int64_t N, const ankh_params *params, 
     nb[kPartNear] = near_blocks(H);
     nb[kPartGlob] = fmm ? 1 : spectral_blocks(H);
     nb[kPartCorr] = fmm ? fmm_part_slots(H)
-                        : std::max(corr_blocks(H), tc_max_blocks(n, g.ldm));   // SIMT or tensor-core CTAs
+                        : std::max(corr_blocks(H), tc_max_blocks(n, g.ldm, H.sm_count));   // SIMT or tensor-core CTAs
     nb[kPartSelf] = self_blocks(H);
     nb[kPartQ] = self_blocks(H);
     H.part_off[0] = 0;
@@ -729,7 +729,7 @@ static int create_handle(double box_edge, int64_t N, const ankh_params *params, 
         return bail(ANKH_ECUDA, "upload C");
     if ((p.flags & ANKH_MIXED) && g.ldm % 32 == 0 && g.ldm <= 512 && n <= 128) {
         int S, R;
-        tc_tile_shape(n, S, R);
+        tc_tile_shape(n, (g.ldm + 127) / 128, H.sm_count, S, R);
         H.tc.ldk = tc_ldk(g.ldm);
         const int ldk = H.tc.ldk;
         // z-rows with a one-leaf halo; a non-periodic box has one extra all-zero z-row block

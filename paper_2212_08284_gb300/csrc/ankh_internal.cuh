@@ -242,8 +242,8 @@ void fmm_free(Handle &H);
 int fmm_part_slots(const Handle &H);   // energy partial slots of the M2L launch
 void mark_stage(Handle &H, int stage_done, cudaStream_t s);   // optional per-stage timing
 int run_fmm(Handle &H, const float *x, const float *q, const float *mu, const float *theta, cudaStream_t s);
-void tc_tile_shape(int n, int &S, int &R);
-int tc_max_blocks(int n, int ldm);   // CTAs of the tensor-core correction (energy partial slots)
+void tc_tile_shape(int n, int halves, int sms, int &S, int &R);
+int tc_max_blocks(int n, int ldm, int sms);   // CTAs of the tensor-core correction (energy partial slots)
 int tc_ldk(int ldm);                 // node stride of the fp16 split operands
 int split_exponent(float maxabs);    // e with max |x| 2^e <= 2^14 (0 for 0 or non-finite)
 int corr_tc_blocks(const Handle &H);

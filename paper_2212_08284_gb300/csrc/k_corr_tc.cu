@@ -3,9 +3,10 @@
 // Same contraction as k_corr.cu (see there for the definition):
 //   Psi[ldm x N] = sum_{d=0..26} C_d[ldm x ldm] . B_d[ldm x N],
 //   B_d[:, j] = M_{t_j + d},
-// for tiles of N target leaves (R z-rows of the leaf grid, each padded to S
-// columns, N = R S <= 128) and 128-row slices of the target nodes (ldm = 128
-// for L_u = 5; 224 for L_u = 6, two slices; rows beyond ldm are zero).
+// for tiles of R z-rows of the leaf grid, each padded to S >= n leaves (S a
+// multiple of 8), the MMA width being N = R S rounded up to 16 (<= 128), and
+// 128-row slices of the target nodes (ldm = 128 for L_u = 5; 224 for L_u = 6,
+// two slices; rows beyond ldm are zero).
 //
 // Split precision "2xFP16": every FP32 operand x is scaled by a power of two
 // (2^eC for C, fixed per box; 2^eM for M, from max |M| of the call, so that
@@ -119,9 +120,12 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem =
         reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    const int N = R * S;                   // <= kMaxN
-    const uint32_t bbytes = (uint32_t)N * kRowBytes;
+    const int N = R * S;                   // leaf columns of a tile
+    const int Nm = (N + 15) & ~15;         // MMA width (<= kMaxN); rows N .. Nm-1 of B stay zero
+    const int Nb = (Nm + 31) & ~31;        // TMEM column stride of the accumulator buffers
+    const uint32_t bbytes = (uint32_t)Nm * kRowBytes;
     const uint32_t stage = 2 * kABytes + 2 * bbytes;
+    const uint32_t txbytes = 2 * kABytes + 2 * (uint32_t)N * kRowBytes;   // what the copies of a stage deliver
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStages * stage);
     uint64_t *empty = full + kStages;
     uint64_t *acc_full = empty + kStages;       // [kAccBufs] large buffer ready for draining
@@ -137,6 +141,17 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
     const int kch = ldk / kKc;            // K chunks per offset d
     const int kIters = noff * kch;        // stages per work item
     const int nmine = blockIdx.x < nwork ? (nwork - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    if (Nm > N) {
+        // B rows N .. Nm-1 of every stage: zero (no copy writes them), read by
+        // the MMAs through the async proxy
+        const int per = (Nm - N) * kRowBytes / 16;
+        for (int i = threadIdx.x; i < kStages * 2 * per; i += blockDim.x) {
+            const int st = i / (2 * per), hl = (i / per) % 2, o = i % per;
+            *reinterpret_cast<uint4 *>(smem + (size_t)st * stage + 2 * kABytes + (size_t)hl * bbytes +
+                                       (size_t)N * kRowBytes + (size_t)o * 16) = make_uint4(0u, 0u, 0u, 0u);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&full[s], 1);
@@ -212,7 +227,7 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
                         break;
                     }
                     unsigned char *st = smem + (size_t)s * stage;
-                    mbar_expect_tx(&full[s], stage);
+                    mbar_expect_tx(&full[s], txbytes);
                     tma_2d(st, &tmAhi, &full[s], jd * ldk + kc * kKc, row0);
                     tma_2d(st + kABytes, &tmAlo, &full[s], jd * ldk + kc * kKc, row0);
 #pragma unroll
@@ -231,7 +246,7 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
         // MMA issuer: large products of each stage into one of two TMEM buffers
         // (drained by the epilogue warps), small corrections into the item's
         // small accumulator
-        const uint32_t idesc = idesc_f16(kRows, N);
+        const uint32_t idesc = idesc_f16(kRows, Nm);
         int consumed = 0, gi = 0, s = 0;
         uint32_t ph = 0;
         bool stop = false;
@@ -259,8 +274,8 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
             }
             consumed = gi + 1;
             fence_after();
-            const uint32_t big = tmem + (uint32_t)(b * N);
-            const uint32_t small = tmem + (uint32_t)((kAccBufs + par) * N);
+            const uint32_t big = tmem + (uint32_t)(b * Nb);
+            const uint32_t small = tmem + (uint32_t)((kAccBufs + par) * Nb);
             const uint32_t base = su32(smem + (size_t)s * stage);
             const uint32_t ahi = base, alo = base + kABytes, bhi = base + 2 * kABytes, blo = bhi + bbytes;
             // descriptors built once per stage; a K step of 16 halves (32 bytes
@@ -289,7 +304,7 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
         // sixteen epilogue warps: warp w owns TMEM lanes 32 (w mod 4) and the 32
         // columns 32 (w div 4) .. (a group past N owns none but keeps the barriers)
         const int qd = warp & 3, grp = warp >> 2, col0 = grp * 32;
-        const bool have = col0 < N;
+        const bool have = col0 < Nm;
         float acc[32];
 #pragma unroll
         for (int q = 0; q < 32; ++q) acc[q] = 0.f;
@@ -314,11 +329,12 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
                 mv[q] = valid ? __ldg(&M[ofs[q]]) : 0.f;
             }
             uint32_t v[8];
-            tmem_ld8_nowait(lanebase + (uint32_t)((kAccBufs + (pend & 1)) * N + c0), v);
+            tmem_ld8_nowait(lanebase + (uint32_t)((kAccBufs + (pend & 1)) * Nb + c0), v);
             tmem_wait_ld();
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-                const float pv = __uint_as_float(v[q]);
+                // a padding column may hold anything: it takes no part
+                const float pv = ofs[q] >= 0 ? __uint_as_float(v[q]) : 0.f;
                 if (q & 1) pe1 = fmaf(mv[q], pv, pe1);
                 else pe0 = fmaf(mv[q], pv, pe0);
                 if (FORCES && ofs[q] >= 0) psi[ofs[q]] = pv;
@@ -332,7 +348,7 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
             if (lane == 0) mbar_arrive(&small_free[pend & 1]);
             pend = -1;
         };
-        const int ncols = have ? 32 : 0;   // N is a multiple of 32 (tc_tile_shape)
+        const int ncols = have ? min(32, Nm - col0) : 0;   // a multiple of 8
         int gi = 0;
         for (int j = 0; j < nmine && ok; ++j)
         for (int it = 0; it < kIters; ++it, ++gi) {
@@ -343,7 +359,7 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
             fence_after();
             if (have) {
                 uint32_t v[32];
-                tmem_ld32_nowait(lanebase + (uint32_t)(b * N), v);
+                tmem_ld32_nowait(lanebase + (uint32_t)(b * Nb), v);
                 tmem_wait_ld();
 #pragma unroll
                 for (int q = 0; q < 32; ++q) acc[q] += __uint_as_float(v[q]);
@@ -366,7 +382,7 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
                     if (pcol >= ncols) release_pending();
                 }
                 if (have) {
-                    const uint32_t ts = lanebase + (uint32_t)((kAccBufs + (j & 1)) * N);
+                    const uint32_t ts = lanebase + (uint32_t)((kAccBufs + (j & 1)) * Nb);
                     uint32_t v[32];
                     tmem_ld32_nowait(ts, v);
                     tmem_wait_ld();
@@ -480,19 +496,36 @@ static size_t tc_smem_bytes(int N)
     return (size_t)tcg::kStages * stage + 1024 + 256;
 }
 
-// Tile of R z-rows of S (>= n, multiple of 32) leaves, N = R S <= 128: N is
-// then a multiple of 32, the column group of one epilogue warp.
-void tc_tile_shape(int n, int &S, int &R)
+// Tile of R z-rows of S leaves (S >= n, a multiple of 8 so that every z-row
+// block of B starts on a 1 KB swizzle atom), R <= 8, MMA width
+// roundup16(R S) <= 128.
+// R minimises the estimated time: waves of work items over the SMs times the
+// cost of one item, whose stages move the A slice (as many bytes as 128 B
+// rows) and the B rows -- so 128 + width.  Ties go to the larger R.
+void tc_tile_shape(int n, int halves, int sms, int &S, int &R)
 {
-    S = ((n + 31) / 32) * 32;
-    R = std::max(1, tcg::kMaxN / S);
+    S = ((n + 7) / 8) * 8;
+    const int rmax = std::max(1, std::min(8, tcg::kMaxN / S));   // the producer tracks up to 8 z-rows
+    int64_t best = -1;
+    R = rmax;
+    for (int r = rmax; r >= 1; --r) {
+        const int64_t items = (int64_t)((n * n + r - 1) / r) * halves;
+        const int64_t waves = (items + sms - 1) / sms;
+        const int64_t width = ((int64_t)r * S + 15) / 16 * 16;
+        const int64_t cost = waves * (128 + width);
+        if (best < 0 || cost < best) {
+            best = cost;
+            R = r;
+        }
+    }
 }
 
-int tc_max_blocks(int n, int ldm)
+int tc_max_blocks(int n, int ldm, int sms)
 {
     int S, R;
-    tc_tile_shape(n, S, R);
-    return ((n * n + R - 1) / R) * ((ldm + tcg::kRows - 1) / tcg::kRows);
+    const int halves = (ldm + tcg::kRows - 1) / tcg::kRows;
+    tc_tile_shape(n, halves, sms, S, R);
+    return ((n * n + R - 1) / R) * halves;
 }
 
 bool tc_prepare(Handle &H, std::string &err)
@@ -501,13 +534,14 @@ bool tc_prepare(Handle &H, std::string &err)
     const Geo &g = H.g;
     if (g.ldm % 32 != 0 || g.ldm > 512 || g.n > 128) return true;   // plain FP32 kernel is used
     int S, R;
-    tc_tile_shape(g.n, S, R);
+    tc_tile_shape(g.n, (g.ldm + tcg::kRows - 1) / tcg::kRows, H.sm_count, S, R);
     H.tc.S = S;
     H.tc.R = R;
     H.tc.rowstride = S + 2;
-    H.tc.N = R * S;
+    H.tc.N = (R * S + 15) / 16 * 16;   // MMA width
+    const int nb = (H.tc.N + 31) / 32 * 32;
     H.tc.tmem_cols = 32;
-    while ((int)H.tc.tmem_cols < (tcg::kAccBufs + 2) * H.tc.N) H.tc.tmem_cols <<= 1;   // large buffers + 2 small
+    while ((int)H.tc.tmem_cols < (tcg::kAccBufs + 2) * nb) H.tc.tmem_cols <<= 1;   // large buffers + 2 small
     H.tc.tiles = (g.n * g.n + R - 1) / R;
     H.tc.halves = (g.ldm + tcg::kRows - 1) / tcg::kRows;
     if (H.tc.tiles * H.tc.halves > H.part_off[kPartCorr + 1] - H.part_off[kPartCorr]) {
