@@ -250,13 +250,24 @@ __global__ void __launch_bounds__(128) k_fine(Geo g, const float *__restrict__ M
 }
 
 // L2P fused with the node potentials and the gradient assembly, one thread
-// per sorted atom: the node potentials of its leaf,
+// per sorted atom.  The node potentials of a leaf,
 //   Pi_t[k] = phi[g(t,k)] / M - psi_t[k]
-// (the merged-grid potential at the node minus the adjacent-leaf correction,
-// both read through the cache and shared by the leaf's atoms), contracted
-// with its basis -- the adjoint of P2M -- for the far-field gradient, plus the
-// near-field gradient, the self-term gradient and the k = 0 potential;
-// torques; write to the caller's atom order.
+// (the merged-grid potential at the node minus the adjacent-leaf
+// correction), are formed once per leaf: each warp stages them for the
+// distinct leaves of its 32 atoms in shared memory (up to kL2PLeaves at a
+// time, lane (a, b) writing the L_u nodes along z of its (x, y) node row).
+// Each atom contracts them with its basis -- the adjoint of P2M --
+//   V[p][q][r] = sum_abc Pi[a,b,c] ux^(p)[a] uy^(q)[b] uz^(r)[c],  p + q + r <= 3,
+// z first, then y, then x; adds the near-field gradient, the self-term
+// gradient and the k = 0 potential; forms torques and writes in the
+// caller's atom order.
+template <int LU>
+struct L2PShape {
+    static constexpr int CP = (LU + 3) & ~3;            // nodes along z, padded to float4s
+    static constexpr int LEAF = LU * LU * CP;           // staged floats per leaf
+    static constexpr int LEAVES = LU <= 6 ? 8 : 4;      // leaves staged per warp at a time
+};
+
 template <int LU, bool FASTW>
 __global__ void __launch_bounds__(128, LU <= 5 ? 4 : 2)
 k_l2p(Geo g, const int *__restrict__ scell, const int *__restrict__ perm, const float4 *__restrict__ A0,
@@ -266,70 +277,106 @@ k_l2p(Geo g, const int *__restrict__ scell, const int *__restrict__ perm, const 
       const double *__restrict__ terms, float *__restrict__ dEdx, float *__restrict__ dEdq,
       float *__restrict__ dEdmu, float *__restrict__ dEdth, float *__restrict__ torque)
 {
-    constexpr int Lm = LU - 1;
+    constexpr int Lm = LU - 1, CP = L2PShape<LU>::CP, LEAF = L2PShape<LU>::LEAF, NL = L2PShape<LU>::LEAVES;
+    __shared__ __align__(16) float sPi[4][NL][LEAF];
+    __shared__ int sCell[4][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= Nslot) return;
-    const int cell = scell[s];
-    const float *__restrict__ psil = psi + (int64_t)cell * g.ldm;
-    // merged-grid offsets of the leaf's nodes along each axis (periodic wrap)
-    const int n = g.n, nf = g.nf;
-    const int cx = cell / (n * n), cy = (cell / n) - cx * n, cz = cell - (cell / n) * n;
-    int ox[LU], oy[LU], oz[LU];            // nf^3 <= 2^30: 32-bit offsets
-#pragma unroll
-    for (int a = 0; a < LU; ++a) {
-        int gx = cx * Lm + a, gy = cy * Lm + a, gz = cz * Lm + a;
-        gx -= gx >= nf ? nf : 0;
-        gy -= gy >= nf ? nf : 0;
-        gz -= gz >= nf ? nf : 0;
-        ox[a] = gx * nf * nf;
-        oy[a] = gy * nf;
-        oz[a] = gz;
-    }
-    const float dcpot = (float)terms[6];
-    const float xi = g.xi;
-    {
-        const float4 a0 = A0[s], a1 = A1[s], a2 = A2[s], a3 = A3[s];
-        float ux[4][LU], uy[4][LU], uz[4][LU];
+    const bool active = s < Nslot;
+    const int cell = active ? scell[s] : -1;
+    // the warp's distinct leaves in order (slots are sorted by leaf)
+    const int prev = __shfl_up_sync(0xffffffffu, cell, 1);
+    const bool leader = active && (lane == 0 || cell != prev);
+    const unsigned lead = __ballot_sync(0xffffffffu, leader);
+    const int nl = __popc(lead);
+    const int rank = __popc(lead & (0xffffffffu >> (31 - lane))) - 1;   // leaders at or below this lane, less one
+    if (leader) sCell[warp][rank] = cell;
+    const int n = g.n, nf = g.nf, ldm = g.ldm;
+    float ux[4][LU], uy[4][LU], uz[4][LU];
+    float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (active) {
+        a0 = A0[s];
         basis_any<LU, FASTW, 4>(a0.x * g.two_over_h, W, g.Lc, Wc, ux);
         basis_any<LU, FASTW, 4>(a0.y * g.two_over_h, W, g.Lc, Wc, uy);
         basis_any<LU, FASTW, 4>(a0.z * g.two_over_h, W, g.Lc, Wc, uz);
-        // V[px][py][pz] = sum_k Pi[k] ux^(px) uy^(py) uz^(pz), px + py + pz <= 3
-        float V[4][4][4];
+    }
+    float V[4][4][4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
+        for (int j = 0; j < 4; ++j)
 #pragma unroll
-                for (int k = 0; k < 4; ++k) V[i][j][k] = 0.f;
+            for (int k = 0; k < 4; ++k) V[i][j][k] = 0.f;
+    for (int j0 = 0; j0 < nl; j0 += NL) {
+        const int nlc = min(NL, nl - j0);
+        __syncwarp();
+        for (int ab = lane; ab < LU * LU; ab += 32) {
+            const int a = ab / LU, bb = ab - a * LU;
+            for (int k = 0; k < nlc; ++k) {
+                const int t = sCell[warp][j0 + k];
+                const int cx = t / (n * n), cy = (t / n) - cx * n, cz = t - (t / n) * n;
+                int gx = cx * Lm + a, gy = cy * Lm + bb;   // nf^3 <= 2^30: 32-bit offsets
+                gx -= gx >= nf ? nf : 0;
+                gy -= gy >= nf ? nf : 0;
+                const float *__restrict__ prow = phi + (gx * nf + gy) * nf;
+                const float *__restrict__ srow = psi + (int64_t)t * ldm + ab * LU;
+                float *dst = &sPi[warp][k][ab * CP];
 #pragma unroll
-        for (int c = 0; c < LU; ++c) {
-            float Y[4][4];
+                for (int c = 0; c < LU; ++c) {
+                    int gz = cz * Lm + c;
+                    gz -= gz >= nf ? nf : 0;
+                    dst[c] = fmaf(__ldg(&prow[gz]), invM, -__ldg(&srow[c]));
+                }
+            }
+        }
+        __syncwarp();
+        if (active && rank >= j0 && rank < j0 + nlc) {
+            const float *sp = &sPi[warp][rank - j0][0];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int a = 0; a < LU; ++a) {
+                float Wq[4][4];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) Y[i][j] = 0.f;
+                for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int bb = 0; bb < LU; ++bb) {
-                float X[4] = {0.f, 0.f, 0.f, 0.f};
+                    for (int j = 0; j < 4; ++j) Wq[i][j] = 0.f;
 #pragma unroll
-                for (int a = 0; a < LU; ++a) {
-                    const float pi = fmaf(__ldg(&phi[ox[a] + oy[bb] + oz[c]]), invM,
-                                          -__ldg(&psil[(a * LU + bb) * LU + c]));
+                for (int bb = 0; bb < LU; ++bb) {
+                    float pv[CP];
 #pragma unroll
-                    for (int p = 0; p < 4; ++p) X[p] = fmaf(pi, ux[p][a], X[p]);
+                    for (int c4 = 0; c4 < CP / 4; ++c4) {
+                        const float4 v = *reinterpret_cast<const float4 *>(sp + (a * LU + bb) * CP + 4 * c4);
+                        pv[4 * c4] = v.x;
+                        pv[4 * c4 + 1] = v.y;
+                        pv[4 * c4 + 2] = v.z;
+                        pv[4 * c4 + 3] = v.w;
+                    }
+                    float Z[4];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        float z = 0.f;
+#pragma unroll
+                        for (int c = 0; c < LU; ++c) z = fmaf(pv[c], uz[r][c], z);
+                        Z[r] = z;
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+#pragma unroll
+                        for (int r = 0; r < 4 - q; ++r) Wq[q][r] = fmaf(Z[r], uy[q][bb], Wq[q][r]);
                 }
 #pragma unroll
                 for (int p = 0; p < 4; ++p)
 #pragma unroll
-                    for (int q = 0; q < 4 - p; ++q) Y[p][q] = fmaf(X[p], uy[q][bb], Y[p][q]);
+                    for (int q = 0; q < 4 - p; ++q)
+#pragma unroll
+                        for (int r = 0; r < 4 - p - q; ++r) V[p][q][r] = fmaf(Wq[q][r], ux[p][a], V[p][q][r]);
             }
-#pragma unroll
-            for (int p = 0; p < 4; ++p)
-#pragma unroll
-                for (int q = 0; q < 4 - p; ++q)
-#pragma unroll
-                    for (int r = 0; r < 4 - p - q; ++r) V[p][q][r] = fmaf(Y[p][q], uz[r][c], V[p][q][r]);
         }
+    }
+    if (!active) return;
+    const float dcpot = (float)terms[6];
+    const float xi = g.xi;
+    {
+        const float4 a1 = A1[s], a2 = A2[s], a3 = A3[s];
         const float q = a0.w, mx = a1.x, my = a1.y, mz = a1.z;
         const float xx = a2.x, xy = a2.y, xz = a2.z, yy = a2.w, yz = a3.x, zz = a3.y;
         const float txy2 = 2.f * xy, txz2 = 2.f * xz, tyz2 = 2.f * yz;
