@@ -488,6 +488,253 @@ __global__ void __launch_bounds__(512) k_fft_x_spectral(FftPlan pl, float2 *__re
 }
 
 // ---------------------------------------------------------------------------
+// Compile-time plans for the grid lengths of the library's default
+// configurations (the same Stockham stages, every index and trip count a
+// constant).  The passes along y and x read their first stage's inputs from
+// global memory and write their last stage's outputs there; the stages run
+// in place in one shared tile (each thread reads all inputs of its
+// butterflies, a barrier, then writes all outputs); the twiddles of a stage
+// come from a per-stage table W^(r k L/(p R)), r = 1 .. R-1, k < p (1 for
+// k = 0, so no branch).  Along x the forward transform's last stage keeps
+// its outputs in registers for the spectral product, and the inverse runs
+// the radices in reverse order, so that its first stage takes exactly those
+// registers as inputs (forward stage 3, butterfly i, holds the points
+// i + r L/R3, the inputs of inverse stage 1's butterfly i).
+template <int L>
+struct FftSpec;
+template <>
+struct FftSpec<216> {
+    static constexpr int R1 = 6, R2 = 6, R3 = 6, NT = 288;
+};
+template <>
+struct FftSpec<80> {
+    static constexpr int R1 = 8, R2 = 5, R3 = 2, NT = 320;
+};
+template <>
+struct FftSpec<72> {
+    static constexpr int R1 = 8, R2 = 3, R3 = 3, NT = 192;
+};
+
+constexpr int kSpecTK = 16;   // lines per block (kz columns)
+
+template <int L, int R, int NT>
+struct SpecStage {
+    static constexpr int LR = L / R, NB = LR * kSpecTK, NBT = (NB + NT - 1) / NT;
+};
+
+// Twiddle table of a stage (radix R, p earlier points): t[k (R-1) + r-1] =
+// W^(r k L/(p R)) with W = e^{SIGN 2 pi i / L}, from the e^{-2 pi i e / L} table.
+template <int L, int R, int P, int SIGN, int NT>
+__device__ __forceinline__ void spec_twiddles(float2 *t, const float2 *__restrict__ tw)
+{
+    constexpr int TWS = L / (P * R);
+    for (int e = threadIdx.x; e < P * (R - 1); e += NT) {
+        const int k = e / (R - 1), r = e % (R - 1) + 1;
+        float2 w = tw[(r * k * TWS) % L];
+        if (SIGN > 0) w.y = -w.y;
+        t[e] = w;
+    }
+}
+
+// This thread's butterflies of a stage: m-th one is f = threadIdx.x + m NT,
+// line l = f mod TK, index i = f / TK; inputs at points i + r L/R.
+template <int L, int R, int NT, class Src>
+__device__ __forceinline__ void spec_gather(float2 (&u)[SpecStage<L, R, NT>::NBT][R], Src src)
+{
+    using S = SpecStage<L, R, NT>;
+#pragma unroll
+    for (int m = 0; m < S::NBT; ++m) {
+        const int f = threadIdx.x + m * NT;
+        if (S::NB % NT == 0 || f < S::NB) {
+            const int l = f % kSpecTK, i = f / kSpecTK;
+#pragma unroll
+            for (int r = 0; r < R; ++r) u[m][r] = src(i + r * S::LR, l);
+        }
+    }
+}
+
+template <int L, int R, int P, int SIGN, int NT>
+__device__ __forceinline__ void spec_butterflies(float2 (&u)[SpecStage<L, R, NT>::NBT][R], const float2 *t)
+{
+    using S = SpecStage<L, R, NT>;
+#pragma unroll
+    for (int m = 0; m < S::NBT; ++m) {
+        const int f = threadIdx.x + m * NT;
+        if (S::NB % NT == 0 || f < S::NB) {
+            if (P > 1) {
+                const int k = (f / kSpecTK) % P;
+#pragma unroll
+                for (int r = 1; r < R; ++r) u[m][r] = cmul(u[m][r], t[k * (R - 1) + r - 1]);
+            }
+            Dft<R, SIGN>::run(u[m]);
+        }
+    }
+}
+
+// outputs of butterfly i at points (i / p) p R + i mod p + r p
+template <int L, int R, int P, int NT, class Dst>
+__device__ __forceinline__ void spec_scatter(const float2 (&u)[SpecStage<L, R, NT>::NBT][R], Dst dst)
+{
+    using S = SpecStage<L, R, NT>;
+#pragma unroll
+    for (int m = 0; m < S::NBT; ++m) {
+        const int f = threadIdx.x + m * NT;
+        if (S::NB % NT == 0 || f < S::NB) {
+            const int l = f % kSpecTK, i = f / kSpecTK;
+            const int j = (i / P) * P * R + i % P;
+#pragma unroll
+            for (int r = 0; r < R; ++r) dst(j + r * P, l, u[m][r]);
+        }
+    }
+}
+
+// Pass Y / Y' for a compile-time length: the TK columns kz0 .. kz0 + TK - 1
+// of the plane x, all L values of y, in place in global memory.
+template <int L, int SIGN>
+__global__ void __launch_bounds__(FftSpec<L>::NT) k_fft_y_spec(int Lh, float2 *__restrict__ s,
+                                                             const float2 *__restrict__ tw)
+{
+    using F = FftSpec<L>;
+    constexpr int NT = F::NT, R1 = F::R1, R2 = F::R2, R3 = F::R3, TK = kSpecTK;
+    __shared__ float2 a[L * TK];
+    __shared__ float2 t2[R1 * (R2 - 1)], t3[R1 * R2 * (R3 - 1)];
+    spec_twiddles<L, R2, R1, SIGN, NT>(t2, tw);
+    spec_twiddles<L, R3, R1 * R2, SIGN, NT>(t3, tw);
+    const int kz0 = blockIdx.x * TK, x = blockIdx.y;
+    float2 *base = s + (int64_t)x * L * Lh + kz0;
+    const int nvalid = min(TK, Lh - kz0);
+    {
+        float2 u[SpecStage<L, R1, NT>::NBT][R1];
+        spec_gather<L, R1, NT>(u, [&](int pos, int l) {
+            return l < nvalid ? base[(int64_t)pos * Lh + l] : make_float2(0.f, 0.f);
+        });
+        spec_butterflies<L, R1, 1, SIGN, NT>(u, nullptr);
+        spec_scatter<L, R1, 1, NT>(u, [&](int pos, int l, float2 v) { a[pos * TK + l] = v; });
+    }
+    __syncthreads();
+    {
+        float2 u[SpecStage<L, R2, NT>::NBT][R2];
+        spec_gather<L, R2, NT>(u, [&](int pos, int l) { return a[pos * TK + l]; });
+        __syncthreads();
+        spec_butterflies<L, R2, R1, SIGN, NT>(u, t2);
+        spec_scatter<L, R2, R1, NT>(u, [&](int pos, int l, float2 v) { a[pos * TK + l] = v; });
+    }
+    __syncthreads();
+    {
+        float2 u[SpecStage<L, R3, NT>::NBT][R3];
+        spec_gather<L, R3, NT>(u, [&](int pos, int l) { return a[pos * TK + l]; });
+        spec_butterflies<L, R3, R1 * R2, SIGN, NT>(u, t3);
+        spec_scatter<L, R3, R1 * R2, NT>(u, [&](int pos, int l, float2 v) {
+            if (l < nvalid) base[(int64_t)pos * Lh + l] = v;
+        });
+    }
+}
+
+// Pass X for a compile-time length: forward FFT along x, the energy sum and
+// with forces D rho^ and the inverse along x (modes as k_fft_x_spectral).
+template <int L>
+__global__ void __launch_bounds__(FftSpec<L>::NT) k_fft_x_spec(int Lh, float2 *__restrict__ s,
+                                                             const float *__restrict__ D,
+                                                             const float2 *__restrict__ tw, int mode,
+                                                             double *__restrict__ part)
+{
+    using F = FftSpec<L>;
+    constexpr int NT = F::NT, R1 = F::R1, R2 = F::R2, R3 = F::R3, TK = kSpecTK;
+    __shared__ float2 a[L * TK];
+    __shared__ float2 f2[R1 * (R2 - 1)], f3[R1 * R2 * (R3 - 1)];   // forward stages 2, 3
+    __shared__ float2 i2[R3 * (R2 - 1)], i3[R3 * R2 * (R1 - 1)];   // inverse stages 2, 3 (radices R3, R2, R1)
+    __shared__ double sred[NT / 32];
+    spec_twiddles<L, R2, R1, -1, NT>(f2, tw);
+    spec_twiddles<L, R3, R1 * R2, -1, NT>(f3, tw);
+    spec_twiddles<L, R2, R3, 1, NT>(i2, tw);
+    spec_twiddles<L, R1, R3 * R2, 1, NT>(i3, tw);
+    const int kz0 = blockIdx.x * TK, y = blockIdx.y;
+    const int64_t pstride = (int64_t)L * Lh;          // between x planes
+    float2 *base = s + (int64_t)y * Lh + kz0;
+    const float *Db = D + (int64_t)y * Lh + kz0;
+    const int nvalid = min(TK, Lh - kz0);
+    {
+        float2 u[SpecStage<L, R1, NT>::NBT][R1];
+        spec_gather<L, R1, NT>(u, [&](int pos, int l) {
+            return l < nvalid ? base[pos * pstride + l] : make_float2(0.f, 0.f);
+        });
+        spec_butterflies<L, R1, 1, -1, NT>(u, nullptr);
+        spec_scatter<L, R1, 1, NT>(u, [&](int pos, int l, float2 v) { a[pos * TK + l] = v; });
+    }
+    __syncthreads();
+    {
+        float2 u[SpecStage<L, R2, NT>::NBT][R2];
+        spec_gather<L, R2, NT>(u, [&](int pos, int l) { return a[pos * TK + l]; });
+        __syncthreads();
+        spec_butterflies<L, R2, R1, -1, NT>(u, f2);
+        spec_scatter<L, R2, R1, NT>(u, [&](int pos, int l, float2 v) { a[pos * TK + l] = v; });
+    }
+    __syncthreads();
+    using S3 = SpecStage<L, R3, NT>;
+    float2 u[S3::NBT][R3];
+    spec_gather<L, R3, NT>(u, [&](int pos, int l) { return a[pos * TK + l]; });
+    spec_butterflies<L, R3, R1 * R2, -1, NT>(u, f3);
+    // forward stage 3, butterfly i (< L/R3 = R1 R2, so i / p = 0) holds the
+    // frequencies kx = i + r L/R3
+    if (mode == 2) {
+        spec_scatter<L, R3, R1 * R2, NT>(u, [&](int pos, int l, float2 v) {
+            if (l < nvalid) base[pos * pstride + l] = v;
+        });
+        return;
+    }
+    const bool forces = mode == 1;
+    const bool even = (L & 1) == 0;
+    double en = 0.0;
+#pragma unroll
+    for (int m = 0; m < S3::NBT; ++m) {
+        const int f = threadIdx.x + m * NT;
+        if (S3::NB % NT == 0 || f < S3::NB) {
+            const int l = f % TK, i = f / TK;
+            const int kz = kz0 + l;
+#pragma unroll
+            for (int r = 0; r < R3; ++r) {
+                const float2 c = u[m][r];
+                const float d = l < nvalid ? Db[(i + r * S3::LR) * pstride + l] : 0.f;
+                const float w = (kz == 0 || (even && kz == Lh - 1)) ? 1.f : 2.f;
+                en += (double)(w * d * (c.x * c.x + c.y * c.y));
+                u[m][r] = cscale(c, d);
+            }
+        }
+    }
+    // fixed-order block sum of the energy partials
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) en += __shfl_down_sync(0xffffffffu, en, off);
+    if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = en;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < NT / 32; ++w) t += sred[w];
+        part[blockIdx.y * gridDim.x + blockIdx.x] = t;
+    }
+    if (!forces) return;
+    // inverse stage 1 (radix R3, no twiddles) on the registers
+    spec_butterflies<L, R3, 1, 1, NT>(u, nullptr);
+    spec_scatter<L, R3, 1, NT>(u, [&](int pos, int l, float2 v) { a[pos * TK + l] = v; });
+    __syncthreads();
+    {
+        float2 v[SpecStage<L, R2, NT>::NBT][R2];
+        spec_gather<L, R2, NT>(v, [&](int pos, int l) { return a[pos * TK + l]; });
+        __syncthreads();
+        spec_butterflies<L, R2, R3, 1, NT>(v, i2);
+        spec_scatter<L, R2, R3, NT>(v, [&](int pos, int l, float2 w) { a[pos * TK + l] = w; });
+    }
+    __syncthreads();
+    {
+        float2 v[SpecStage<L, R1, NT>::NBT][R1];
+        spec_gather<L, R1, NT>(v, [&](int pos, int l) { return a[pos * TK + l]; });
+        spec_butterflies<L, R1, R3 * R2, 1, NT>(v, i3);
+        spec_scatter<L, R1, R3 * R2, NT>(v, [&](int pos, int l, float2 w) {
+            if (l < nvalid) base[pos * pstride + l] = w;
+        });
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Host side
 
 bool fft_prepare(Handle &H, std::string &err)
@@ -622,6 +869,13 @@ static void launch_z(const FftPlan &pl, bool inverse, float *rho, float2 *spec, 
 template <int SIGN>
 static void launch_y(const FftPlan &pl, float2 *spec, const float2 *tw, cudaStream_t s)
 {
+    const dim3 gs((pl.Lh + kSpecTK - 1) / kSpecTK, pl.L);
+    switch (pl.L) {
+    case 216: k_fft_y_spec<216, SIGN><<<gs, FftSpec<216>::NT, 0, s>>>(pl.Lh, spec, tw); return;
+    case 80: k_fft_y_spec<80, SIGN><<<gs, FftSpec<80>::NT, 0, s>>>(pl.Lh, spec, tw); return;
+    case 72: k_fft_y_spec<72, SIGN><<<gs, FftSpec<72>::NT, 0, s>>>(pl.Lh, spec, tw); return;
+    default: break;
+    }
     const dim3 g((pl.Lh + pl.tk - 1) / pl.tk, pl.L);
     if (pl.tk == 16) k_fft_y<SIGN, 16><<<g, pl.ty, smem_y(pl), s>>>(pl, spec, tw);
     else k_fft_y<SIGN, 8><<<g, pl.ty, smem_y(pl), s>>>(pl, spec, tw);
@@ -633,6 +887,12 @@ static void launch_x(const Handle &H, int mode, cudaStream_t s)
     const dim3 g((pl.Lh + pl.tk - 1) / pl.tk, pl.L);
     float2 *spec = reinterpret_cast<float2 *>(H.d_rhohat);
     double *part = H.d_part + H.part_off[kPartGlob];
+    switch (pl.L) {
+    case 216: k_fft_x_spec<216><<<g, FftSpec<216>::NT, 0, s>>>(pl.Lh, spec, H.d_D, H.d_tw, mode, part); return;
+    case 80: k_fft_x_spec<80><<<g, FftSpec<80>::NT, 0, s>>>(pl.Lh, spec, H.d_D, H.d_tw, mode, part); return;
+    case 72: k_fft_x_spec<72><<<g, FftSpec<72>::NT, 0, s>>>(pl.Lh, spec, H.d_D, H.d_tw, mode, part); return;
+    default: break;
+    }
     if (pl.tk == 16) k_fft_x_spectral<16><<<g, pl.ty, smem_x(pl), s>>>(pl, spec, H.d_D, H.d_tw, mode, part);
     else k_fft_x_spectral<8><<<g, pl.ty, smem_x(pl), s>>>(pl, spec, H.d_D, H.d_tw, mode, part);
 }
