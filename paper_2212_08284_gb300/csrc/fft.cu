@@ -517,10 +517,25 @@ struct FftSpec<72> {
 
 constexpr int kSpecTK = 16;   // lines per block (kz columns)
 
-template <int L, int R, int NT>
+template <int L, int R, int NT, int TK = kSpecTK>
 struct SpecStage {
-    static constexpr int LR = L / R, NB = LR * kSpecTK, NBT = (NB + NT - 1) / NT;
+    static constexpr int LR = L / R, NB = LR * TK, NBT = (NB + NT - 1) / NT;
 };
+
+// Butterfly f of a stage: line and index.  Line-fastest (the passes along y
+// and x, whose lines are adjacent in memory) or index-fastest (the passes
+// along z, whose points are).
+template <int LR, int TK, bool IFAST>
+__device__ __forceinline__ void spec_li(int f, int &l, int &i)
+{
+    if (IFAST) {
+        l = f / LR;
+        i = f - l * LR;
+    } else {
+        l = f % TK;
+        i = f / TK;
+    }
+}
 
 // Twiddle table of a stage (radix R, p earlier points): t[k (R-1) + r-1] =
 // W^(r k L/(p R)) with W = e^{SIGN 2 pi i / L}, from the e^{-2 pi i e / L} table.
@@ -537,32 +552,35 @@ __device__ __forceinline__ void spec_twiddles(float2 *t, const float2 *__restric
 }
 
 // This thread's butterflies of a stage: m-th one is f = threadIdx.x + m NT,
-// line l = f mod TK, index i = f / TK; inputs at points i + r L/R.
-template <int L, int R, int NT, class Src>
-__device__ __forceinline__ void spec_gather(float2 (&u)[SpecStage<L, R, NT>::NBT][R], Src src)
+// its line l and index i from spec_li; inputs at points i + r L/R.
+template <int L, int R, int NT, int TK = kSpecTK, bool IFAST = false, class Src>
+__device__ __forceinline__ void spec_gather(float2 (&u)[SpecStage<L, R, NT, TK>::NBT][R], Src src)
 {
-    using S = SpecStage<L, R, NT>;
+    using S = SpecStage<L, R, NT, TK>;
 #pragma unroll
     for (int m = 0; m < S::NBT; ++m) {
         const int f = threadIdx.x + m * NT;
         if (S::NB % NT == 0 || f < S::NB) {
-            const int l = f % kSpecTK, i = f / kSpecTK;
+            int l, i;
+            spec_li<S::LR, TK, IFAST>(f, l, i);
 #pragma unroll
             for (int r = 0; r < R; ++r) u[m][r] = src(i + r * S::LR, l);
         }
     }
 }
 
-template <int L, int R, int P, int SIGN, int NT>
-__device__ __forceinline__ void spec_butterflies(float2 (&u)[SpecStage<L, R, NT>::NBT][R], const float2 *t)
+template <int L, int R, int P, int SIGN, int NT, int TK = kSpecTK, bool IFAST = false>
+__device__ __forceinline__ void spec_butterflies(float2 (&u)[SpecStage<L, R, NT, TK>::NBT][R], const float2 *t)
 {
-    using S = SpecStage<L, R, NT>;
+    using S = SpecStage<L, R, NT, TK>;
 #pragma unroll
     for (int m = 0; m < S::NBT; ++m) {
         const int f = threadIdx.x + m * NT;
         if (S::NB % NT == 0 || f < S::NB) {
             if (P > 1) {
-                const int k = (f / kSpecTK) % P;
+                int l, i;
+                spec_li<S::LR, TK, IFAST>(f, l, i);
+                const int k = i % P;
 #pragma unroll
                 for (int r = 1; r < R; ++r) u[m][r] = cmul(u[m][r], t[k * (R - 1) + r - 1]);
             }
@@ -572,15 +590,16 @@ __device__ __forceinline__ void spec_butterflies(float2 (&u)[SpecStage<L, R, NT>
 }
 
 // outputs of butterfly i at points (i / p) p R + i mod p + r p
-template <int L, int R, int P, int NT, class Dst>
-__device__ __forceinline__ void spec_scatter(const float2 (&u)[SpecStage<L, R, NT>::NBT][R], Dst dst)
+template <int L, int R, int P, int NT, int TK = kSpecTK, bool IFAST = false, class Dst>
+__device__ __forceinline__ void spec_scatter(const float2 (&u)[SpecStage<L, R, NT, TK>::NBT][R], Dst dst)
 {
-    using S = SpecStage<L, R, NT>;
+    using S = SpecStage<L, R, NT, TK>;
 #pragma unroll
     for (int m = 0; m < S::NBT; ++m) {
         const int f = threadIdx.x + m * NT;
         if (S::NB % NT == 0 || f < S::NB) {
-            const int l = f % kSpecTK, i = f / kSpecTK;
+            int l, i;
+            spec_li<S::LR, TK, IFAST>(f, l, i);
             const int j = (i / P) * P * R + i % P;
 #pragma unroll
             for (int r = 0; r < R; ++r) dst(j + r * P, l, u[m][r]);
@@ -734,6 +753,119 @@ __global__ void __launch_bounds__(FftSpec<L>::NT) k_fft_x_spec(int Lh, float2 *_
     }
 }
 
+// Pass Z for a compile-time length: r2c along z.  Block: 2 TK consecutive
+// rows (x, y) of L reals as TK complex lines (row 2q the real, row 2q + 1 the
+// imaginary part of line q), lines held line-major in shared memory (points
+// contiguous, as in global memory: the butterflies run index-fastest).
+template <int L>
+__global__ void __launch_bounds__(FftSpec<L>::NT) k_fft_z_r2c_spec(int nrows, const float *__restrict__ in,
+                                                                 float2 *__restrict__ out,
+                                                                 const float2 *__restrict__ tw)
+{
+    using F = FftSpec<L>;
+    constexpr int NT = F::NT, R1 = F::R1, R2 = F::R2, R3 = F::R3, TK = kSpecTK, LP = L + 1, LH = L / 2 + 1;
+    __shared__ float2 a[TK * LP];
+    __shared__ float2 t2[R1 * (R2 - 1)], t3[R1 * R2 * (R3 - 1)];
+    spec_twiddles<L, R2, R1, -1, NT>(t2, tw);
+    spec_twiddles<L, R3, R1 * R2, -1, NT>(t3, tw);
+    const int row0 = blockIdx.x * 2 * TK;
+    {
+        float2 u[SpecStage<L, R1, NT>::NBT][R1];
+        spec_gather<L, R1, NT, TK, true>(u, [&](int pos, int q) {
+            const int r0 = row0 + 2 * q;
+            const float re = r0 < nrows ? in[(int64_t)r0 * L + pos] : 0.f;
+            const float im = r0 + 1 < nrows ? in[(int64_t)(r0 + 1) * L + pos] : 0.f;
+            return make_float2(re, im);
+        });
+        spec_butterflies<L, R1, 1, -1, NT, TK, true>(u, nullptr);
+        spec_scatter<L, R1, 1, NT, TK, true>(u, [&](int pos, int q, float2 v) { a[q * LP + pos] = v; });
+    }
+    __syncthreads();
+    {
+        float2 u[SpecStage<L, R2, NT>::NBT][R2];
+        spec_gather<L, R2, NT, TK, true>(u, [&](int pos, int q) { return a[q * LP + pos]; });
+        __syncthreads();
+        spec_butterflies<L, R2, R1, -1, NT, TK, true>(u, t2);
+        spec_scatter<L, R2, R1, NT, TK, true>(u, [&](int pos, int q, float2 v) { a[q * LP + pos] = v; });
+    }
+    __syncthreads();
+    {
+        float2 u[SpecStage<L, R3, NT>::NBT][R3];
+        spec_gather<L, R3, NT, TK, true>(u, [&](int pos, int q) { return a[q * LP + pos]; });
+        __syncthreads();
+        spec_butterflies<L, R3, R1 * R2, -1, NT, TK, true>(u, t3);
+        spec_scatter<L, R3, R1 * R2, NT, TK, true>(u, [&](int pos, int q, float2 v) { a[q * LP + pos] = v; });
+    }
+    __syncthreads();
+    // X = (Z_k + conj Z_{L-k}) / 2,  Y = (Z_k - conj Z_{L-k}) / 2i,  k = 0 .. L/2
+    for (int f = threadIdx.x; f < 2 * TK * LH; f += NT) {
+        const int rr = f / LH, k = f - rr * LH;
+        if (row0 + rr >= nrows) continue;
+        const int q = rr >> 1;
+        const float2 zk = a[q * LP + k], zm = a[q * LP + (k == 0 ? 0 : L - k)];
+        const float2 v = (rr & 1) ? make_float2(0.5f * (zk.y + zm.y), 0.5f * (zm.x - zk.x))
+                                  : make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+        out[(int64_t)row0 * LH + f] = v;                    // rows of L/2 + 1 values, contiguous
+    }
+}
+
+// Pass Z' for a compile-time length: c2r along z.  Line q is Z_k = X_k + i Y_k
+// of the Hermitian half rows 2q and 2q + 1 (X_{L-k} = conj X_k, the imaginary
+// parts of X_0 and X_{L/2} dropped as for a real row); one inverse FFT; the
+// real parts go to row 2q and the imaginary parts to row 2q + 1.
+template <int L>
+__global__ void __launch_bounds__(FftSpec<L>::NT) k_fft_z_c2r_spec(int nrows, const float2 *__restrict__ in,
+                                                                 float *__restrict__ out,
+                                                                 const float2 *__restrict__ tw)
+{
+    using F = FftSpec<L>;
+    constexpr int NT = F::NT, R1 = F::R1, R2 = F::R2, R3 = F::R3, TK = kSpecTK, LP = L + 1, LH = L / 2 + 1;
+    __shared__ float2 a[TK * LP];
+    __shared__ float2 t2[R1 * (R2 - 1)], t3[R1 * R2 * (R3 - 1)];
+    spec_twiddles<L, R2, R1, 1, NT>(t2, tw);
+    spec_twiddles<L, R3, R1 * R2, 1, NT>(t3, tw);
+    const int row0 = blockIdx.x * 2 * TK;
+    {
+        float2 u[SpecStage<L, R1, NT>::NBT][R1];
+        spec_gather<L, R1, NT, TK, true>(u, [&](int pos, int q) {
+            const int r0 = row0 + 2 * q;
+            const int kk = pos < LH ? pos : L - pos;
+            float2 x = r0 < nrows ? in[(int64_t)r0 * LH + kk] : make_float2(0.f, 0.f);
+            float2 y = r0 + 1 < nrows ? in[(int64_t)(r0 + 1) * LH + kk] : make_float2(0.f, 0.f);
+            if (kk == 0 || 2 * kk == L) {
+                x.y = 0.f;
+                y.y = 0.f;
+            }
+            if (pos >= LH) {
+                x.y = -x.y;
+                y.y = -y.y;
+            }
+            return make_float2(x.x - y.y, x.y + y.x);
+        });
+        spec_butterflies<L, R1, 1, 1, NT, TK, true>(u, nullptr);
+        spec_scatter<L, R1, 1, NT, TK, true>(u, [&](int pos, int q, float2 v) { a[q * LP + pos] = v; });
+    }
+    __syncthreads();
+    {
+        float2 u[SpecStage<L, R2, NT>::NBT][R2];
+        spec_gather<L, R2, NT, TK, true>(u, [&](int pos, int q) { return a[q * LP + pos]; });
+        __syncthreads();
+        spec_butterflies<L, R2, R1, 1, NT, TK, true>(u, t2);
+        spec_scatter<L, R2, R1, NT, TK, true>(u, [&](int pos, int q, float2 v) { a[q * LP + pos] = v; });
+    }
+    __syncthreads();
+    {
+        float2 u[SpecStage<L, R3, NT>::NBT][R3];
+        spec_gather<L, R3, NT, TK, true>(u, [&](int pos, int q) { return a[q * LP + pos]; });
+        spec_butterflies<L, R3, R1 * R2, 1, NT, TK, true>(u, t3);
+        spec_scatter<L, R3, R1 * R2, NT, TK, true>(u, [&](int pos, int q, float2 v) {
+            const int r0 = row0 + 2 * q;
+            if (r0 < nrows) out[(int64_t)r0 * L + pos] = v.x;
+            if (r0 + 1 < nrows) out[(int64_t)(r0 + 1) * L + pos] = v.y;
+        });
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Host side
 
@@ -853,9 +985,23 @@ static size_t smem_z(const FftPlan &pl) { return sizeof(float2) * (pl.L + 2 * pl
 static size_t smem_y(const FftPlan &pl) { return sizeof(float2) * (pl.L + 2 * pl.L * pl.tk); }
 static size_t smem_x(const FftPlan &pl) { return smem_y(pl) + sizeof(float) * pl.L * pl.tk; }
 
+template <int L>
+static void launch_z_spec(int nrows, bool inverse, float *rho, float2 *spec, const float2 *tw, cudaStream_t s)
+{
+    const unsigned nb = (unsigned)((nrows + 2 * kSpecTK - 1) / (2 * kSpecTK));
+    if (!inverse) k_fft_z_r2c_spec<L><<<nb, FftSpec<L>::NT, 0, s>>>(nrows, rho, spec, tw);
+    else k_fft_z_c2r_spec<L><<<nb, FftSpec<L>::NT, 0, s>>>(nrows, spec, rho, tw);
+}
+
 static void launch_z(const FftPlan &pl, bool inverse, float *rho, float2 *spec, const float2 *tw, cudaStream_t s)
 {
     const int nrows = pl.L * pl.L;
+    switch (pl.L) {
+    case 216: launch_z_spec<216>(nrows, inverse, rho, spec, tw, s); return;
+    case 80: launch_z_spec<80>(nrows, inverse, rho, spec, tw, s); return;
+    case 72: launch_z_spec<72>(nrows, inverse, rho, spec, tw, s); return;
+    default: break;
+    }
     const unsigned nb = (unsigned)((nrows + 2 * pl.zl - 1) / (2 * pl.zl));
     if (!inverse) {
         if (pl.zl == 8) k_fft_z_r2c<8><<<nb, pl.tz, smem_z(pl), s>>>(pl, nrows, rho, spec, tw);
