@@ -489,8 +489,8 @@ __global__ void __launch_bounds__(512) k_fft_x_spectral(FftPlan pl, float2 *__re
 
 // ---------------------------------------------------------------------------
 // Compile-time plans for the grid lengths of the library's default
-// configurations (the same Stockham stages, every index and trip count a
-// constant).  The passes along y and x read their first stage's inputs from
+// configurations and of boxes down to a few thousand atoms (the same
+// Stockham stages, three of them, every index and trip count a constant).  The passes along y and x read their first stage's inputs from
 // global memory and write their last stage's outputs there; the stages run
 // in place in one shared tile (each thread reads all inputs of its
 // butterflies, a barrier, then writes all outputs); the twiddles of a stage
@@ -514,6 +514,42 @@ template <>
 struct FftSpec<72> {
     static constexpr int R1 = 8, R2 = 3, R3 = 3, NT = 192;
 };
+// the grids of smaller boxes (n = 6 .. 18 leaves per axis, L_u = 5 or 6)
+template <>
+struct FftSpec<24> {
+    static constexpr int R1 = 4, R2 = 3, R3 = 2, NT = 96;
+};
+template <>
+struct FftSpec<40> {
+    static constexpr int R1 = 5, R2 = 4, R3 = 2, NT = 160;
+};
+template <>
+struct FftSpec<45> {
+    static constexpr int R1 = 5, R2 = 3, R3 = 3, NT = 128;
+};
+template <>
+struct FftSpec<50> {
+    static constexpr int R1 = 5, R2 = 5, R3 = 2, NT = 224;
+};
+template <>
+struct FftSpec<60> {
+    static constexpr int R1 = 5, R2 = 4, R3 = 3, NT = 160;
+};
+template <>
+struct FftSpec<70> {
+    static constexpr int R1 = 7, R2 = 5, R3 = 2, NT = 288;
+};
+template <>
+struct FftSpec<75> {
+    static constexpr int R1 = 5, R2 = 5, R3 = 3, NT = 224;
+};
+template <>
+struct FftSpec<90> {
+    static constexpr int R1 = 6, R2 = 5, R3 = 3, NT = 256;
+};
+
+// the lengths with a compile-time plan
+#define ANKH_FFT_SPEC_LENGTHS(X) X(24) X(40) X(45) X(50) X(60) X(70) X(72) X(75) X(80) X(90) X(216)
 
 constexpr int kSpecTK = 16;   // lines per block (kz columns)
 
@@ -997,9 +1033,9 @@ static void launch_z(const FftPlan &pl, bool inverse, float *rho, float2 *spec, 
 {
     const int nrows = pl.L * pl.L;
     switch (pl.L) {
-    case 216: launch_z_spec<216>(nrows, inverse, rho, spec, tw, s); return;
-    case 80: launch_z_spec<80>(nrows, inverse, rho, spec, tw, s); return;
-    case 72: launch_z_spec<72>(nrows, inverse, rho, spec, tw, s); return;
+#define ANKH_Z(LV) case LV: launch_z_spec<LV>(nrows, inverse, rho, spec, tw, s); return;
+    ANKH_FFT_SPEC_LENGTHS(ANKH_Z)
+#undef ANKH_Z
     default: break;
     }
     const unsigned nb = (unsigned)((nrows + 2 * pl.zl - 1) / (2 * pl.zl));
@@ -1017,9 +1053,9 @@ static void launch_y(const FftPlan &pl, float2 *spec, const float2 *tw, cudaStre
 {
     const dim3 gs((pl.Lh + kSpecTK - 1) / kSpecTK, pl.L);
     switch (pl.L) {
-    case 216: k_fft_y_spec<216, SIGN><<<gs, FftSpec<216>::NT, 0, s>>>(pl.Lh, spec, tw); return;
-    case 80: k_fft_y_spec<80, SIGN><<<gs, FftSpec<80>::NT, 0, s>>>(pl.Lh, spec, tw); return;
-    case 72: k_fft_y_spec<72, SIGN><<<gs, FftSpec<72>::NT, 0, s>>>(pl.Lh, spec, tw); return;
+#define ANKH_Y(LV) case LV: k_fft_y_spec<LV, SIGN><<<gs, FftSpec<LV>::NT, 0, s>>>(pl.Lh, spec, tw); return;
+    ANKH_FFT_SPEC_LENGTHS(ANKH_Y)
+#undef ANKH_Y
     default: break;
     }
     const dim3 g((pl.Lh + pl.tk - 1) / pl.tk, pl.L);
@@ -1034,9 +1070,10 @@ static void launch_x(const Handle &H, int mode, cudaStream_t s)
     float2 *spec = reinterpret_cast<float2 *>(H.d_rhohat);
     double *part = H.d_part + H.part_off[kPartGlob];
     switch (pl.L) {
-    case 216: k_fft_x_spec<216><<<g, FftSpec<216>::NT, 0, s>>>(pl.Lh, spec, H.d_D, H.d_tw, mode, part); return;
-    case 80: k_fft_x_spec<80><<<g, FftSpec<80>::NT, 0, s>>>(pl.Lh, spec, H.d_D, H.d_tw, mode, part); return;
-    case 72: k_fft_x_spec<72><<<g, FftSpec<72>::NT, 0, s>>>(pl.Lh, spec, H.d_D, H.d_tw, mode, part); return;
+#define ANKH_X(LV) \
+    case LV: k_fft_x_spec<LV><<<g, FftSpec<LV>::NT, 0, s>>>(pl.Lh, spec, H.d_D, H.d_tw, mode, part); return;
+    ANKH_FFT_SPEC_LENGTHS(ANKH_X)
+#undef ANKH_X
     default: break;
     }
     if (pl.tk == 16) k_fft_x_spectral<16><<<g, pl.ty, smem_x(pl), s>>>(pl, spec, H.d_D, H.d_tw, mode, part);
