@@ -504,7 +504,7 @@ template <int L>
 struct FftSpec;
 template <>
 struct FftSpec<216> {
-    static constexpr int R1 = 6, R2 = 6, R3 = 6, NT = 288;
+    static constexpr int R1 = 6, R2 = 6, R3 = 6, NT = 288, MINB = 4;   // four blocks per SM: <= 56 registers
 };
 template <>
 struct FftSpec<80> {
@@ -552,6 +552,16 @@ struct FftSpec<90> {
 #define ANKH_FFT_SPEC_LENGTHS(X) X(24) X(40) X(45) X(50) X(60) X(70) X(72) X(75) X(80) X(90) X(216)
 
 constexpr int kSpecTK = 16;   // lines per block (kz columns)
+
+// resident blocks per SM the launch bounds ask for (1 unless the plan says)
+template <class F, class = void>
+struct SpecMinBlocks {
+    static constexpr int v = 1;
+};
+template <class F>
+struct SpecMinBlocks<F, decltype((void)F::MINB)> {
+    static constexpr int v = F::MINB;
+};
 
 template <int L, int R, int NT, int TK = kSpecTK>
 struct SpecStage {
@@ -646,7 +656,7 @@ __device__ __forceinline__ void spec_scatter(const float2 (&u)[SpecStage<L, R, N
 // Pass Y / Y' for a compile-time length: the TK columns kz0 .. kz0 + TK - 1
 // of the plane x, all L values of y, in place in global memory.
 template <int L, int SIGN>
-__global__ void __launch_bounds__(FftSpec<L>::NT) k_fft_y_spec(int Lh, float2 *__restrict__ s,
+__global__ void __launch_bounds__(FftSpec<L>::NT, SpecMinBlocks<FftSpec<L>>::v) k_fft_y_spec(int Lh, float2 *__restrict__ s,
                                                              const float2 *__restrict__ tw)
 {
     using F = FftSpec<L>;
@@ -688,7 +698,7 @@ __global__ void __launch_bounds__(FftSpec<L>::NT) k_fft_y_spec(int Lh, float2 *_
 // Pass X for a compile-time length: forward FFT along x, the energy sum and
 // with forces D rho^ and the inverse along x (modes as k_fft_x_spectral).
 template <int L>
-__global__ void __launch_bounds__(FftSpec<L>::NT) k_fft_x_spec(int Lh, float2 *__restrict__ s,
+__global__ void __launch_bounds__(FftSpec<L>::NT, SpecMinBlocks<FftSpec<L>>::v) k_fft_x_spec(int Lh, float2 *__restrict__ s,
                                                              const float *__restrict__ D,
                                                              const float2 *__restrict__ tw, int mode,
                                                              double *__restrict__ part)
@@ -794,7 +804,7 @@ __global__ void __launch_bounds__(FftSpec<L>::NT) k_fft_x_spec(int Lh, float2 *_
 // imaginary part of line q), lines held line-major in shared memory (points
 // contiguous, as in global memory: the butterflies run index-fastest).
 template <int L>
-__global__ void __launch_bounds__(FftSpec<L>::NT) k_fft_z_r2c_spec(int nrows, const float *__restrict__ in,
+__global__ void __launch_bounds__(FftSpec<L>::NT, SpecMinBlocks<FftSpec<L>>::v) k_fft_z_r2c_spec(int nrows, const float *__restrict__ in,
                                                                  float2 *__restrict__ out,
                                                                  const float2 *__restrict__ tw)
 {
@@ -850,7 +860,7 @@ __global__ void __launch_bounds__(FftSpec<L>::NT) k_fft_z_r2c_spec(int nrows, co
 // parts of X_0 and X_{L/2} dropped as for a real row); one inverse FFT; the
 // real parts go to row 2q and the imaginary parts to row 2q + 1.
 template <int L>
-__global__ void __launch_bounds__(FftSpec<L>::NT) k_fft_z_c2r_spec(int nrows, const float2 *__restrict__ in,
+__global__ void __launch_bounds__(FftSpec<L>::NT, SpecMinBlocks<FftSpec<L>>::v) k_fft_z_c2r_spec(int nrows, const float2 *__restrict__ in,
                                                                  float *__restrict__ out,
                                                                  const float2 *__restrict__ tw)
 {
