@@ -718,6 +718,21 @@ __global__ void __launch_bounds__(FftSpec<L>::NT, SpecMinBlocks<FftSpec<L>>::v) 
     float2 *base = s + (int64_t)y * Lh + kz0;
     const float *Db = D + (int64_t)y * Lh + kz0;
     const int nvalid = min(TK, Lh - kz0);
+    using S3 = SpecStage<L, R3, NT>;
+    // D at the frequencies this thread's forward stage-3 butterflies end
+    // with, loaded first so that the loads overlap the forward stages
+    float dv[S3::NBT][R3];
+    if (mode != 2) {
+#pragma unroll
+        for (int m = 0; m < S3::NBT; ++m) {
+            const int f = threadIdx.x + m * NT;
+            const int l = f % TK, i = f / TK;
+#pragma unroll
+            for (int r = 0; r < R3; ++r)
+                dv[m][r] = ((S3::NB % NT == 0 || f < S3::NB) && l < nvalid) ? Db[(i + r * S3::LR) * pstride + l]
+                                                                             : 0.f;
+        }
+    }
     {
         float2 u[SpecStage<L, R1, NT>::NBT][R1];
         spec_gather<L, R1, NT>(u, [&](int pos, int l) {
@@ -735,7 +750,6 @@ __global__ void __launch_bounds__(FftSpec<L>::NT, SpecMinBlocks<FftSpec<L>>::v) 
         spec_scatter<L, R2, R1, NT>(u, [&](int pos, int l, float2 v) { a[pos * TK + l] = v; });
     }
     __syncthreads();
-    using S3 = SpecStage<L, R3, NT>;
     float2 u[S3::NBT][R3];
     spec_gather<L, R3, NT>(u, [&](int pos, int l) { return a[pos * TK + l]; });
     spec_butterflies<L, R3, R1 * R2, -1, NT>(u, f3);
@@ -759,7 +773,7 @@ __global__ void __launch_bounds__(FftSpec<L>::NT, SpecMinBlocks<FftSpec<L>>::v) 
 #pragma unroll
             for (int r = 0; r < R3; ++r) {
                 const float2 c = u[m][r];
-                const float d = l < nvalid ? Db[(i + r * S3::LR) * pstride + l] : 0.f;
+                const float d = dv[m][r];
                 const float w = (kz == 0 || (even && kz == Lh - 1)) ? 1.f : 2.f;
                 en += (double)(w * d * (c.x * c.x + c.y * c.y));
                 u[m][r] = cscale(c, d);
