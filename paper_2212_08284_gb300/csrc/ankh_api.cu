@@ -629,7 +629,9 @@ static int create_handle(double box_edge, int64_t N, const ankh_params *params, 
                                          (int64_t)1 << 30);
     ANKH_AL(H.d_items, H.max_items);
     ANKH_AL(H.d_nitems, 1);
-    H.rs = radix_plan(N, g.ncell);
+    H.rs = radix_plan(N, g.ncell, H.sm_count);
+    if (H.rs.npass == 1 && H.rs.bits[0] > 10 && radix_prepare() != cudaSuccess)
+        return bail(ANKH_ECUDA, "cudaFuncSetAttribute (radix scatter)");
     ANKH_AL(H.rsb.vtmp[0], N);
     if (H.rs.npass > 2) ANKH_AL(H.rsb.vtmp[1], N);
     ANKH_AL(H.rsb.hist, H.rs.hist_len);
@@ -953,15 +955,14 @@ int ankh_get_info(const ankh_handle *h, ankh_info *info)
 
 int ankh_ldm(const ankh_handle *h) { return h ? h->h.g.ldm : 0; }
 
-// Kernels of one ANKH-FFT evaluation as run_sequence issues them: bin, leaf
-// scan (2), radix sort (histogram, 2 scan kernels, scatter per digit pass),
-// gather, k = 0 term, P2M, merge, forward FFT along z and y, the pass along x
+// Kernels of one ANKH-FFT evaluation as run_sequence issues them: the leaf
+// sort (sort_launches: bin, leaf scan, radix passes, gather), k = 0 term, P2M, merge, forward FFT along z and y, the pass along x
 // with the spectral sum, [fp16 split,] correction, near field, and with
 // forces the inverse FFT along y and z and L2P; then the energy reduction.
 // The cudaMemsetAsync of the split exponent is not a kernel.
 static int launch_count(const Handle &H, bool forces, bool with_near)
 {
-    int k = 1 + 2 + 4 * H.rs.npass + 1 + 1 + 1 + 1 + 2 + 1;
+    int k = sort_launches(H) + 1 + 1 + 1 + 2 + 1;
     if (H.tc.enabled && (H.flags & ANKH_MIXED)) k += 1;
     k += 1;                    // correction
     if (with_near) k += 1;

@@ -52,7 +52,9 @@ struct RadixBufs {
     int *hist, *goff;       // [hist_len] digit counts per tile, [hist_len + 1] their exclusive scan
     int *bsum;              // block totals of the scans
 };
-RadixPlan radix_plan(int64_t N, int ncell);
+// wide_tiles: the most tiles for which one 12-bit pass replaces two (0: never)
+RadixPlan radix_plan(int64_t N, int ncell, int wide_tiles = 0);
+cudaError_t radix_prepare();   // shared-memory attribute of the wide scatter pass
 
 // Hand-written 3-D real FFT of the merged grid (fft.cu): one mixed-radix
 // Stockham plan for the L = nf points of every axis.
@@ -203,6 +205,7 @@ void set_error(const std::string &msg);
 // kernels launchers (each returns cudaGetLastError())
 cudaError_t launch_bin(Handle &H, const float *x, cudaStream_t s);
 cudaError_t launch_scan(Handle &H, cudaStream_t s);
+int sort_launches(const Handle &H);   // kernels of the leaf sort stage
 cudaError_t launch_scatter_sort_gather(Handle &H, const float *x, const float *q, const float *mu,
                                        const float *theta, cudaStream_t s);
 cudaError_t launch_radix(int N, const int *cellid, const RadixPlan &rp, const RadixBufs &b, int *perm, int *inv,

@@ -217,6 +217,28 @@ __global__ void __launch_bounds__(1024) k_scan_apply(int len, const int *__restr
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 1023) out[len] = base + tot;
 }
 
+// Single-block forms of the two scans for short inputs (one launch instead
+// of two): thread t sums the contiguous chunk [t C, (t + 1) C), C =
+// ceil(len / 1024), the chunk sums are scanned across the block, then each
+// thread writes its chunk's prefixes.  Same integer results.
+constexpr int kScanSmall = 1024 * 64;   // longest input scanned by one block
+
+__global__ void __launch_bounds__(1024) k_scan_small(int len, const int *__restrict__ v, int *__restrict__ out)
+{
+    __shared__ int wt[32];
+    const int C = (len + 1023) / 1024, b = threadIdx.x * C, e = min(len, b + C);
+    int loc = 0;
+    for (int i = b; i < e; ++i) loc += v[i];
+    int tot;
+    int run = block_excl_scan_1024(loc, wt, &tot);
+    for (int i = b; i < e; ++i) {
+        const int c = v[i];
+        out[i] = run;
+        run += c;
+    }
+    if (threadIdx.x == 1023) out[len] = tot;
+}
+
 // Scan of the leaf counts that also lays out the near-field work items: leaf
 // t with c_t atoms gives ceil(c_t / kNearItemTargets) items (t, first target),
 // in leaf order, so a leaf holding many atoms is spread over many warps.
@@ -234,6 +256,35 @@ __global__ void __launch_bounds__(1024) k_leafscan_totals(int ncell, const int *
     if (threadIdx.x == 0) {
         bsum[blockIdx.x] = tc;
         bsum[gridDim.x + blockIdx.x] = ti;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_leafscan_small(int ncell, const int *__restrict__ count,
+                                                         int *__restrict__ start, int2 *__restrict__ items,
+                                                         int *__restrict__ nitems)
+{
+    __shared__ int wt[32];
+    const int C = (ncell + 1023) / 1024, b = threadIdx.x * C, e = min(ncell, b + C);
+    int lc = 0, li = 0;
+    for (int i = b; i < e; ++i) {
+        const int c = count[i];
+        lc += c;
+        li += (c + kNearItemTargets - 1) / kNearItemTargets;
+    }
+    int tc, ti;
+    int rc = block_excl_scan_1024(lc, wt, &tc);
+    __syncthreads();
+    int ri = block_excl_scan_1024(li, wt, &ti);
+    for (int i = b; i < e; ++i) {
+        const int c = count[i], ch = (c + kNearItemTargets - 1) / kNearItemTargets;
+        start[i] = rc;
+        for (int j = 0; j < ch; ++j) items[ri + j] = make_int2(i, j * kNearItemTargets);
+        rc += c;
+        ri += ch;
+    }
+    if (threadIdx.x == 1023) {
+        start[ncell] = tc;
+        *nitems = ti;
     }
 }
 
@@ -285,6 +336,7 @@ constexpr int kRsWarps = kRsThreads / 32;
 constexpr int kRsRounds = 16;                          // 32-element rounds per warp
 constexpr int kRsTile = kRsWarps * 32 * kRsRounds;     // 4096 elements per tile
 constexpr int kRsMaxBits = 10;                         // <= 36 KB shared memory per scatter block
+constexpr int kRsWideBits = 12;                        // one wide pass: 144 KB per scatter block
 
 __global__ void __launch_bounds__(kRsThreads) k_rs_hist(int N, const int *__restrict__ cellid,
                                                         const int *__restrict__ vin, int shift, int bits,
@@ -360,12 +412,16 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(int N, const int *__r
     }
 }
 
-RadixPlan radix_plan(int64_t N, int ncell)
+RadixPlan radix_plan(int64_t N, int ncell, int wide_tiles)
 {
     RadixPlan rp;
     int B = 1;
     while (B < 31 && ((int64_t)1 << B) < ncell) ++B;   // ids 0 .. ncell - 1 fit in B bits
-    rp.npass = (B + kRsMaxBits - 1) / kRsMaxBits;
+    rp.ntiles = (int)((N + kRsTile - 1) / kRsTile);
+    // one pass of up to 12 bits where the tiles fit the wide_tiles blocks
+    // (one 144 KB block per SM) instead of two: four launches fewer
+    rp.npass = (B > kRsMaxBits && B <= kRsWideBits && rp.ntiles <= wide_tiles) ? 1
+                                                                                : (B + kRsMaxBits - 1) / kRsMaxBits;
     const int base = B / rp.npass, rem = B % rp.npass;
     int sh = 0;
     for (int p = 0; p < 3; ++p) {
@@ -373,12 +429,19 @@ RadixPlan radix_plan(int64_t N, int ncell)
         rp.shift[p] = sh;
         sh += rp.bits[p];
     }
-    rp.ntiles = (int)((N + kRsTile - 1) / kRsTile);
     int maxbits = 0;
     for (int p = 0; p < rp.npass; ++p) maxbits = rp.bits[p] > maxbits ? rp.bits[p] : maxbits;
     rp.hist_len = ((int64_t)1 << maxbits) * rp.ntiles;
     rp.bsum_len = (int)((rp.hist_len + 1023) / 1024) + 1;
     return rp;
+}
+
+// The scatter's dynamic shared memory for the wide pass (the attribute is the
+// kernel's, process-wide: set to the largest need).
+cudaError_t radix_prepare()
+{
+    return cudaFuncSetAttribute(k_rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (kRsWarps + 1) * (1 << kRsWideBits) * (int)sizeof(int));
 }
 
 cudaError_t launch_radix(int N, const int *cellid, const RadixPlan &rp, const RadixBufs &b, int *perm, int *inv,
@@ -393,8 +456,12 @@ cudaError_t launch_radix(int N, const int *cellid, const RadixPlan &rp, const Ra
         const int sb = (len + 1023) / 1024;
         k_rs_hist<<<rp.ntiles, kRsThreads, nb * sizeof(int), s>>>(N, cellid, vin, rp.shift[p], rp.bits[p],
                                                                   rp.ntiles, b.hist);
-        k_scan_totals<<<sb, 1024, 0, s>>>(len, b.hist, b.bsum);
-        k_scan_apply<<<sb, 1024, 0, s>>>(len, b.hist, b.bsum, b.goff);
+        if (len <= kScanSmall) {
+            k_scan_small<<<1, 1024, 0, s>>>(len, b.hist, b.goff);
+        } else {
+            k_scan_totals<<<sb, 1024, 0, s>>>(len, b.hist, b.bsum);
+            k_scan_apply<<<sb, 1024, 0, s>>>(len, b.hist, b.bsum, b.goff);
+        }
         k_rs_scatter<<<rp.ntiles, kRsThreads, (kRsWarps + 1) * nb * sizeof(int), s>>>(
             N, cellid, vin, rp.shift[p], rp.bits[p], rp.ntiles, b.goff, vout, last ? inv : nullptr);
         vin = vout;
@@ -481,8 +548,26 @@ cudaError_t launch_bin(Handle &H, const float *x, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// Kernels of the leaf sort as launch_bin, launch_scan and
+// launch_scatter_sort_gather issue them: binning, the leaf scan (one or two),
+// per digit pass a histogram, its scan (one or two) and the scatter, then
+// the gather.
+int sort_launches(const Handle &H)
+{
+    int k = 1 + (H.g.ncell <= kScanSmall ? 1 : 2);
+    for (int p = 0; p < H.rs.npass; ++p) {
+        const int64_t len = ((int64_t)1 << H.rs.bits[p]) * H.rs.ntiles;
+        k += 2 + (len <= kScanSmall ? 1 : 2);
+    }
+    return k + 1;
+}
+
 cudaError_t launch_scan(Handle &H, cudaStream_t s)
 {
+    if (H.g.ncell <= kScanSmall) {
+        k_leafscan_small<<<1, 1024, 0, s>>>(H.g.ncell, H.d_count, H.d_start, H.d_items, H.d_nitems);
+        return cudaGetLastError();
+    }
     const int nb = (H.g.ncell + 1023) / 1024;
     k_leafscan_totals<<<nb, 1024, 0, s>>>(H.g.ncell, H.d_count, H.d_bsum);
     k_leafscan_apply<<<nb, 1024, 0, s>>>(H.g.ncell, H.d_count, H.d_bsum, H.d_start, H.d_items, H.d_nitems);

@@ -92,3 +92,12 @@ def heavy_leaf_box(seed=5):
     b.mu[:] = 0
     b.theta[:] = 0
     return b, n
+
+
+def uniform_box(n_atoms, box=60.0, seed=0):
+    """n_atoms uniform in [-box/2, box/2)^3, normal charges."""
+    rng = np.random.default_rng(seed)
+    x = ((rng.random((n_atoms, 3)) - 0.5) * box).astype(np.float32)
+    q = rng.normal(size=n_atoms).astype(np.float32)
+    return synth.Box(x=x, q=q, mu=np.zeros((n_atoms, 3), np.float32), theta=np.zeros((n_atoms, 6), np.float32),
+                     box=box, name="uniform")

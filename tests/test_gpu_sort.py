@@ -14,7 +14,7 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 from oracle import ankh_ref as ar          # noqa: E402
-from cases import clustered_half_in_eight, clustered_one_leaf, heavy_leaf_box   # noqa: E402
+from cases import clustered_half_in_eight, clustered_one_leaf, heavy_leaf_box, uniform_box   # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -81,3 +81,26 @@ def test_heavy_leaf_energy_and_gradient_match_fp64_ankh(api):
         assert np.sqrt(np.mean(err ** 2)) <= 3e-5 * rms
         assert np.max(np.abs(err)) <= 20 * 3e-5 * rms
     m.close()
+
+
+@pytest.mark.parametrize("N,n", [(20000, 8), (20000, 12), (30000, 16), (30000, 18), (700000, 16)],
+                         ids=["9bit_one_pass", "11bit_wide", "12bit_wide", "13bit_two_passes",
+                              "12bit_171_tiles_two_passes"])
+def test_sort_plans_match_oracle(api, N, n):
+    """Every shape of the radix plan (one pass of up to 10 bits; one wide pass
+    of 11-12 bits where the 4,096-atom tiles fit one wave of the SMs; two
+    passes otherwise) orders uniform random atoms exactly as the oracle."""
+    b = uniform_box(N, seed=N + n)
+    check_against_oracle(b, n, *ordering(api, b, n))
+
+
+def test_wide_radix_pass_saves_three_launches(api):
+    """12-bit leaf ids on one wave of tiles take one radix pass (histogram,
+    scan, scatter), 13-bit ids two: the library's launch count differs by
+    exactly those three kernels."""
+    counts = []
+    for n in (16, 18):
+        m = api.Ankh(60.0, 30000, n_cells=n, Lu=5, max_order=0)
+        counts.append(api.ankh_launch_count(m.h, False))
+        m.close()
+    assert counts[1] - counts[0] == 3
