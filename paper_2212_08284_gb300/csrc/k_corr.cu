@@ -30,8 +30,11 @@ __device__ __forceinline__ int neighbour_leaf(int t, int d, int n, int nonperiod
 template <bool FORCES>
 __global__ void __launch_bounds__(256)
 k_corr_simt(Geo g, const float *__restrict__ M, const float *__restrict__ C, float *__restrict__ psi,
-            double *__restrict__ part, int d0)
+            double *__restrict__ part)
 {
+    // forces: all 27 offsets; energy alone: d = 0 and the 13 positive
+    // offsets, the latter twice (C_(-d) = C_d^T)
+    constexpr int d0 = FORCES ? 0 : 13;
     __shared__ __align__(16) float sA[kLC][kKT + 4];
     __shared__ __align__(16) float sB[kLC][kCT + 4];
     __shared__ double sh[32];
@@ -47,8 +50,6 @@ k_corr_simt(Geo g, const float *__restrict__ M, const float *__restrict__ C, flo
 #pragma unroll
         for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
 
-    // forces (d0 = 0): all 27 offsets; energy alone (d0 = 13): d = 0 and the
-    // 13 positive offsets, the latter twice (C_(-d) = C_d^T)
     for (int d = d0; d < 27; ++d) {
         const float *Cd = C + (int64_t)d * ldm * ldm;
         const float wd = (d0 == 0 || d == 13) ? 1.f : 2.f;
@@ -119,9 +120,9 @@ cudaError_t launch_corr(Handle &H, bool forces, cudaStream_t s)
     dim3 grid((H.g.ncell + kCT - 1) / kCT, (H.g.ldm + kKT - 1) / kKT);
     double *part = H.d_part + H.part_off[kPartCorr];
     if (forces)
-        k_corr_simt<true><<<grid, 256, 0, s>>>(H.g, H.d_M, H.d_C, H.d_psi, part, 0);
+        k_corr_simt<true><<<grid, 256, 0, s>>>(H.g, H.d_M, H.d_C, H.d_psi, part);
     else
-        k_corr_simt<false><<<grid, 256, 0, s>>>(H.g, H.d_M, H.d_C, H.d_psi, part, 13);
+        k_corr_simt<false><<<grid, 256, 0, s>>>(H.g, H.d_M, H.d_C, H.d_psi, part);
     return cudaGetLastError();
 }
 
