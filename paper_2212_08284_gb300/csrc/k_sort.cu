@@ -538,8 +538,8 @@ k_gather(int N, const int *__restrict__ inv, const int *__restrict__ cellid, con
 
 cudaError_t launch_bin(Handle &H, const float *x, cudaStream_t s)
 {
-    cudaMemsetAsync(H.d_count, 0, sizeof(int) * H.g.ncell, s);
-    cudaMemsetAsync(H.d_flag, 0, sizeof(int), s);
+    // the leaf counts and the error flag (allocated right after them)
+    cudaMemsetAsync(H.d_count, 0, sizeof(int) * (H.g.ncell + 1), s);
     int N = (int)H.N;
     if (H.g.nonperiodic)
         k_bin_np<<<(N + 255) / 256, 256, 0, s>>>(N, x, H.g, H.d_ctr, H.d_cellid, H.d_count, H.d_flag, H.d_loc);
