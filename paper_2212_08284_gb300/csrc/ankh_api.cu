@@ -345,6 +345,10 @@ static void free_device(Handle *H)
     H->have_events = 0;
     if (H->d_tw) cudaFree(H->d_tw);
     H->d_tw = nullptr;
+    for (int v = 0; v < 2; ++v)
+        if (H->gexec[v]) cudaGraphExecDestroy(H->gexec[v]);
+    if (H->gcap) cudaStreamDestroy(H->gcap);
+    H->gcap = nullptr;
     if (H->have_copy_stream) {
         cudaEventDestroy(H->ev_call);
         cudaEventDestroy(H->ev_x);
@@ -366,7 +370,8 @@ static cudaError_t dalloc(Handle *H, T **p, size_t count)
 void mark_stage(Handle &H, int stage_done, cudaStream_t s)
 {
     if (!H.timing || !H.have_events || H.nrec > kNumStages) return;
-    cudaEventRecord(H.ev[H.nrec], s);
+    // external: under stream capture an event record node of the graph
+    cudaEventRecordWithFlags(H.ev[H.nrec], s, cudaEventRecordExternal);
     H.ev_stage[H.nrec] = stage_done;
     H.nrec++;
 }
@@ -446,6 +451,50 @@ static int run_part_adjoint(Handle &H, float *dEdx, float *dEdq, float *dEdmu, f
     ANKH_CU(launch_fft_inverse(H, s), "inverse FFT");
     ANKH_CU(launch_l2p(H, dEdx, dEdq, dEdmu, dEdtheta, torque, s), "l2p");
     ANKH_CU(launch_reduce(H, s), "reduce");
+    return ANKH_OK;
+}
+
+// run_sequence through a CUDA graph: captured on the handle's own stream at
+// the first call (and again when a pointer, the stream's capture state or
+// the timing switch changes), then replayed on s with one launch.  The stage
+// events of ankh_set_timing are captured as event nodes.  A stream that is
+// itself capturing, and the ANKH-FMM path, run the kernels directly.
+static int run_graphed(Handle &H, const float *x, const float *q, const float *mu, const float *theta,
+                       bool forces, float *dEdx, float *dEdq, float *dEdmu, float *dEdtheta, float *torque,
+                       cudaStream_t s)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (H.fmm.enabled || cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+        return run_sequence(H, x, q, mu, theta, forces, dEdx, dEdq, dEdmu, dEdtheta, torque, s);
+    const int v = forces ? 1 : 0;
+    const void *key[10] = {x, q, mu, theta, dEdx, dEdq, dEdmu, dEdtheta, torque,
+                           reinterpret_cast<const void *>((intptr_t)(H.timing ? 1 : 0))};
+    bool same = H.gvalid[v] != 0;
+    for (int k = 0; k < 10 && same; ++k) same = key[k] == H.gkey[v][k];
+    if (!same) {
+        if (H.gexec[v]) cudaGraphExecDestroy(H.gexec[v]);
+        H.gexec[v] = nullptr;
+        H.gvalid[v] = 0;
+        if (!H.gcap) ANKH_CU(cudaStreamCreateWithFlags(&H.gcap, cudaStreamNonBlocking), "graph capture stream");
+        ANKH_CU(cudaStreamBeginCapture(H.gcap, cudaStreamCaptureModeThreadLocal), "begin capture");
+        const int rc = run_sequence(H, x, q, mu, theta, forces, dEdx, dEdq, dEdmu, dEdtheta, torque, H.gcap);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(H.gcap, &graph);
+        if (rc != ANKH_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (ce != cudaSuccess) return fail(ANKH_ECUDA, std::string("end capture: ") + cudaGetErrorString(ce));
+        const cudaError_t ie = cudaGraphInstantiate(&H.gexec[v], graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) {
+            H.gexec[v] = nullptr;
+            return fail(ANKH_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
+        }
+        for (int k = 0; k < 10; ++k) H.gkey[v][k] = key[k];
+        H.gvalid[v] = 1;
+    }
+    ANKH_CU(cudaGraphLaunch(H.gexec[v], s), "graph launch");
     return ANKH_OK;
 }
 
@@ -837,7 +886,7 @@ int ankh_energy(ankh_handle *h, const float *x, const float *q, const float *mu,
     if (rc) return rc;
     if (!E_host) return fail(ANKH_EINVAL, "E_host is NULL");
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    rc = run_sequence(h->h, x, q, mu, theta, false, nullptr, nullptr, nullptr, nullptr, nullptr, s);
+    rc = run_graphed(h->h, x, q, mu, theta, false, nullptr, nullptr, nullptr, nullptr, nullptr, s);
     if (rc) return rc;
     return fetch_terms(h->h, E_host, s);
 }
@@ -849,7 +898,7 @@ int ankh_energy_forces(ankh_handle *h, const float *x, const float *q, const flo
     int rc = check_inputs(h, x, q);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    rc = run_sequence(h->h, x, q, mu, theta, true, dEdx, dEdq, dEdmu, dEdtheta, torque, s);
+    rc = run_graphed(h->h, x, q, mu, theta, true, dEdx, dEdq, dEdmu, dEdtheta, torque, s);
     if (rc) return rc;
     if (E_host) return fetch_terms(h->h, E_host, s);
     return ANKH_OK;

@@ -185,6 +185,13 @@ struct Handle {
     cudaEvent_t ev_call, ev_x, ev_inputs;
     int have_copy_stream;
     cudaEvent_t gather_wait;  // set for one run_sequence call: event the gather waits for
+    // ankh_energy / ankh_energy_forces: the evaluation as a CUDA graph per
+    // variant (0 energy, 1 forces), captured on gcap and replayed while the
+    // call's pointers and the timing switch stay the same
+    cudaStream_t gcap;
+    cudaGraphExec_t gexec[2];
+    const void *gkey[2][10];
+    int gvalid[2];
     double last_terms[6];
     FftPlan fft;
     float2 *d_tw;           // [L] FFT twiddles e^{-2 pi i e / L} (FP32 from FP64)
