@@ -158,7 +158,13 @@ int ankh_create_cached(double box_edge, int64_t N, const ankh_params *params, co
  * x: N x 3 device; q: N device; mu: N x 3 device or NULL; theta: N x 6 device
  * or NULL.  *E_host receives the energy after the stream work completes (the
  * call synchronises the stream).  Errors: ANKH_EINVAL, ANKH_ECUDA,
- * ANKH_ENUMERIC. */
+ * ANKH_ENUMERIC.
+ * Execution (this call and ankh_energy_forces): the first call records the
+ * evaluation's kernels into a CUDA graph on the handle's own stream and
+ * launches it on cuda_stream; later calls with the same pointers (and the
+ * same ankh_set_timing state) launch that graph again, which reads whatever
+ * the buffers hold then; a different pointer records a new graph.  While
+ * cuda_stream is itself being captured the kernels are launched directly. */
 int ankh_energy(ankh_handle *h, const float *x, const float *q, const float *mu,
                 const float *theta, double *E_host, void *cuda_stream);
 
