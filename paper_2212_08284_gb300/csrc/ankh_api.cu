@@ -332,7 +332,7 @@ static void free_device(Handle *H)
 {
     if (!H) return;
     void *ptrs[] = {H->d_cellid, H->rsb.vtmp[0], H->rsb.vtmp[1], H->rsb.hist, H->rsb.goff, H->rsb.bsum,
-                    H->d_items, H->d_nitems, H->d_count, H->d_start, H->d_perm, H->d_inv, H->d_loc, H->d_ctr, H->d_scell, H->d_bsum,
+                    H->d_items, H->d_nitems, H->d_count, H->d_start, H->d_perm, H->d_loc, H->d_ctr, H->d_scell, H->d_bsum,
                     H->d_A0, H->d_A1, H->d_A2, H->d_A3, H->d_W, H->d_M, H->d_rho, H->d_rhohat, H->d_D,
                     H->d_phi, H->d_C, H->d_Chi, H->d_Clo, H->d_ChiE, H->d_CloE, H->d_psi, H->d_gnear, H->d_part,
                     H->d_partoff, H->d_rscr, H->d_ticket, H->d_terms, H->d_hostbuf, H->d_Mhi, H->d_Mlo, H->d_mmax, H->d_ind, H->d_ind_part};
@@ -689,7 +689,6 @@ static int create_handle(double box_edge, int64_t N, const ankh_params *params, 
     ANKH_AL(H.rsb.goff, H.rs.hist_len + 1);
     ANKH_AL(H.rsb.bsum, H.rs.bsum_len);
     ANKH_AL(H.d_perm, N);
-    ANKH_AL(H.d_inv, N);
     ANKH_AL(H.d_loc, N);
     ANKH_AL(H.d_ctr, 3 * n);
     {

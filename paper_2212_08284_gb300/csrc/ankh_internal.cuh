@@ -155,7 +155,6 @@ struct Handle {
     int max_items;          // ncell + ceil(N / kNearItemTargets): bound on the items of any input
     RadixPlan rs;           // leaf sort
     RadixBufs rsb;
-    int *d_inv;             // [N] sorted slot of each atom (inverse of perm)
     float4 *d_loc;          // [N] coordinates relative to the leaf centre (caller's order)
     float2 *d_ctr;          // [3n] leaf centres -r_B + (c + 1/2) h, c = -n .. 2n-1, as FP32 hi + lo
     float4 *d_A0, *d_A1, *d_A2, *d_A3;   // (lx, ly, lz, q) (mu, 0) (txx, txy, txz, tyy) (tyz, tzz, 0, 0)
