@@ -46,10 +46,10 @@ FP32_LANES_PER_SM = 128
 # Entries are removed whenever the kernel changes and re-measured.
 DRAM_TRAFFIC: dict = {
     # stage: kernels (read + write per launch); the timed evaluation, ncu, one pass per kernel
-    ("near", "water_1008000_qmuTheta", 54, 5): 95.76e6,      # k_near
-    ("corr", "water_1008000_qmuTheta", 54, 5): 336.91e6,     # k_split_f16 + k_corr_tc
-    ("p2m", "water_1008000_qmuTheta", 54, 5): 92.75e6,       # k_p2m
-    ("l2p", "water_1008000_qmuTheta", 54, 5): 369.01e6,      # k_l2p
+    ("near", "water_1008000_qmuTheta", 54, 5): 95.30e6,      # k_near
+    ("corr", "water_1008000_qmuTheta", 54, 5): 336.45e6,     # k_split_f16 + k_corr_tc
+    ("p2m", "water_1008000_qmuTheta", 54, 5): 93.69e6,       # k_p2m
+    ("l2p", "water_1008000_qmuTheta", 54, 5): 368.92e6,      # k_l2p
 }
 
 
