@@ -370,8 +370,11 @@ static cudaError_t dalloc(Handle *H, T **p, size_t count)
 void mark_stage(Handle &H, int stage_done, cudaStream_t s)
 {
     if (!H.timing || !H.have_events || H.nrec > kNumStages) return;
-    // external: under stream capture an event record node of the graph
-    cudaEventRecordWithFlags(H.ev[H.nrec], s, cudaEventRecordExternal);
+    // under stream capture an event record node of the graph (external), else a plain record
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cs);
+    if (cs == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(H.ev[H.nrec], s, cudaEventRecordExternal);
+    else cudaEventRecord(H.ev[H.nrec], s);
     H.ev_stage[H.nrec] = stage_done;
     H.nrec++;
 }

@@ -117,3 +117,22 @@ def test_call_inside_a_callers_capture(api):
     for k in out:
         assert torch.equal(out[k], ref[k])
     m.close()
+
+
+def test_stage_times_without_a_graph(api):
+    """The host-buffer call launches the kernels directly (no graph): the
+    stage events are plain records there, and the call still succeeds with
+    timing on."""
+    b = synth.small_box(600, 24, box=26.0)
+    m = api.Ankh(b.box, b.n, n_cells=6, Lu=5)
+    api.ankh_set_timing(m.h, True)
+    host = lambda a: np.ascontiguousarray(a, dtype=np.float32)
+    outs = {k: np.zeros(s, np.float32) for k, s in (("dEdx", (b.n, 3)), ("dEdq", (b.n,)), ("dEdmu", (b.n, 3)),
+                                                      ("dEdtheta", (b.n, 6)), ("torque", (b.n, 3)))}
+    for _ in range(2):
+        api.ankh_energy_forces_host(m.h, host(b.x), host(b.q), host(b.mu), host(b.theta), outs["dEdx"],
+                                    outs["dEdq"], outs["dEdmu"], outs["dEdtheta"], outs["torque"])
+        st = api.ankh_stage_times(m.h)
+        assert st["near"] > 0 and st["l2p"] > 0
+    api.ankh_set_timing(m.h, False)
+    m.close()
