@@ -166,6 +166,40 @@ struct Dft<7, SIGN> {
 };
 
 template <int SIGN>
+struct Dft<9, SIGN> {
+    static __device__ __forceinline__ void run(float2 *u)
+    {
+        // 9 = 3 x 3: X[k1 + 3 k2] = DFT_3 over b of w^(b k1) Y[b][k1],
+        // Y[b][.] = DFT_3 over a of u[3a + b], w = e^{SIGN 2 pi i / 9}
+        float2 y[3][3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            float2 e[3] = {u[b], u[b + 3], u[b + 6]};
+            Dft<3, SIGN>::run(e);
+            y[b][0] = e[0];
+            y[b][1] = e[1];
+            y[b][2] = e[2];
+        }
+        const float sg = (float)SIGN;
+        const float2 w1 = make_float2(0.76604444311897804f, sg * 0.64278760968653933f);    // 40 degrees
+        const float2 w2 = make_float2(0.17364817766693035f, sg * 0.98480775301220806f);    // 80
+        const float2 w4 = make_float2(-0.93969262078590838f, sg * 0.34202014332566873f);   // 160
+        y[1][1] = cmul(y[1][1], w1);
+        y[1][2] = cmul(y[1][2], w2);
+        y[2][1] = cmul(y[2][1], w2);
+        y[2][2] = cmul(y[2][2], w4);
+#pragma unroll
+        for (int k1 = 0; k1 < 3; ++k1) {
+            float2 f[3] = {y[0][k1], y[1][k1], y[2][k1]};
+            Dft<3, SIGN>::run(f);
+            u[k1] = f[0];
+            u[k1 + 3] = f[1];
+            u[k1 + 6] = f[2];
+        }
+    }
+};
+
+template <int SIGN>
 struct Dft<8, SIGN> {
     static __device__ __forceinline__ void run(float2 *u)
     {
@@ -547,11 +581,33 @@ template <>
 struct FftSpec<90> {
     static constexpr int R1 = 6, R2 = 5, R3 = 3, NT = 256;
 };
+// eight lines per block: also the test length of the radix-9 butterfly and
+// of the narrow tile of the 432-point plan
+template <>
+struct FftSpec<54> {
+    static constexpr int R1 = 9, R2 = 3, R3 = 2, NT = 128, TK = 8;
+};
+// the zero-padded grid of the non-periodic 1,008,000-atom box (n = 53):
+// eight lines per block (27 KB of shared memory)
+template <>
+struct FftSpec<432> {
+    static constexpr int R1 = 8, R2 = 6, R3 = 9, NT = 288, TK = 8;
+};
 
 // the lengths with a compile-time plan
-#define ANKH_FFT_SPEC_LENGTHS(X) X(24) X(40) X(45) X(50) X(60) X(70) X(72) X(75) X(80) X(90) X(216)
+#define ANKH_FFT_SPEC_LENGTHS(X) X(24) X(40) X(45) X(50) X(54) X(60) X(70) X(72) X(75) X(80) X(90) X(216) X(432)
 
-constexpr int kSpecTK = 16;   // lines per block (kz columns)
+constexpr int kSpecTK = 16;   // lines per block (kz columns, or complex z lines): default
+
+// lines per block of a plan (kSpecTK unless the plan says)
+template <class F, class = void>
+struct SpecLines {
+    static constexpr int v = kSpecTK;
+};
+template <class F>
+struct SpecLines<F, decltype((void)F::TK)> {
+    static constexpr int v = F::TK;
+};
 
 // resident blocks per SM the launch bounds ask for (1 unless the plan says)
 template <class F, class = void>
@@ -660,7 +716,7 @@ __global__ void __launch_bounds__(FftSpec<L>::NT, SpecMinBlocks<FftSpec<L>>::v) 
                                                              const float2 *__restrict__ tw)
 {
     using F = FftSpec<L>;
-    constexpr int NT = F::NT, R1 = F::R1, R2 = F::R2, R3 = F::R3, TK = kSpecTK;
+    constexpr int NT = F::NT, R1 = F::R1, R2 = F::R2, R3 = F::R3, TK = SpecLines<F>::v;
     __shared__ float2 a[L * TK];
     __shared__ float2 t2[R1 * (R2 - 1)], t3[R1 * R2 * (R3 - 1)];
     spec_twiddles<L, R2, R1, SIGN, NT>(t2, tw);
@@ -669,27 +725,27 @@ __global__ void __launch_bounds__(FftSpec<L>::NT, SpecMinBlocks<FftSpec<L>>::v) 
     float2 *base = s + (int64_t)x * L * Lh + kz0;
     const int nvalid = min(TK, Lh - kz0);
     {
-        float2 u[SpecStage<L, R1, NT>::NBT][R1];
-        spec_gather<L, R1, NT>(u, [&](int pos, int l) {
+        float2 u[SpecStage<L, R1, NT, TK>::NBT][R1];
+        spec_gather<L, R1, NT, TK>(u, [&](int pos, int l) {
             return l < nvalid ? base[(int64_t)pos * Lh + l] : make_float2(0.f, 0.f);
         });
-        spec_butterflies<L, R1, 1, SIGN, NT>(u, nullptr);
-        spec_scatter<L, R1, 1, NT>(u, [&](int pos, int l, float2 v) { a[pos * TK + l] = v; });
+        spec_butterflies<L, R1, 1, SIGN, NT, TK>(u, nullptr);
+        spec_scatter<L, R1, 1, NT, TK>(u, [&](int pos, int l, float2 v) { a[pos * TK + l] = v; });
     }
     __syncthreads();
     {
-        float2 u[SpecStage<L, R2, NT>::NBT][R2];
-        spec_gather<L, R2, NT>(u, [&](int pos, int l) { return a[pos * TK + l]; });
+        float2 u[SpecStage<L, R2, NT, TK>::NBT][R2];
+        spec_gather<L, R2, NT, TK>(u, [&](int pos, int l) { return a[pos * TK + l]; });
         __syncthreads();
-        spec_butterflies<L, R2, R1, SIGN, NT>(u, t2);
-        spec_scatter<L, R2, R1, NT>(u, [&](int pos, int l, float2 v) { a[pos * TK + l] = v; });
+        spec_butterflies<L, R2, R1, SIGN, NT, TK>(u, t2);
+        spec_scatter<L, R2, R1, NT, TK>(u, [&](int pos, int l, float2 v) { a[pos * TK + l] = v; });
     }
     __syncthreads();
     {
-        float2 u[SpecStage<L, R3, NT>::NBT][R3];
-        spec_gather<L, R3, NT>(u, [&](int pos, int l) { return a[pos * TK + l]; });
-        spec_butterflies<L, R3, R1 * R2, SIGN, NT>(u, t3);
-        spec_scatter<L, R3, R1 * R2, NT>(u, [&](int pos, int l, float2 v) {
+        float2 u[SpecStage<L, R3, NT, TK>::NBT][R3];
+        spec_gather<L, R3, NT, TK>(u, [&](int pos, int l) { return a[pos * TK + l]; });
+        spec_butterflies<L, R3, R1 * R2, SIGN, NT, TK>(u, t3);
+        spec_scatter<L, R3, R1 * R2, NT, TK>(u, [&](int pos, int l, float2 v) {
             if (l < nvalid) base[(int64_t)pos * Lh + l] = v;
         });
     }
@@ -704,7 +760,7 @@ __global__ void __launch_bounds__(FftSpec<L>::NT, SpecMinBlocks<FftSpec<L>>::v) 
                                                              double *__restrict__ part)
 {
     using F = FftSpec<L>;
-    constexpr int NT = F::NT, R1 = F::R1, R2 = F::R2, R3 = F::R3, TK = kSpecTK;
+    constexpr int NT = F::NT, R1 = F::R1, R2 = F::R2, R3 = F::R3, TK = SpecLines<F>::v;
     __shared__ float2 a[L * TK];
     __shared__ float2 f2[R1 * (R2 - 1)], f3[R1 * R2 * (R3 - 1)];   // forward stages 2, 3
     __shared__ float2 i2[R3 * (R2 - 1)], i3[R3 * R2 * (R1 - 1)];   // inverse stages 2, 3 (radices R3, R2, R1)
@@ -718,7 +774,7 @@ __global__ void __launch_bounds__(FftSpec<L>::NT, SpecMinBlocks<FftSpec<L>>::v) 
     float2 *base = s + (int64_t)y * Lh + kz0;
     const float *Db = D + (int64_t)y * Lh + kz0;
     const int nvalid = min(TK, Lh - kz0);
-    using S3 = SpecStage<L, R3, NT>;
+    using S3 = SpecStage<L, R3, NT, TK>;
     // D at the frequencies this thread's forward stage-3 butterflies end
     // with, loaded first so that the loads overlap the forward stages
     float dv[S3::NBT][R3];
@@ -734,29 +790,29 @@ __global__ void __launch_bounds__(FftSpec<L>::NT, SpecMinBlocks<FftSpec<L>>::v) 
         }
     }
     {
-        float2 u[SpecStage<L, R1, NT>::NBT][R1];
-        spec_gather<L, R1, NT>(u, [&](int pos, int l) {
+        float2 u[SpecStage<L, R1, NT, TK>::NBT][R1];
+        spec_gather<L, R1, NT, TK>(u, [&](int pos, int l) {
             return l < nvalid ? base[pos * pstride + l] : make_float2(0.f, 0.f);
         });
-        spec_butterflies<L, R1, 1, -1, NT>(u, nullptr);
-        spec_scatter<L, R1, 1, NT>(u, [&](int pos, int l, float2 v) { a[pos * TK + l] = v; });
+        spec_butterflies<L, R1, 1, -1, NT, TK>(u, nullptr);
+        spec_scatter<L, R1, 1, NT, TK>(u, [&](int pos, int l, float2 v) { a[pos * TK + l] = v; });
     }
     __syncthreads();
     {
-        float2 u[SpecStage<L, R2, NT>::NBT][R2];
-        spec_gather<L, R2, NT>(u, [&](int pos, int l) { return a[pos * TK + l]; });
+        float2 u[SpecStage<L, R2, NT, TK>::NBT][R2];
+        spec_gather<L, R2, NT, TK>(u, [&](int pos, int l) { return a[pos * TK + l]; });
         __syncthreads();
-        spec_butterflies<L, R2, R1, -1, NT>(u, f2);
-        spec_scatter<L, R2, R1, NT>(u, [&](int pos, int l, float2 v) { a[pos * TK + l] = v; });
+        spec_butterflies<L, R2, R1, -1, NT, TK>(u, f2);
+        spec_scatter<L, R2, R1, NT, TK>(u, [&](int pos, int l, float2 v) { a[pos * TK + l] = v; });
     }
     __syncthreads();
     float2 u[S3::NBT][R3];
-    spec_gather<L, R3, NT>(u, [&](int pos, int l) { return a[pos * TK + l]; });
-    spec_butterflies<L, R3, R1 * R2, -1, NT>(u, f3);
+    spec_gather<L, R3, NT, TK>(u, [&](int pos, int l) { return a[pos * TK + l]; });
+    spec_butterflies<L, R3, R1 * R2, -1, NT, TK>(u, f3);
     // forward stage 3, butterfly i (< L/R3 = R1 R2, so i / p = 0) holds the
     // frequencies kx = i + r L/R3
     if (mode == 2) {
-        spec_scatter<L, R3, R1 * R2, NT>(u, [&](int pos, int l, float2 v) {
+        spec_scatter<L, R3, R1 * R2, NT, TK>(u, [&](int pos, int l, float2 v) {
             if (l < nvalid) base[pos * pstride + l] = v;
         });
         return;
@@ -792,22 +848,22 @@ __global__ void __launch_bounds__(FftSpec<L>::NT, SpecMinBlocks<FftSpec<L>>::v) 
     }
     if (!forces) return;
     // inverse stage 1 (radix R3, no twiddles) on the registers
-    spec_butterflies<L, R3, 1, 1, NT>(u, nullptr);
-    spec_scatter<L, R3, 1, NT>(u, [&](int pos, int l, float2 v) { a[pos * TK + l] = v; });
+    spec_butterflies<L, R3, 1, 1, NT, TK>(u, nullptr);
+    spec_scatter<L, R3, 1, NT, TK>(u, [&](int pos, int l, float2 v) { a[pos * TK + l] = v; });
     __syncthreads();
     {
-        float2 v[SpecStage<L, R2, NT>::NBT][R2];
-        spec_gather<L, R2, NT>(v, [&](int pos, int l) { return a[pos * TK + l]; });
+        float2 v[SpecStage<L, R2, NT, TK>::NBT][R2];
+        spec_gather<L, R2, NT, TK>(v, [&](int pos, int l) { return a[pos * TK + l]; });
         __syncthreads();
-        spec_butterflies<L, R2, R3, 1, NT>(v, i2);
-        spec_scatter<L, R2, R3, NT>(v, [&](int pos, int l, float2 w) { a[pos * TK + l] = w; });
+        spec_butterflies<L, R2, R3, 1, NT, TK>(v, i2);
+        spec_scatter<L, R2, R3, NT, TK>(v, [&](int pos, int l, float2 w) { a[pos * TK + l] = w; });
     }
     __syncthreads();
     {
-        float2 v[SpecStage<L, R1, NT>::NBT][R1];
-        spec_gather<L, R1, NT>(v, [&](int pos, int l) { return a[pos * TK + l]; });
-        spec_butterflies<L, R1, R3 * R2, 1, NT>(v, i3);
-        spec_scatter<L, R1, R3 * R2, NT>(v, [&](int pos, int l, float2 w) {
+        float2 v[SpecStage<L, R1, NT, TK>::NBT][R1];
+        spec_gather<L, R1, NT, TK>(v, [&](int pos, int l) { return a[pos * TK + l]; });
+        spec_butterflies<L, R1, R3 * R2, 1, NT, TK>(v, i3);
+        spec_scatter<L, R1, R3 * R2, NT, TK>(v, [&](int pos, int l, float2 w) {
             if (l < nvalid) base[pos * pstride + l] = w;
         });
     }
@@ -823,14 +879,14 @@ __global__ void __launch_bounds__(FftSpec<L>::NT, SpecMinBlocks<FftSpec<L>>::v) 
                                                                  const float2 *__restrict__ tw)
 {
     using F = FftSpec<L>;
-    constexpr int NT = F::NT, R1 = F::R1, R2 = F::R2, R3 = F::R3, TK = kSpecTK, LP = L + 1, LH = L / 2 + 1;
+    constexpr int NT = F::NT, R1 = F::R1, R2 = F::R2, R3 = F::R3, TK = SpecLines<F>::v, LP = L + 1, LH = L / 2 + 1;
     __shared__ float2 a[TK * LP];
     __shared__ float2 t2[R1 * (R2 - 1)], t3[R1 * R2 * (R3 - 1)];
     spec_twiddles<L, R2, R1, -1, NT>(t2, tw);
     spec_twiddles<L, R3, R1 * R2, -1, NT>(t3, tw);
     const int row0 = blockIdx.x * 2 * TK;
     {
-        float2 u[SpecStage<L, R1, NT>::NBT][R1];
+        float2 u[SpecStage<L, R1, NT, TK>::NBT][R1];
         spec_gather<L, R1, NT, TK, true>(u, [&](int pos, int q) {
             const int r0 = row0 + 2 * q;
             const float re = r0 < nrows ? in[(int64_t)r0 * L + pos] : 0.f;
@@ -842,7 +898,7 @@ __global__ void __launch_bounds__(FftSpec<L>::NT, SpecMinBlocks<FftSpec<L>>::v) 
     }
     __syncthreads();
     {
-        float2 u[SpecStage<L, R2, NT>::NBT][R2];
+        float2 u[SpecStage<L, R2, NT, TK>::NBT][R2];
         spec_gather<L, R2, NT, TK, true>(u, [&](int pos, int q) { return a[q * LP + pos]; });
         __syncthreads();
         spec_butterflies<L, R2, R1, -1, NT, TK, true>(u, t2);
@@ -850,7 +906,7 @@ __global__ void __launch_bounds__(FftSpec<L>::NT, SpecMinBlocks<FftSpec<L>>::v) 
     }
     __syncthreads();
     {
-        float2 u[SpecStage<L, R3, NT>::NBT][R3];
+        float2 u[SpecStage<L, R3, NT, TK>::NBT][R3];
         spec_gather<L, R3, NT, TK, true>(u, [&](int pos, int q) { return a[q * LP + pos]; });
         __syncthreads();
         spec_butterflies<L, R3, R1 * R2, -1, NT, TK, true>(u, t3);
@@ -879,14 +935,14 @@ __global__ void __launch_bounds__(FftSpec<L>::NT, SpecMinBlocks<FftSpec<L>>::v) 
                                                                  const float2 *__restrict__ tw)
 {
     using F = FftSpec<L>;
-    constexpr int NT = F::NT, R1 = F::R1, R2 = F::R2, R3 = F::R3, TK = kSpecTK, LP = L + 1, LH = L / 2 + 1;
+    constexpr int NT = F::NT, R1 = F::R1, R2 = F::R2, R3 = F::R3, TK = SpecLines<F>::v, LP = L + 1, LH = L / 2 + 1;
     __shared__ float2 a[TK * LP];
     __shared__ float2 t2[R1 * (R2 - 1)], t3[R1 * R2 * (R3 - 1)];
     spec_twiddles<L, R2, R1, 1, NT>(t2, tw);
     spec_twiddles<L, R3, R1 * R2, 1, NT>(t3, tw);
     const int row0 = blockIdx.x * 2 * TK;
     {
-        float2 u[SpecStage<L, R1, NT>::NBT][R1];
+        float2 u[SpecStage<L, R1, NT, TK>::NBT][R1];
         spec_gather<L, R1, NT, TK, true>(u, [&](int pos, int q) {
             const int r0 = row0 + 2 * q;
             const int kk = pos < LH ? pos : L - pos;
@@ -907,7 +963,7 @@ __global__ void __launch_bounds__(FftSpec<L>::NT, SpecMinBlocks<FftSpec<L>>::v) 
     }
     __syncthreads();
     {
-        float2 u[SpecStage<L, R2, NT>::NBT][R2];
+        float2 u[SpecStage<L, R2, NT, TK>::NBT][R2];
         spec_gather<L, R2, NT, TK, true>(u, [&](int pos, int q) { return a[q * LP + pos]; });
         __syncthreads();
         spec_butterflies<L, R2, R1, 1, NT, TK, true>(u, t2);
@@ -915,7 +971,7 @@ __global__ void __launch_bounds__(FftSpec<L>::NT, SpecMinBlocks<FftSpec<L>>::v) 
     }
     __syncthreads();
     {
-        float2 u[SpecStage<L, R3, NT>::NBT][R3];
+        float2 u[SpecStage<L, R3, NT, TK>::NBT][R3];
         spec_gather<L, R3, NT, TK, true>(u, [&](int pos, int q) { return a[q * LP + pos]; });
         spec_butterflies<L, R3, R1 * R2, 1, NT, TK, true>(u, t3);
         spec_scatter<L, R3, R1 * R2, NT, TK, true>(u, [&](int pos, int q, float2 v) {
@@ -1035,9 +1091,20 @@ bool fft_prepare(Handle &H, std::string &err)
     return true;
 }
 
+// lines per block of the pass along x: the compile-time plan's, else the run-time plan's
+static int x_lines(int L)
+{
+    switch (L) {
+#define ANKH_T(LV) case LV: return SpecLines<FftSpec<LV>>::v;
+    ANKH_FFT_SPEC_LENGTHS(ANKH_T)
+#undef ANKH_T
+    default: return L <= 512 ? 16 : 8;
+    }
+}
+
 int spectral_blocks(const Handle &H)
 {
-    const int L = H.g.nf, tk = L <= 512 ? 16 : 8;
+    const int L = H.g.nf, tk = x_lines(L);
     return ((L / 2 + 1 + tk - 1) / tk) * L;
 }
 
@@ -1048,7 +1115,8 @@ static size_t smem_x(const FftPlan &pl) { return smem_y(pl) + sizeof(float) * pl
 template <int L>
 static void launch_z_spec(int nrows, bool inverse, float *rho, float2 *spec, const float2 *tw, cudaStream_t s)
 {
-    const unsigned nb = (unsigned)((nrows + 2 * kSpecTK - 1) / (2 * kSpecTK));
+    constexpr int tk = SpecLines<FftSpec<L>>::v;
+    const unsigned nb = (unsigned)((nrows + 2 * tk - 1) / (2 * tk));
     if (!inverse) k_fft_z_r2c_spec<L><<<nb, FftSpec<L>::NT, 0, s>>>(nrows, rho, spec, tw);
     else k_fft_z_c2r_spec<L><<<nb, FftSpec<L>::NT, 0, s>>>(nrows, spec, rho, tw);
 }
@@ -1075,9 +1143,13 @@ static void launch_z(const FftPlan &pl, bool inverse, float *rho, float2 *spec, 
 template <int SIGN>
 static void launch_y(const FftPlan &pl, float2 *spec, const float2 *tw, cudaStream_t s)
 {
-    const dim3 gs((pl.Lh + kSpecTK - 1) / kSpecTK, pl.L);
     switch (pl.L) {
-#define ANKH_Y(LV) case LV: k_fft_y_spec<LV, SIGN><<<gs, FftSpec<LV>::NT, 0, s>>>(pl.Lh, spec, tw); return;
+#define ANKH_Y(LV)                                                                                          \
+    case LV: {                                                                                              \
+        constexpr int tk = SpecLines<FftSpec<LV>>::v;                                                       \
+        k_fft_y_spec<LV, SIGN><<<dim3((pl.Lh + tk - 1) / tk, pl.L), FftSpec<LV>::NT, 0, s>>>(pl.Lh, spec, tw); \
+        return;                                                                                             \
+    }
     ANKH_FFT_SPEC_LENGTHS(ANKH_Y)
 #undef ANKH_Y
     default: break;
@@ -1094,8 +1166,13 @@ static void launch_x(const Handle &H, int mode, cudaStream_t s)
     float2 *spec = reinterpret_cast<float2 *>(H.d_rhohat);
     double *part = H.d_part + H.part_off[kPartGlob];
     switch (pl.L) {
-#define ANKH_X(LV) \
-    case LV: k_fft_x_spec<LV><<<g, FftSpec<LV>::NT, 0, s>>>(pl.Lh, spec, H.d_D, H.d_tw, mode, part); return;
+#define ANKH_X(LV)                                                                                          \
+    case LV: {                                                                                              \
+        constexpr int tk = SpecLines<FftSpec<LV>>::v;                                                       \
+        k_fft_x_spec<LV><<<dim3((pl.Lh + tk - 1) / tk, pl.L), FftSpec<LV>::NT, 0, s>>>(pl.Lh, spec, H.d_D,    \
+                                                                                   H.d_tw, mode, part);    \
+        return;                                                                                             \
+    }
     ANKH_FFT_SPEC_LENGTHS(ANKH_X)
 #undef ANKH_X
     default: break;

@@ -3,8 +3,8 @@ shared memory, the spectral product fused into the pass along x) against
 numpy's FP64 transforms, element by element, on even and odd grids whose
 lengths use every radix the plans pick (15 = 5.3, 48 = 8.6, 196 = 7.7.4,
 225 = 5.5.3.3 with the run-time plans; 216 = 6.6.6, 80 = 8.5.2,
-72 = 8.3.3, 24 = 4.3.2, 40 = 5.4.2, 45 = 5.3.3, 70 = 7.5.2 and 90 = 6.5.3
-with the compile-time plans).
+72 = 8.3.3, 24 = 4.3.2, 40 = 5.4.2, 45 = 5.3.3, 70 = 7.5.2, 90 = 6.5.3 and
+54 = 9.3.2 with the compile-time plans).
 
 Bars (FP32 transforms of M = L^3 points, ~log2 M stages of one rounding
 each): RMS error <= 2e-6 of the RMS value, every element within 2e-5 of the
@@ -26,9 +26,10 @@ def api(gpu):
     return A
 
 
-# (n, L_u): L = n (L_u - 1) = 15, 48, 196, 225 (run-time plans); 216, 80, 72, 24, 40, 45, 70, 90
-# (compile-time plans)
-SIZES = [(5, 4), (12, 5), (49, 5), (45, 6), (54, 5), (16, 6), (18, 5), (6, 5), (8, 6), (9, 6), (14, 6), (18, 6)]
+# (n, L_u): L = n (L_u - 1) = 15, 48, 196, 225 (run-time plans); 216, 80, 72, 24, 40, 45, 70, 90,
+# 54 (compile-time plans; 54 = 9.3.2 with eight lines per block, as the 432-point plan)
+SIZES = [(5, 4), (12, 5), (49, 5), (45, 6), (54, 5), (16, 6), (18, 5), (6, 5), (8, 6), (9, 6), (14, 6), (18, 6),
+         (18, 4)]
 
 
 def random_even_spectrum(rng, L):
