@@ -737,8 +737,8 @@ static int create_handle(double box_edge, int64_t N, const ankh_params *params, 
     ANKH_AL(H.d_part, H.part_off[kPartCount]);
     ANKH_AL(H.d_partoff, kPartCount + 1);
     ANKH_AL(H.d_rscr, kReduceBlocks * kPartCount);
-    ANKH_AL(H.d_ticket, 1);
-    cudaMemset(H.d_ticket, 0, sizeof(unsigned));
+    ANKH_AL(H.d_ticket, 2);   // the energy reduction's, the gather's
+    cudaMemset(H.d_ticket, 0, 2 * sizeof(unsigned));
     ANKH_AL(H.d_terms, 9);
     if (cudaMallocHost(&H.h_terms, 9 * sizeof(double)) != cudaSuccess)
         return bail(ANKH_ENOMEM, "cudaMallocHost");
@@ -1008,13 +1008,14 @@ int ankh_get_info(const ankh_handle *h, ankh_info *info)
 int ankh_ldm(const ankh_handle *h) { return h ? h->h.g.ldm : 0; }
 
 // Kernels of one ANKH-FFT evaluation as run_sequence issues them: the leaf
-// sort (sort_launches: bin, leaf scan, radix passes, gather), k = 0 term, P2M, merge, forward FFT along z and y, the pass along x
-// with the spectral sum, [fp16 split,] correction, near field, and with
+// sort (sort_launches: bin, leaf scan, radix passes, gather with the k = 0
+// term), P2M, merge, forward FFT along z and y, the pass along x with the
+// spectral sum, [fp16 split,] correction, near field, and with
 // forces the inverse FFT along y and z and L2P; then the energy reduction.
 // The cudaMemsetAsync of the split exponent is not a kernel.
 static int launch_count(const Handle &H, bool forces, bool with_near)
 {
-    int k = sort_launches(H) + 1 + 1 + 1 + 2 + 1;
+    int k = sort_launches(H) + 1 + 1 + 2 + 1;
     if (H.tc.enabled && (H.flags & ANKH_MIXED)) k += 1;
     k += 1;                    // correction
     if (with_near) k += 1;

@@ -32,24 +32,6 @@ __device__ __forceinline__ double strided_sum(const double *__restrict__ p, int 
     return v;
 }
 
-// total charge and the k = 0 potential D0 Q / M -> terms[6], terms[7] (Q)
-__global__ void __launch_bounds__(1024) k_dc(const double *__restrict__ part_q, int nq, double D0, double invM,
-                                             double *__restrict__ terms)
-{
-    __shared__ double sh[32];
-    double Q = strided_sum(part_q, 0, nq, (int)threadIdx.x, 1024);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) Q += __shfl_down_sync(0xffffffffu, Q, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = Q;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double u = 0.0;
-        for (int w = 0; w < 32; ++w) u += sh[w];
-        terms[7] = u;
-        terms[6] = D0 * u * invM;
-    }
-}
-
 static_assert(kReduceBlocks <= 32, "the last block adds the block sums within one warp");
 
 // Fixed-order FP64 reduction of all energy partials, over kReduceBlocks
@@ -65,7 +47,7 @@ k_reduce(const double *__restrict__ part, const int *__restrict__ off_dev, doubl
 {
     __shared__ double sh[8];
     __shared__ bool last;
-    for (int slot = 0; slot < kPartQ; ++slot) {   // near, far, correction, self (Q is k_dc's)
+    for (int slot = 0; slot < kPartQ; ++slot) {   // near, far, correction, self (Q: the gather's last block)
         const int b = off_dev[slot], len = off_dev[slot + 1] - b;
         const int per = (len + (int)gridDim.x - 1) / (int)gridDim.x;
         const int lo = b + min(len, (int)blockIdx.x * per), hi = b + min(len, ((int)blockIdx.x + 1) * per);
@@ -119,9 +101,9 @@ k_reduce(const double *__restrict__ part, const int *__restrict__ off_dev, doubl
 // the self term and Q partials are produced by the gather kernel (k_sort.cu)
 cudaError_t launch_self_dc(Handle &H, cudaStream_t s)
 {
-    k_dc<<<1, 1024, 0, s>>>(H.d_part + H.part_off[kPartQ], self_blocks(H), H.D0, 1.0 / (double)H.g.M,
-                            H.d_terms);
-    return cudaGetLastError();
+    (void)H;
+    (void)s;
+    return cudaSuccess;   // the gather's last block forms Q and the k = 0 potential
 }
 
 cudaError_t launch_reduce(Handle &H, cudaStream_t s)

@@ -491,9 +491,11 @@ __global__ void __launch_bounds__(256)
 k_gather_slot(int N, const int *__restrict__ perm, const int *__restrict__ cellid, const float4 *__restrict__ loc,
               const float *__restrict__ q, const float *__restrict__ mu, const float *__restrict__ th, Geo g,
               int *__restrict__ scell, float4 *__restrict__ A0, float4 *__restrict__ A1, float4 *__restrict__ A2,
-              float4 *__restrict__ A3, double *__restrict__ part_self, double *__restrict__ part_q)
+              float4 *__restrict__ A3, double *__restrict__ part_self, double *__restrict__ part_q, double D0,
+              double invM, double *__restrict__ terms, unsigned *__restrict__ ticket)
 {
     __shared__ double sh1[8], sh2[8];
+    __shared__ bool last;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     double es = 0.0, qs = 0.0;
     if (s < N) {
@@ -535,6 +537,28 @@ k_gather_slot(int N, const int *__restrict__ perm, const int *__restrict__ celli
         }
         part_self[blockIdx.x] = u;
         part_q[blockIdx.x] = v;
+    }
+    // the last block to finish (ticket) forms the total charge from the
+    // blocks' partials in a fixed order, and the k = 0 potential D0 Q / M
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double Q = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) Q += __ldcg(&part_q[b]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) Q += __shfl_down_sync(0xffffffffu, Q, o);
+    if ((threadIdx.x & 31) == 0) sh2[threadIdx.x >> 5] = Q;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double u = 0.0;
+        for (int w = 0; w < 8; ++w) u += sh2[w];
+        terms[7] = u;
+        terms[6] = D0 * u * invM;
+        *ticket = 0u;
     }
 }
 
@@ -587,7 +611,8 @@ cudaError_t launch_scatter_sort_gather(Handle &H, const float *x, const float *q
     k_gather_slot<<<(N + 255) / 256, 256, 0, s>>>(N, H.d_perm, H.d_cellid, H.d_loc, q, H.max_order >= 1 ? mu : nullptr,
                                               H.max_order >= 2 ? theta : nullptr, H.g, H.d_scell,
                                               H.d_A0, H.d_A1, H.d_A2, H.d_A3, H.d_part + H.part_off[kPartSelf],
-                                              H.d_part + H.part_off[kPartQ]);
+                                              H.d_part + H.part_off[kPartQ], H.D0, 1.0 / (double)H.g.M, H.d_terms,
+                                              H.d_ticket + 1);
     return cudaGetLastError();
 }
 
