@@ -122,14 +122,6 @@ class ClockSampler:
                             "step, then the timed steps)"}
 
 
-def radix_passes(ncell: int) -> int:
-    """Digit passes of the library's leaf sort (ids of B bits, <= 10 bits a pass)."""
-    B = 1
-    while B < 31 and (1 << B) < ncell:
-        B += 1
-    return (B + 9) // 10
-
-
 def preroll(clocks, step, seconds=0.4):
     """Start the clock sampler and run the untimed step for `seconds` so that
     the samples (and the clocks) are those of the loaded GPU; marks the start
@@ -657,9 +649,7 @@ def run_fmm(args, rank, world, dev, api, synth, dist, cfg):
             "precompute_s": t_pre, "accuracy": acc, "clocks": clk, "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": world * args.e2e_steps / t_e2e, "unit": "evals/s",
                     "h2d_bytes_per_step": 4 * N * (3 + 1 + 3 + 6), "d2h_bytes_per_step": 9 * 8},
-            # sort (bin, leaf scan, radix passes, gather), self, P2M, M2M per level,
-            # split, M2L, root, near, reduce
-            "gpu_launches": (4 + 4 * radix_passes(n ** 3) + 7 + depth) * args.steps}), flush=True)
+            "gpu_launches": api.ankh_launch_count(model.h, False) * args.steps}), flush=True)
     model.close()
 
 

@@ -221,8 +221,8 @@ int ankh_get_info(const ankh_handle *h, ankh_info *info);
 /* Kernels launched by one evaluation on h (forces != 0: ankh_energy_forces,
  * else ankh_energy) into *count: the count the library's launch sequence
  * issues, from its plan (digit passes of the leaf sort, the fp16 split of
- * the tensor-core correction).  Errors: ANKH_EINVAL (NULL, or an ANKH_FMM
- * handle). */
+ * the tensor-core correction, the levels of ANKH_FMM).  Errors: ANKH_EINVAL
+ * (NULL, or forces on an ANKH_FMM handle). */
 int ankh_launch_count(const ankh_handle *h, int forces, int *count);
 
 /* Copy an internal device buffer of the last call into caller memory dst

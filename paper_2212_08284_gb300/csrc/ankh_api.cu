@@ -1197,7 +1197,14 @@ void ankh_destroy_batch(ankh_batch *b) { batch_free(b); }
 int ankh_launch_count(const ankh_handle *h, int forces, int *count)
 {
     if (!h || !count) return fail(ANKH_EINVAL, "NULL argument");
-    if (h->h.fmm.enabled) return fail(ANKH_EINVAL, "ANKH_FMM handles are not counted");
+    if (h->h.fmm.enabled) {
+        // Alg. 3 as run_fmm issues it: the leaf sort, P2M, one M2M kernel per
+        // level below the leaves, the root term, the fp16 split, M2L, the near
+        // field and the reduction (energy only)
+        if (forces) return fail(ANKH_EINVAL, "ANKH_FMM computes the energy only (Alg. 3)");
+        *count = sort_launches(h->h) + 1 + h->h.fmm.E + 1 + 1 + 1 + 1 + 1;
+        return ANKH_OK;
+    }
     *count = launch_count(h->h, forces != 0, true);
     return ANKH_OK;
 }
