@@ -257,6 +257,13 @@ int ankh_energy_forces_batch(ankh_batch *b, const float *x, const float *q, cons
  * all boxes per group sharing xi and the near-field kernel variant.
  * Errors: ANKH_EINVAL (NULL). */
 int ankh_batch_launch_count(const ankh_batch *b, int *count);
+/* Optional timing of the batched near field: with enable != 0 the next
+ * batch call records CUDA events (inside its graph) before and after the
+ * near-field launches, and ankh_batch_near_ms returns their interval in
+ * milliseconds for the last such call (waiting for it).  Errors:
+ * ANKH_EINVAL (NULL; for ankh_batch_near_ms, no timed call yet), ANKH_ECUDA. */
+int ankh_batch_set_timing(ankh_batch *b, int enable);
+int ankh_batch_near_ms(const ankh_batch *b, double *ms);
 /* Borrow the handle of box i (owned by the batch; do not destroy it). */
 int ankh_batch_box(const ankh_batch *b, int i, ankh_handle **h);
 void ankh_destroy_batch(ankh_batch *b);

@@ -32,7 +32,7 @@ EXPORTED = ["ankh_default_params", "ankh_create", "ankh_create_cached", "ankh_en
             "ankh_ldm", "ankh_set_timing", "ankh_stage_times", "ankh_bin_sort_noalloc", "ankh_destroy",
             "ankh_last_error", "ankh_version", "ankh_create_batch", "ankh_energy_forces_batch",
             "ankh_batch_box", "ankh_destroy_batch", "ankh_induce", "ankh_measure_fp32_peak", "ankh_debug_fft", "ankh_accuracy_rule",
-            "ankh_launch_count", "ankh_batch_launch_count"]
+            "ankh_launch_count", "ankh_batch_launch_count", "ankh_batch_set_timing", "ankh_batch_near_ms"]
 STAGES = ["sort", "self", "p2m", "merge", "fft_fwd", "spectral", "corr", "near", "fft_inv", "l2p",
           "unused", "reduce"]
 
@@ -113,6 +113,10 @@ def load_library(path: str = LIB_PATH):
         lib.ankh_launch_count.restype = ctypes.c_int
         lib.ankh_batch_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
         lib.ankh_batch_launch_count.restype = ctypes.c_int
+        lib.ankh_batch_set_timing.argtypes = [vp, ctypes.c_int]
+        lib.ankh_batch_set_timing.restype = ctypes.c_int
+        lib.ankh_batch_near_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+        lib.ankh_batch_near_ms.restype = ctypes.c_int
         lib.ankh_destroy_batch.argtypes = [vp]
         lib.ankh_destroy_batch.restype = None
         lib.ankh_destroy.argtypes = [vp]
@@ -412,6 +416,17 @@ def ankh_batch_launch_count(b) -> int:
     out = ctypes.c_int()
     _check(load_library().ankh_batch_launch_count(b, ctypes.byref(out)))
     return int(out.value)
+
+
+def ankh_batch_set_timing(b, enable: bool) -> None:
+    _check(load_library().ankh_batch_set_timing(b, 1 if enable else 0))
+
+
+def ankh_batch_near_ms(b) -> float:
+    """Duration of the batched near field in the last timed batch call (ms)."""
+    out = ctypes.c_double()
+    _check(load_library().ankh_batch_near_ms(b, ctypes.byref(out)))
+    return float(out.value)
 
 
 def ankh_batch_box(h, i: int) -> ctypes.c_void_p:

@@ -1097,12 +1097,18 @@ struct ankh_batch {
     cudaGraphExec_t exec = nullptr;
     const void *last[11] = {nullptr};
     bool have_exec = false;
+    // ankh_batch_set_timing: events around the batched near-field launches,
+    // recorded by the graph (external event nodes)
+    cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;
+    bool timing = false, timed_graph = false;
 };
 
 static void batch_free(ankh_batch *b)
 {
     if (!b) return;
     for (auto &g : b->near_groups) near_batch_free(g);
+    if (b->ev_t0) cudaEventDestroy(b->ev_t0);
+    if (b->ev_t1) cudaEventDestroy(b->ev_t1);
     if (b->ev_near) cudaEventDestroy(b->ev_near);
     if (b->nearst) cudaStreamDestroy(b->nearst);
     if (b->exec) cudaGraphExecDestroy(b->exec);
@@ -1209,6 +1215,28 @@ int ankh_launch_count(const ankh_handle *h, int forces, int *count)
     return ANKH_OK;
 }
 
+int ankh_batch_set_timing(ankh_batch *b, int enable)
+{
+    if (!b) return fail(ANKH_EINVAL, "batch is NULL");
+    if (enable && !b->ev_t0) {
+        if (cudaEventCreate(&b->ev_t0) != cudaSuccess || cudaEventCreate(&b->ev_t1) != cudaSuccess)
+            return fail(ANKH_ECUDA, "cudaEventCreate");
+    }
+    b->timing = enable != 0;
+    return ANKH_OK;
+}
+
+int ankh_batch_near_ms(const ankh_batch *b, double *ms)
+{
+    if (!b || !ms) return fail(ANKH_EINVAL, "NULL argument");
+    if (!b->timing || !b->timed_graph) return fail(ANKH_EINVAL, "no timed batch call since ankh_batch_set_timing");
+    ANKH_CU(cudaEventSynchronize(b->ev_t1), "cudaEventSynchronize");
+    float t = 0.f;
+    ANKH_CU(cudaEventElapsedTime(&t, b->ev_t0, b->ev_t1), "cudaEventElapsedTime");
+    *ms = t;
+    return ANKH_OK;
+}
+
 int ankh_batch_launch_count(const ankh_batch *b, int *count)
 {
     if (!b || !count) return fail(ANKH_EINVAL, "NULL argument");
@@ -1232,7 +1260,7 @@ int ankh_energy_forces_batch(ankh_batch *b, const float *x, const float *q, cons
     if (!b || !x || !q || !E_host) return fail(ANKH_EINVAL, "batch, x, q and E_host are required");
     cudaStream_t s = (cudaStream_t)cuda_stream;
     const void *ptrs[11] = {x, q, mu, theta, dEdx, dEdq, dEdmu, dEdtheta, torque, (const void *)s, nullptr};
-    bool same = b->have_exec;
+    bool same = b->have_exec && b->timed_graph == b->timing;
     for (int k = 0; k < 10 && same; ++k) same = (ptrs[k] == b->last[k]);
     if (!same) {
         if (b->exec) cudaGraphExecDestroy(b->exec);
@@ -1260,9 +1288,11 @@ int ankh_energy_forces_batch(ankh_batch *b, const float *x, const float *q, cons
             cudaEventRecord(b->joins[k], b->streams[k]);
             cudaStreamWaitEvent(b->nearst, b->joins[k], 0);
         }
+        if (b->timing) cudaEventRecordWithFlags(b->ev_t0, b->nearst, cudaEventRecordExternal);
         for (auto &g : b->near_groups)
             if (rc == ANKH_OK && launch_near_batch(g, true, b->nearst) != cudaSuccess)
                 rc = fail(ANKH_ECUDA, "batched near field");
+        if (b->timing) cudaEventRecordWithFlags(b->ev_t1, b->nearst, cudaEventRecordExternal);
         cudaEventRecord(b->ev_near, b->nearst);
         // (3) every box's far field up to the adjacent-leaf correction
         for (size_t i = 0; i < b->boxes.size() && rc == ANKH_OK; ++i)
@@ -1295,6 +1325,7 @@ int ankh_energy_forces_batch(ankh_batch *b, const float *x, const float *q, cons
         ANKH_CU(cudaGraphInstantiate(&b->exec, b->graph, 0), "graph instantiate");
         for (int k = 0; k < 10; ++k) b->last[k] = ptrs[k];
         b->have_exec = true;
+        b->timed_graph = b->timing;
     }
     ANKH_CU(cudaGraphLaunch(b->exec, s), "graph launch");
     ANKH_CU(cudaStreamSynchronize(s), "synchronize");

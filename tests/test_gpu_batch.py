@@ -88,3 +88,34 @@ def test_handles_of_different_sizes_coexist(api):
     assert m1.energy(f(big.x), f(big.q), f(big.mu), f(big.theta)) == E1
     for m in [m1] + others:
         m.close()
+
+
+def test_batch_near_field_timing(api):
+    """ankh_batch_set_timing records events around the batched near field
+    inside the batch graph: a positive duration, shorter than the call, and
+    the same results bit for bit as an untimed call."""
+    import torch
+    sizes = [1000, 2200, 1500]
+    boxes = [synth.water_box(w, 9100 + i, multipoles=True, name=f"t{i}") for i, w in enumerate(sizes)]
+    cat = lambda f: torch.from_numpy(np.ascontiguousarray(np.concatenate([f(b) for b in boxes]),
+                                                          dtype=np.float32)).cuda()
+    x, q, mu, th = cat(lambda b: b.x), cat(lambda b: b.q), cat(lambda b: b.mu), cat(lambda b: b.theta)
+    bt = api.AnkhBatch([b.box for b in boxes], [b.n for b in boxes], Lu=5)
+    E0, g0 = bt.energy_forces(x, q, mu, th)
+    api.ankh_batch_set_timing(bt.h, True)
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    E1, _ = bt.energy_forces(x, q, mu, th, out=g0)
+    e1.record(s)
+    e1.synchronize()
+    ms = api.ankh_batch_near_ms(bt.h)
+    assert 0.0 < ms <= e0.elapsed_time(e1)
+    assert E1 == E0
+    g1 = {k: v.clone() for k, v in g0.items()}
+    api.ankh_batch_set_timing(bt.h, False)
+    E2, _ = bt.energy_forces(x, q, mu, th, out=g0)
+    assert E2 == E0
+    for k in g0:
+        assert torch.equal(g0[k], g1[k])
+    bt.close()
