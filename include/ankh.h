@@ -282,9 +282,9 @@ int ankh_stage_times(const ankh_handle *h, double ms[ANKH_NUM_STAGES]);
 
 /* Leaf binning and stable sort without any allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot call
- * cudaMalloc (an engine that plans all device memory at start-up, code that
- * runs while its stream is captured into a CUDA graph, a host whose device
- * allocator belongs to another runtime).  Its output equals the output of the
+ * cudaMalloc (an engine that plans all device memory at start-up and treats
+ * a later allocation as an error, a host whose device allocator belongs to
+ * another runtime and must not be bypassed).  Its output equals the output of the
  * sort stage of ankh_energy (the leaf of each atom by the correctly rounded
  * FP64 chain of that stage, without its FP32 screen, then the stable radix
  * sort by leaf), with its scratch in a static device array of the library

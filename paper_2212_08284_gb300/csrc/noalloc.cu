@@ -2,9 +2,8 @@
 //
 // Some callers cannot call cudaMalloc: a molecular-dynamics engine that plans
 // all device memory at start-up and treats any later allocation as an error,
-// code that runs while its stream is being captured into a CUDA graph (where
-// cudaMalloc is not allowed), or a host application whose device allocator
-// belongs to another runtime.  For them, ankh_bin_sort_noalloc produces the
+// or a host application whose device allocator belongs to another runtime and
+// must not be bypassed.  For them, ankh_bin_sort_noalloc produces the
 // output of the sort stage of the handle-based path (the leaf of every atom by
 // the correctly rounded FP64 chain, then the stable radix sort by leaf), with
 // its scratch (per-atom leaf ids, the values between radix passes, per-leaf

@@ -2,8 +2,8 @@
 the allocating path.
 
 ankh_bin_sort_noalloc serves callers that cannot call cudaMalloc (an engine
-that plans all device memory at start-up, code running inside CUDA-graph
-stream capture, a host whose allocator belongs to another runtime); its
+that plans all device memory at start-up, a host whose allocator belongs to
+another runtime); its
 scratch is a static device array of the library.  Binning and sorting are
 integer work, so the comparison is bit-exact.  Two calls in a row check that
 the shared static scratch is reset correctly between calls.  The cases cover
