@@ -46,7 +46,7 @@ FP32_LANES_PER_SM = 128
 # Entries are removed whenever the kernel changes and re-measured.
 DRAM_TRAFFIC: dict = {
     # stage: kernels (read + write per launch); the timed evaluation, ncu, one pass per kernel
-    ("near", "water_1008000_qmuTheta", 54, 5): 95.30e6,      # k_near
+    ("near", "water_1008000_qmuTheta", 54, 5): 95.81e6,      # k_near (one-warp blocks)
     ("corr", "water_1008000_qmuTheta", 54, 5): 336.45e6,     # k_split_f16 + k_corr_tc
     ("p2m", "water_1008000_qmuTheta", 54, 5): 93.69e6,       # k_p2m
     ("l2p", "water_1008000_qmuTheta", 54, 5): 368.92e6,      # k_l2p

@@ -54,7 +54,11 @@ namespace ankh {
 //   kSeriesShort 4 terms (xi r_max <= 0.2; the next term is below 3e-9 of B0)
 enum { kErfcLib = 0, kSeriesLong = 1, kSeriesShort = 2 };
 
-constexpr int kNearWarps = 4;
+// One warp per block: a block's energy partial waits for all its warps, and
+// with several warps a warp that drew light items sat at that barrier holding
+// its slot (four-warp blocks: 12 % of the warp slots parked there); a
+// one-warp block frees its slot the moment its items are done.
+constexpr int kNearWarps = 1;
 constexpr int kNearChunk = 64;
 // Items per warp: the launch covers the largest possible item count with
 // max_items / (k kNearWarps) blocks, which the hardware hands to the SMs as
@@ -64,7 +68,7 @@ constexpr int kNearChunk = 64;
 // waves of resident blocks (fewer blocks, fewer energy partials), else 2 or
 // 1, so that a box of some ten thousand atoms still fills every SM.
 constexpr int kNearMaxItemsPerWarp = 4;
-constexpr int kNearBlocksPerSM = 7;   // resident blocks of 128 threads (<= 73 registers per thread)
+constexpr int kNearBlocksPerSM = 28;   // resident one-warp blocks (<= 73 registers per thread)
 constexpr int kNearMinWaves = 8;
 
 template <bool FORCES>
@@ -193,7 +197,7 @@ __device__ __forceinline__ void near_block(const NearBox &a, const BCoef &bc, in
     const int nonperiodic = a.nonperiodic;
     constexpr int K = NAcc<FORCES>::K;
     __shared__ float4 sSrc[kNearWarps][kNearChunk][4];
-    __shared__ int sBeg[kNearWarps][28], sPre[kNearWarps][28];
+    __shared__ int sBeg[kNearWarps][28], sPre[kNearWarps][32];
     __shared__ float sRed[kNearWarps][K][32];
     __shared__ int sZero[kNearWarps][32];
     __shared__ double sE[kNearWarps];
@@ -231,7 +235,7 @@ __device__ __forceinline__ void near_block(const NearBox &a, const BCoef &bc, in
             sBeg[warp][lane] = beg;
             sPre[warp][lane] = incl - cnt;
         }
-        if (lane == 27) sPre[warp][27] = ns;
+        if (lane >= 27) sPre[warp][lane] = ns;
         __syncwarp();
         {
             const int nt = min(32, nt_all - t0);
@@ -257,14 +261,11 @@ __device__ __forceinline__ void near_block(const NearBox &a, const BCoef &bc, in
                 __syncwarp();
                 for (int k = lane; k < cs; k += 32) {
                     const int f = c0 + k;
-                    // leaf d with sPre[d] <= f < sPre[d+1]
-                    int lo = 0, hi = 27;
-                    while (hi - lo > 1) {
-                        const int mid = (lo + hi) >> 1;
-                        if (sPre[warp][mid] <= f) lo = mid;
-                        else hi = mid;
-                    }
-                    const int d = lo;
+                    // leaf d with sPre[d] <= f < sPre[d+1]: five fixed halving steps
+                    // over the prefixes, padded to 32 entries with ns (> f)
+                    int d = 0;
+#pragma unroll
+                    for (int st = 16; st > 0; st >>= 1) d += sPre[warp][d + st] <= f ? st : 0;
                     const int slot = sBeg[warp][d] + (f - sPre[warp][d]);
                     float4 a0 = A0[slot];
                     const float4 a1 = A1[slot], a2 = A2[slot], a3 = A3[slot];
@@ -352,7 +353,7 @@ __device__ __forceinline__ void near_block(const NearBox &a, const BCoef &bc, in
 }
 
 template <bool FORCES, int MODE>
-__global__ void __launch_bounds__(kNearWarps * 32, 7) k_near(const __grid_constant__ NearBox a, BCoef bc)
+__global__ void __launch_bounds__(kNearWarps * 32, kNearBlocksPerSM) k_near(const __grid_constant__ NearBox a, BCoef bc)
 {
     near_block<FORCES, MODE>(a, bc, blockIdx.x, gridDim.x);
 }
@@ -363,7 +364,7 @@ __global__ void __launch_bounds__(kNearWarps * 32, 7) k_near(const __grid_consta
 // partials and gradients.  All boxes of one launch share xi (bc) and the
 // B0 evaluation.
 template <bool FORCES, int MODE>
-__global__ void __launch_bounds__(kNearWarps * 32, 7)
+__global__ void __launch_bounds__(kNearWarps * 32, kNearBlocksPerSM)
 k_near_batch(const NearBox *__restrict__ boxes, const int *__restrict__ block0, int nbox, BCoef bc)
 {
     __shared__ int sbox;
